@@ -1,0 +1,168 @@
+"""Seeded synthetic graphs shaped like the paper's workloads.
+
+This module only draws inputs: edge lists, sources and feature matrices. It holds none of the
+propagation arithmetic, so both the FP64 oracle and the CUDA library can take their inputs from it.
+
+The paper evaluates on social and citation graphs (YouTube, Orkut, Twitter, Friendster, Reddit,
+Yelp, Amazon, Papers100M; Section 5, Tables 3 and 4). Those datasets are not available here, so
+the generators below stand in for them with the same node counts, edge counts and power-law degree
+skew:
+
+* R-MAT (Chakrabarti et al., SDM'04): recursive quadrant choice with probabilities (a, b, c, d).
+* Chung-Lu (Chung and Lu, 2002): edge (u, v) drawn with probability proportional to w_u * w_v,
+  expected degrees w following a power law with the given exponent, capped at sqrt(sum w).
+
+Every generator returns exactly ``m`` distinct undirected edges without self-loops, as two int32
+arrays ``(u, v)`` with ``u < v`` before the random relabelling of node ids. Draws are repeated
+until at least ``m`` distinct edges exist; a uniformly random subset of any surplus is dropped.
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+
+import numpy as np
+
+__all__ = [
+    "rmat_edges",
+    "chung_lu_edges",
+    "chung_lu_weights",
+    "cached",
+]
+
+
+def _distinct_sorted(keys):
+    """Sorted distinct values of an int64 array (sort + adjacent compare)."""
+    keys = np.sort(keys)
+    if keys.size == 0:
+        return keys
+    keep = np.empty(keys.size, bool)
+    keep[0] = True
+    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+    return keys[keep]
+
+
+def _canonical(u, v, n):
+    lo = np.minimum(u, v).astype(np.int64)
+    hi = np.maximum(u, v).astype(np.int64)
+    keep = lo != hi
+    return lo[keep] * n + hi[keep]
+
+
+def _draw_until(m, n, draw, rng):
+    """Call ``draw(k)`` -> (u, v) until ``m`` distinct non-loop undirected edges exist.
+
+    If the draws hold more than ``m`` distinct edges, a uniformly random subset of the surplus is
+    removed, so the result is exactly ``m`` edges, sorted by (lo, hi).
+    """
+    keys = np.empty(0, np.int64)
+    want = int(m * 1.05) + 1024
+    while True:
+        u, v = draw(want)
+        keys = _distinct_sorted(np.concatenate([keys, _canonical(u, v, n)]))
+        if keys.size >= m:
+            break
+        want = int((m - keys.size) * 1.5) + 1024
+    surplus = keys.size - m
+    if surplus:
+        drop = rng.choice(keys.size, size=surplus, replace=False)
+        keep = np.ones(keys.size, bool)
+        keep[drop] = False
+        keys = keys[keep]
+    return keys // n, keys % n
+
+
+def _relabel(lo, hi, n, rng):
+    perm = rng.permutation(n).astype(np.int32)
+    return perm[lo], perm[hi]
+
+
+def rmat_edges(n: int, m: int, seed: int, a=0.57, b=0.19, c=0.19, scale: int | None = None):
+    """R-MAT graph with ``n`` nodes and exactly ``m`` distinct undirected edges.
+
+    Node ids are drawn on a ``2**scale`` grid (``scale`` defaults to ceil(log2 n)); draws with an
+    endpoint >= n are discarded and redrawn. Ids are randomly relabelled afterwards.
+    """
+    if scale is None:
+        scale = max(1, int(np.ceil(np.log2(max(n, 2)))))
+    rng = np.random.default_rng(seed)
+    ab, abc = a + b, a + b + c
+
+    def draw(k):
+        u = np.zeros(k, np.int64)
+        v = np.zeros(k, np.int64)
+        for _ in range(scale):
+            r = rng.random(k)
+            bu = (r >= ab).astype(np.int64)                       # quadrants c, d: lower half
+            bv = ((r >= a) & (r < ab)) | (r >= abc)               # quadrants b, d: right half
+            u = (u << 1) | bu
+            v = (v << 1) | bv.astype(np.int64)
+        keep = (u < n) & (v < n)
+        return u[keep], v[keep]
+
+    lo, hi = _draw_until(m, n, draw, rng)
+    return _relabel(lo, hi, n, rng)
+
+
+def chung_lu_weights(n: int, m: int, gamma: float):
+    """Expected degrees w_i proportional to (i+1)^(-1/(gamma-1)), sum 2m, capped at sqrt(2m).
+
+    The cap is applied iteratively with renormalisation so that the uncapped nodes carry the rest
+    of the total 2m.
+    """
+    w = np.arange(1, n + 1, dtype=np.float64) ** (-1.0 / (gamma - 1.0))
+    total = 2.0 * m
+    cap = np.sqrt(total)
+    capped = np.zeros(n, bool)
+    for _ in range(64):
+        free = ~capped
+        scale = (total - cap * capped.sum()) / w[free].sum()
+        ww = np.where(capped, cap, w * scale)
+        newly = (ww > cap) & free
+        if not newly.any():
+            return ww
+        capped |= newly
+    return np.minimum(ww, cap)
+
+
+def chung_lu_edges(n: int, m: int, gamma: float, seed: int):
+    """Chung-Lu graph with ``n`` nodes and exactly ``m`` distinct undirected edges.
+
+    Each draw picks both endpoints independently with probability proportional to the expected
+    degree, so the pair (u, v) has probability proportional to w_u * w_v. Ids are randomly
+    relabelled afterwards.
+    """
+    rng = np.random.default_rng(seed)
+    w = chung_lu_weights(n, m, gamma)
+    p = w / w.sum()
+
+    def draw(k):
+        # k iid endpoint pairs: the multiset of first endpoints comes from multinomial counts;
+        # the second endpoints are drawn the same way and put in random order, which pairs
+        # them independently with the first ones.
+        ids = np.arange(n, dtype=np.int64)
+        u = np.repeat(ids, rng.multinomial(k, p))
+        v = np.repeat(ids, rng.multinomial(k, p))
+        rng.shuffle(v)
+        return u, v
+
+    lo, hi = _draw_until(m, n, draw, rng)
+    return _relabel(lo, hi, n, rng)
+
+
+def cached(tag: str, fn, *args, **kwargs):
+    """Run ``fn(*args, **kwargs)`` -> tuple of arrays, caching to ``$AGP_SYNTH_CACHE`` if set."""
+    root = os.environ.get("AGP_SYNTH_CACHE")
+    if not root:
+        return fn(*args, **kwargs)
+    key = hashlib.sha1(repr((tag, args, sorted(kwargs.items()))).encode()).hexdigest()[:16]
+    path = os.path.join(root, f"{tag}_{key}.npz")
+    if os.path.exists(path):
+        with np.load(path) as z:
+            return tuple(z[f"a{i}"] for i in range(len(z.files)))
+    out = fn(*args, **kwargs)
+    os.makedirs(root, exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, **{f"a{i}": x for i, x in enumerate(out)})
+    os.replace(tmp, path)
+    return out

@@ -1,0 +1,265 @@
+"""Pins for the oracle's CSR builder, tail sums and Algorithm 1 (exact propagation).
+
+Everything here runs on the CPU. Each check compares the oracle with something that is not the
+oracle: known-answer vectors, brute-force set logic, dense matrix powers, closed forms on regular
+graphs, linear solves, the paper's Figure 1 example and the mass invariant of a column-stochastic
+propagation matrix.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import _graphs as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox known answers
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(t, 16) for t in r]
+        out = oracle.philox4x32_10(vals[0:4], vals[4:6])
+        assert [int(x) for x in out] == vals[6:10]
+
+
+# ---------------------------------------------------------------- CSR builder
+def _csr_by_sets(n, src, dst, loops):
+    nb = [set() for _ in range(n)]
+    for s, d in zip(src.tolist(), dst.tolist()):
+        if s != d:
+            nb[s].add(d)
+            nb[d].add(s)
+    if loops:
+        for u in range(n):
+            nb[u].add(u)
+    deg = np.array([len(s) for s in nb], np.int32)
+    rows = [sorted(s, key=lambda v: (deg[v], v)) for s in nb]
+    return deg, rows
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("loops", [False, True])
+def test_csr_matches_set_construction(seed, loops):
+    n, src, dst = G.random_multigraph(60, 150, seed)
+    g = oracle.build_csr(n, src, dst, add_self_loops=loops)
+    deg, rows = _csr_by_sets(n, src, dst, loops)
+    np.testing.assert_array_equal(g.deg, deg)
+    assert g.rowptr[0] == 0 and np.all(np.diff(g.rowptr) == deg)
+    for u in range(n):
+        assert g.colidx[g.rowptr[u]:g.rowptr[u + 1]].tolist() == rows[u]
+
+
+def test_csr_rows_sorted_and_symmetric():
+    n, src, dst = G.random_multigraph(300, 2000, 7)
+    g = oracle.build_csr(n, src, dst)
+    for u in range(n):
+        row = g.colidx[g.rowptr[u]:g.rowptr[u + 1]]
+        keys = [(g.deg[v], v) for v in row]
+        assert keys == sorted(keys) and len(set(row.tolist())) == row.size and u not in row
+        for v in row:
+            rv = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+            assert u in rv
+
+
+def test_csr_empty_and_isolated():
+    g = oracle.build_csr(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert g.nnz == 0 and g.deg.tolist() == [0] * 5
+    g = oracle.build_csr(3, np.array([1], np.int32), np.array([1], np.int32))  # only a self-loop
+    assert g.nnz == 0
+    g = oracle.build_csr(3, np.array([0], np.int32), np.array([2], np.int32), add_self_loops=True)
+    assert g.deg.tolist() == [2, 1, 2]
+
+
+def test_csr_rejects_out_of_range():
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0], np.int32), np.array([3], np.int32))
+
+
+# ---------------------------------------------------------------- tail sums (Def. 3.1)
+def test_tail_sums_closed_forms():
+    L = 12
+    w, Y = oracle.tail_sums(oracle.PPR, L, 0.2)
+    np.testing.assert_allclose(w, 0.2 * 0.8 ** np.arange(L + 1), rtol=1e-15)
+    np.testing.assert_allclose(Y, 0.8 ** np.arange(L + 2), rtol=1e-15)
+    # HKPR: Y_0 = 1 (Poisson pmf sums to 1) and Y_i = 1 - P(N < i) for N ~ Poisson(t)
+    t = 5.0
+    w, Y = oracle.tail_sums(oracle.HKPR, 30, t)
+    pmf = np.array([math.exp(-t) * t ** k / math.factorial(k) for k in range(31)])
+    np.testing.assert_allclose(w, pmf, rtol=1e-12)
+    assert abs(Y[0] - 1.0) < 1e-14
+    cdf_lt = np.concatenate([[0.0], np.cumsum(pmf)])
+    for i in range(0, 8):  # where 1 - cdf has no cancellation problem
+        assert abs(Y[i] - (1.0 - cdf_lt[i])) < 1e-14
+    # deep tail is positive, decreasing and matches the next-term dominated estimate
+    assert np.all(np.diff(Y) < 0) and Y[31] > 0
+    assert abs(Y[30] / pmf[30] - 1.0) < 0.25
+    # Katz: Y_i = beta^i / (1 - beta)
+    w, Y = oracle.tail_sums(oracle.KATZ, 10, 0.3)
+    np.testing.assert_allclose(Y, 0.3 ** np.arange(12) / 0.7, rtol=1e-15)
+    # transition: w_L = 1
+    w, Y = oracle.tail_sums(oracle.TRANSITION, 4)
+    assert w.tolist() == [0, 0, 0, 0, 1] and Y.tolist() == [1, 1, 1, 1, 1, 0]
+    # finite list
+    w, Y = oracle.tail_sums(oracle.FINITE, 3, w=[0.5, 0.25, 0.0, 0.25])
+    assert Y.tolist() == [1.0, 0.5, 0.25, 0.25, 0.0]
+
+
+# ---------------------------------------------------------------- Algorithm 1 vs brute force
+@pytest.mark.parametrize("seed", range(6))
+def test_basic_matches_dense_matrix_powers(seed):
+    rng = np.random.default_rng(100 + seed)
+    n, src, dst = G.random_multigraph(40, 90, seed)
+    loops = bool(seed % 2)
+    g = oracle.build_csr(n, src, dst, add_self_loops=loops)
+    A = G.dense_adjacency(n, src, dst, loops)
+    a, b = rng.random(), rng.random()
+    L = int(rng.integers(1, 9))
+    w = rng.random(L + 1)
+    x = rng.standard_normal(n)
+    x[rng.random(n) < 0.5] = 0.0
+    wl, Y = oracle.tail_sums(oracle.FINITE, L, w=w)
+    got = oracle.basic(g, a, b, L, wl, Y, x)
+    want = G.dense_propagation(A, a, b, w, x)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+def test_basic_weight_rescaling_is_invisible():
+    """Section 3: propagating w/sum(w) and rescaling gives the same vector as w itself."""
+    n, src, dst = G.random_multigraph(30, 70, 11)
+    g = oracle.build_csr(n, src, dst)
+    x = np.zeros(n); x[3] = 1.0
+    w = np.array([0.3, 0.9, 0.0, 2.0])
+    wl, Y = oracle.tail_sums(oracle.FINITE, 3, w=w)
+    got = oracle.basic(g, 0.5, 0.5, 3, wl, Y, x)
+    want = G.dense_propagation(G.dense_adjacency(n, src, dst), 0.5, 0.5, w, x)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- closed forms
+def test_complete_graph_closed_forms():
+    n, s = 9, 4
+    g = oracle.build_csr(*G.complete(n))
+    e = np.zeros(n); e[s] = 1.0
+    # L-hop transition: P^L e_s = 1/n + (-1/(n-1))^L (e_s - 1/n)
+    for L in (1, 2, 5):
+        w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+        want = 1.0 / n + (-1.0 / (n - 1)) ** L * (e - 1.0 / n)
+        np.testing.assert_allclose(oracle.basic(g, 0, 1, L, w, Y, e), want, rtol=1e-13)
+    # PPR truncated at L: 1/n * (1-(1-alpha)^{L+1}) + alpha (1-q^{L+1})/(1-q) (e_s - 1/n), q = -(1-alpha)/(n-1)
+    alpha, L = 0.2, 20
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    q = -(1 - alpha) / (n - 1)
+    want = (1 - (1 - alpha) ** (L + 1)) / n + alpha * (1 - q ** (L + 1)) / (1 - q) * (e - 1.0 / n)
+    np.testing.assert_allclose(oracle.basic(g, 0, 1, L, w, Y, e), want, rtol=1e-13)
+    # HKPR, infinite sum (L large): 1/n + exp(-t n/(n-1)) (e_s - 1/n)
+    t = 3.0
+    w, Y = oracle.tail_sums(oracle.HKPR, 60, t)
+    want = 1.0 / n + math.exp(-t * n / (n - 1)) * (e - 1.0 / n)
+    np.testing.assert_allclose(oracle.basic(g, 0, 1, 60, w, Y, e), want, rtol=1e-12)
+    # on a regular graph D^-1/2 A D^-1/2 = D^-1 A = A D^-1 (SGC / single-target PPR forms)
+    for a, b in ((0.5, 0.5), (1.0, 0.0)):
+        np.testing.assert_allclose(oracle.basic(g, a, b, 60, w, Y, e), want, rtol=1e-12)
+
+
+def test_cycle_ppr_closed_form():
+    n, alpha = 11, 0.2
+    g = oracle.build_csr(*G.cycle(n))
+    e = np.zeros(n); e[0] = 1.0
+    L = 200  # (1-alpha)^{L+1} < 1e-19
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    got = oracle.basic(g, 0, 1, L, w, Y, e)
+    rho = (1 - math.sqrt(1 - (1 - alpha) ** 2)) / (1 - alpha)
+    Cc = math.sqrt(alpha / (2 - alpha))
+    j = np.arange(n)
+    closed = Cc * (rho ** j + rho ** (n - j)) / (1 - rho ** n)
+    np.testing.assert_allclose(got, closed, rtol=1e-12)
+    # and the DFT form of the same circulant inverse
+    k = np.arange(n)
+    dft = np.array([(alpha / n) * np.sum(np.cos(2 * np.pi * k * jj / n) / (1 - (1 - alpha) * np.cos(2 * np.pi * k / n))) for jj in j])
+    np.testing.assert_allclose(got, dft, rtol=1e-12)
+
+
+def test_cycle_transition_binomial_fold():
+    n, L = 7, 9
+    g = oracle.build_csr(*G.cycle(n))
+    e = np.zeros(n); e[0] = 1.0
+    w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+    want = np.zeros(n)
+    for k in range(L + 1):
+        want[(2 * k - L) % n] += math.comb(L, k) / 2 ** L
+    np.testing.assert_allclose(oracle.basic(g, 0, 1, L, w, Y, e), want, rtol=1e-14)
+
+
+def test_ppr_linear_solve():
+    """PPR fixed point pi = alpha (I - (1-alpha) A D^-1)^-1 x (Section 2, PageRank definition)."""
+    n, src, dst = G.random_multigraph(50, 160, 5, loops=False)
+    g = oracle.build_csr(n, src, dst)
+    A = G.dense_adjacency(n, src, dst)
+    keep = A.sum(1) > 0
+    alpha = 0.25
+    x = np.where(keep, np.random.default_rng(1).random(n), 0.0)
+    x /= x.sum()
+    d = A.sum(1)
+    P = A / np.where(d > 0, d, 1.0)[None, :]
+    want = alpha * np.linalg.solve(np.eye(n) - (1 - alpha) * P, x)
+    L = 150
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    np.testing.assert_allclose(oracle.basic(g, 0, 1, L, w, Y, x), want, rtol=1e-12, atol=1e-16)
+
+
+def test_katz_linear_solve_and_lambda():
+    """Katz: sum beta^i A^i e_s = (I - beta A)^-1 e_s for beta < 1/lambda_1 (Table 1)."""
+    n, src, dst = G.random_multigraph(40, 100, 9, loops=False)
+    g = oracle.build_csr(n, src, dst)
+    A = G.dense_adjacency(n, src, dst)
+    lam_np = np.linalg.eigvalsh(A).max()
+    lam = oracle.power_lambda(g, iters=5000, tol=1e-15)
+    assert abs(lam - lam_np) < 1e-9 * lam_np
+    beta = 0.5 / lam_np
+    L = 80  # (beta lambda)^{L+1} / (1 - beta lambda) < 1e-24
+    w, Y = oracle.tail_sums(oracle.KATZ, L, beta)
+    s = int(np.argmax(A.sum(1)))
+    e = np.zeros(n); e[s] = 1.0
+    want = np.linalg.solve(np.eye(n) - beta * A, e)
+    np.testing.assert_allclose(oracle.basic(g, 0, 0, L, w, Y, e), want, rtol=1e-12)
+
+
+def test_figure1_two_step_transition():
+    golden = {l.split()[0]: float(l.split()[1]) for l in open(os.path.join(GOLDEN, "fig1_toy_graph.txt"))
+              if l.strip() and not l.startswith("#")}
+    k = 25
+    n, src, dst = G.fig1(k)
+    g = oracle.build_csr(n, src, dst)
+    e = np.zeros(n); e[0] = 1.0
+    w, Y = oracle.tail_sums(oracle.TRANSITION, 2)
+    pi = oracle.basic(g, 0, 1, 2, w, Y, e)
+    assert abs(pi[0] - golden["s"]) < 1e-15 and abs(pi[1] - golden["v"]) < 1e-15
+    assert np.all(pi[2:] == golden["u"])
+
+
+def test_mass_invariant_column_stochastic():
+    """a=0, b=1, no isolated node: ||r^(i)||_1 = Y_i ||x||_1 and sum pi = sum_{i<=L} w_i ||x||_1."""
+    n, src, dst = G.random_multigraph(80, 300, 21, loops=False)
+    g = oracle.build_csr(n, src, dst)
+    keep = g.deg > 0
+    x = np.where(keep, np.random.default_rng(2).random(n), 0.0)
+    w, Y = oracle.tail_sums(oracle.HKPR, 15, 4.0)
+    pi = oracle.basic(g, 0, 1, 15, w, Y, x)
+    assert abs(pi.sum() - w.sum() * x.sum()) < 1e-12 * x.sum()
+
+
+def test_signed_signal_is_linear():
+    n, src, dst = G.random_multigraph(30, 80, 4)
+    g = oracle.build_csr(n, src, dst)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(n)
+    w, Y = oracle.tail_sums(oracle.PPR, 8, 0.1)
+    whole = oracle.basic(g, 0.5, 0.5, 8, w, Y, x)
+    plus = oracle.basic(g, 0.5, 0.5, 8, w, Y, np.maximum(x, 0))
+    minus = oracle.basic(g, 0.5, 0.5, 8, w, Y, np.maximum(-x, 0))
+    np.testing.assert_allclose(whole, plus - minus, rtol=1e-12, atol=1e-14)
