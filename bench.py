@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched AGP push on one GB300 (or N replicas).
+
+Workload (the batched Katz / transition-probability configuration): Chung-Lu power-law graph,
+exponent 2.1, 4,000,000 nodes, 120,000,000 distinct undirected edges (a synthetic stand-in for the
+paper's Orkut/YouTube-class social graphs). One step = one launch of 256 Katz queries
+(a = b = 0, w_i = beta^i, beta = 0.85 / lambda_1 with lambda_1 from the library's FP64 power
+iteration, L = 20) plus one launch of 256 L-hop transition-probability queries (a = 0, b = 1,
+w_4 = 1, L = 4), eps = 1e-8, from 256 degree-weighted random sources each (fresh sources every
+step, fixed seeds). Metric: queries per second, whole job.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl agp|reference] [--small]
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs the same workload on its own
+GPU (replicas, weak scaling) and the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import graphs as SG  # noqa: E402
+
+S = 20210603
+HBM_FALLBACK_GBS = 6800.0
+
+# Algorithmic bytes per unit of work (roofline numerator), per kernel:
+#   frontier item (expand): item id 4 + r read 4 + r clear 4 + reserve RMW 8 + degree 4 + row start 8
+#   deterministic push:     colidx 4 + residue atomic RMW 8 (+ neighbour degree 4 when a > 0)
+#   sampler trial:          colidx 4 (+ neighbour degree 4 when a > 0)
+#   accepted sample:        residue atomic RMW 8
+#   frontier append:        item id write 4
+B_ITEM, B_DET, B_TRIAL, B_ACC, B_APPEND, B_DEG = 32, 12, 4, 8, 4, 4
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------------------- workload
+def workload(small: bool):
+    if small:
+        return dict(name="rmat-2^14 ppr+transition (small)", n=16384, m=131072, kind="rmat", Q=64, L_katz=20,
+                    eps=1e-7, seed_graph=S + 1, seed_src=S + 101)
+    return dict(name="chung-lu-2.1 n=4M m=120M katz(L=20)+transition(L=4) x256 sources, eps=1e-8",
+                n=4_000_000, m=120_000_000, kind="chung_lu", Q=256, L_katz=20, eps=1e-8,
+                seed_graph=S + 2, seed_src=S + 102)
+
+
+def make_edges(wl):
+    if wl["kind"] == "rmat":
+        return SG.cached("rmat", SG.rmat_edges, wl["n"], wl["m"], wl["seed_graph"])
+    return SG.cached("chunglu", SG.chung_lu_edges, wl["n"], wl["m"], 2.1, wl["seed_graph"])
+
+
+def degree_weighted_sources(n, u, v, count, seed):
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    p = deg / deg.sum()
+    rng = np.random.default_rng(seed)
+    return rng.choice(n, size=count, p=p).astype(np.int32)
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="agp_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = [l.split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- oracle baseline
+def oracle_sample(n, u, v, sources, eps, L=4, threads=None):
+    """Time the FP64 oracle (Algorithm 2, as it stands) on transition queries in parallel threads."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    og = oracle.build_csr(n, u, v)
+    w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+    t_csr = time.perf_counter() - t0
+    threads = threads or min(len(sources), os.cpu_count() or 1)
+
+    def one(s):
+        x = np.zeros(n)
+        x[s] = 1.0
+        return oracle.randomized(og, 0, 1, L, w, Y, eps, x, int(s))
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, [int(s) for s in sources[:threads]]))
+    dt = time.perf_counter() - t0
+    return og, threads, dt, t_csr
+
+
+def run_reference(args, wl, rank):
+    """Reference arm: the FP64 oracle on the host cores, same workload, bounded sample per step."""
+    if rank != 0:
+        return
+    u, v = make_edges(wl)
+    n = wl["n"]
+    srcs = degree_weighted_sources(n, u, v, wl["Q"] * 2 * (args.warmup + args.steps), wl["seed_src"])
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    og = oracle.build_csr(n, u, v)
+    w, Y = oracle.tail_sums(oracle.TRANSITION, 4)
+    threads = min(os.cpu_count() or 1, 16)
+
+    def one(s):
+        x = np.zeros(n)
+        x[s] = 1.0
+        oracle.randomized(og, 0, 1, 4, w, Y, wl["eps"], x, int(s))
+
+    def step(k, count):
+        base = k * 2 * wl["Q"] + wl["Q"]  # the transition half of step k's sources
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, [int(s) for s in srcs[base:base + count]]))
+
+    for k in range(args.warmup):
+        step(k, 1)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        step(args.warmup + k, threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = threads * args.steps / total
+    sample = (f"{threads} of the 256 L=4 transition queries of each step, one per host thread (the oracle "
+              f"runs per-neighbour Bernoulli trials; its eps=1e-8 Katz queries take minutes each and are left out)")
+    line = {"impl": "reference", "metric": "queries/s", "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="agp", choices=["agp", "reference"])
+    ap.add_argument("--small", action="store_true", help="small R-MAT workload (quick check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-queries", type=int, default=16)
+    args = ap.parse_args()
+    wl = workload(args.small)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, wl, rank)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2106_03058_gb300 as agp
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t0 = time.perf_counter()
+    u, v = make_edges(wl)
+    n, Q = wl["n"], wl["Q"]
+    log(f"[bench] edges ready in {time.perf_counter() - t0:.1f}s")
+    agp.lib()
+    t0 = time.perf_counter()
+    g = agp.build_graph(n, u, v, device=local)
+    log(f"[bench] graph built on GPU in {time.perf_counter() - t0:.2f}s (nnz={g.nnz})")
+    beta, lam = agp.katz_beta(g, 0.85, iters=1000, tol=1e-12)
+    log(f"[bench] lambda_1={lam:.6f} beta={beta:.6e}")
+
+    steps_total = args.warmup + args.steps
+    srcs = degree_weighted_sources(n, u, v, Q * 2 * steps_total, wl["seed_src"])
+    d_srcs = torch.as_tensor(srcs, device=dev)
+    off = torch.arange(Q + 1, dtype=torch.int64, device=dev)
+    out_k = torch.empty((Q, n), dtype=torch.float32, device=dev)
+    out_t = torch.empty((Q, n), dtype=torch.float32, device=dev)
+    eps = wl["eps"]
+
+    def params_for(step):
+        pk = [agp.katz(beta, wl["L_katz"], eps, seed=S + step * 4096 + q) for q in range(Q)]
+        pt = [agp.transition(4, eps, seed=S + step * 4096 + 2048 + q) for q in range(Q)]
+        return pk, pt
+
+    all_params = [params_for(k) for k in range(steps_total)]
+    flags = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
+
+    def run_step(k, extra=0, stats=False):
+        pk, pt = all_params[k]
+        base = k * 2 * Q
+        f = flags | extra | (agp.COLLECT_STATS if stats else 0)
+        sk = agp.query_batch(g, pk, off, d_srcs[base:base + Q], None, out_k, n, f)
+        st = agp.query_batch(g, pt, off, d_srcs[base + Q:base + 2 * Q], None, out_t, n, f)
+        return sk, st
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for k in range(args.warmup):
+        run_step(k)
+    barrier_sync()
+    agp.profile_read(g, reset=True)
+    stream = torch.cuda.current_stream()
+    step_ms = []
+    with ClockSampler(local) as clocks:
+        barrier_sync()
+        for k in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run_step(args.warmup + k, agp.PROFILE)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        barrier_sync()
+    clk = clocks.summary()
+    kern_ms, kern_launches, total_launches = agp.profile_read(g, reset=True)
+    total_ms = max_over_ranks(sum(step_ms))
+    queries = 2 * Q * args.steps * world
+    value = queries / (total_ms / 1e3)
+
+    # per-kernel work of the timed steps (same sources and seeds, counted in a separate pass)
+    work = np.zeros((3, 4))
+    items = 0
+    for k in range(args.steps):
+        sk, st = run_step(args.warmup + k, 0, stats=True)
+        for s_ in list(sk) + list(st):
+            work += np.array([list(r) for r in s_.by_kernel], dtype=np.float64)
+            items += sum(s_.frontier[: s_.levels])
+    # a = 0 for both query types: no neighbour-degree gathers
+    bytes_k = {
+        "expand": items * B_ITEM + work[0, 0] * B_DET + work[0, 1] * B_TRIAL + work[0, 2] * B_ACC + work[0, 3] * B_APPEND,
+        "push": work[1, 0] * B_DET + work[1, 3] * B_APPEND,
+        "sample": work[2, 1] * B_TRIAL + work[2, 2] * B_ACC + work[2, 3] * B_APPEND,
+    }
+    dom = max(("expand", "push", "sample"), key=lambda k_: kern_ms[k_])
+    launches = max(kern_launches[dom], 1)
+    avg_ms = kern_ms[dom] / launches
+    achieved = (bytes_k[dom] / launches) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = float(json.load(open(peaks_path))["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        peak, peak_src = HBM_FALLBACK_GBS, "fallback"
+    edge_ops = work[:, 0].sum() + work[:, 2].sum()
+
+    # ---- plain path: one query per launch sequence, host-synchronised frontier sizes
+    plain_qps = None
+    if args.plain_queries > 0 and rank == 0:
+        k = args.warmup
+        pk, pt = all_params[k]
+        base = k * 2 * Q
+        half = args.plain_queries // 2
+        pf = flags | agp.PLAIN
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        agp.query_batch(g, pk[:half], off[:half + 1], d_srcs[base:base + half], None, out_k, n, pf)
+        agp.query_batch(g, pt[:half], off[:half + 1], d_srcs[base + Q:base + Q + half], None, out_t, n, pf)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        # the batched path on exactly the same queries, for a like-for-like ratio
+        t0 = time.perf_counter()
+        agp.query_batch(g, pk[:half], off[:half + 1], d_srcs[base:base + half], None, out_k, n, flags)
+        agp.query_batch(g, pt[:half], off[:half + 1], d_srcs[base + Q:base + Q + half], None, out_t, n, flags)
+        torch.cuda.synchronize()
+        dtb = time.perf_counter() - t0
+        plain_qps = {"plain_queries_per_s": 2 * half / dt, "batched_same_queries_per_s": 2 * half / dtb,
+                     "queries": 2 * half}
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    h_srcs = srcs.copy()
+    h_off = np.arange(Q + 1, dtype=np.int64)
+    h_out_k = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
+    h_out_t = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
+    e2e_times = []
+    barrier_sync()
+    for k in range(args.steps):
+        pk, pt = all_params[args.warmup + k]
+        base = (args.warmup + k) * 2 * Q
+        t0 = time.perf_counter()
+        agp.query_batch(g, pk, h_off, h_srcs[base:base + Q], None, h_out_k, n, 0)
+        agp.query_batch(g, pt, h_off, h_srcs[base + Q:base + 2 * Q], None, h_out_t, n, 0)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(e2e_times))
+    e2e_value = queries / e2e_total
+    h2d = 2 * (h_off.nbytes + Q * 4)
+    d2h = 2 * Q * n * 4
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        base = args.warmup * 2 * Q + Q
+        threads = min(os.cpu_count() or 1, 16)
+        _, used, dt, t_csr = oracle_sample(n, u, v, srcs[base:base + threads], eps, 4, threads)
+        cpu = {"value": used / dt, "unit": "queries/s", "cores": used, "kind": "oracle",
+               "sample": f"{used} of the 256 L=4 transition queries of one step, one per host thread, FP64 "
+                         f"Algorithm 2 with per-neighbour Bernoulli trials ({dt:.1f}s; CSR build {t_csr:.1f}s "
+                         f"excluded; Katz queries at eps=1e-8 take minutes each in the oracle and are left out)"}
+
+    if rank == 0:
+        line = {
+            "metric": "queries/s", "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "parallelism": f"replicas{world}", "queries_per_step": 2 * Q,
+                       "lambda_1": lam, "beta": beta,
+                       "l2": "flushed before every timed step (256 MB write); CSR 0.96 GB and 8 GB of residues exceed L2"},
+            "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)), "p99_step": float(np.percentile(step_ms, 99)),
+                           "note": "a query's latency is its launch's completion time"},
+            "edges_pushed_per_s": edge_ops * world / (total_ms / 1e3),
+            "plain_path": plain_qps,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bytes_k[dom] / launches, "avg_launch_ms": avg_ms},
+            "kernel_ms": kern_ms, "kernel_launches_profiled": kern_launches,
+            "gpu_launches": int(total_launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        }
+        print(json.dumps(line), flush=True)
+    g.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * agp.h -- C ABI of the GB300 library for Approximate Graph Propagation
+ * (Wang, He, Wei, Wang, Yuan, Du, Wen: "Approximate Graph Propagation", KDD'21, arXiv:2106.03058).
+ *
+ * The library estimates the graph propagation vector of Eq. (1), Section 2,
+ *
+ *     pi = sum_{i=0..L} w_i (D^-a A D^-b)^i x ,
+ *
+ * with the level-by-level randomized push of Algorithm 2 (Section 4): at level i every node u with
+ * a non-zero residue r^(i)(u) reserves (w_i/Y_i) r^(i)(u) (Def. 3.1, Y_i = sum_{k>=i} w_k),
+ * pushes the increment (Y_{i+1}/Y_i) r^(i)(u) / (d_u^b d_v^a) to every neighbour v for which that
+ * increment is >= eps (a prefix of the degree-sorted adjacency list, Section 4 "Pre-sorting"), and
+ * subset-samples every other neighbour with probability increment/eps, adding eps when sampled
+ * (Section 4 "Subset Sampling"). eps = 0 gives Algorithm 1 (exact propagation).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status (AGP_OK = 0 or one of the AGP_E* codes below). No call
+ *    aborts, traps or exits the process. agp_last_error_detail() gives a message for the last
+ *    failure on the calling thread.
+ *  - Device pointers are CUDA device addresses on the graph's device; host pointers are ordinary
+ *    process memory (pageable or pinned). Each argument states which one it takes.
+ *  - The caller owns every input and output buffer. The library owns the graph (device CSR and
+ *    its work buffers) until agp_graph_destroy, and serving results until agp_serve_release.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are stream-ordered and
+ *    return once their work is enqueued, except where an entry point says it synchronises.
+ *  - One graph handle must not be used by two host threads at the same time.
+ *  - Node ids are int32 in [0, n). Degrees count distinct neighbours.
+ */
+#ifndef AGP_H
+#define AGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AGP_API __attribute__((visibility("default")))
+#else
+#define AGP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define AGP_OK 0
+#define AGP_EINVAL 1     /* an argument is out of range or inconsistent                       */
+#define AGP_ENOMEM 2     /* a device or host allocation failed                                 */
+#define AGP_ECUDA 3      /* a CUDA runtime call failed (detail names it)                       */
+#define AGP_EBUDGET 4    /* the request does not fit the configured memory budget              */
+#define AGP_EAGAIN 5     /* serving: the result is not ready yet                               */
+#define AGP_ETIMEDOUT 6  /* a bounded wait ran out                                             */
+#define AGP_ECANCELED 7  /* serving: the request was cancelled                                 */
+#define AGP_EINTERNAL 8  /* a device-side consistency check failed (capacity, bounds)          */
+
+/* Human-readable name of a status code (static storage). */
+AGP_API const char *agp_strerror(int code);
+/* Message describing the last failure on the calling thread (thread-local storage, valid until
+ * the next failing call on this thread). Empty string if none. */
+AGP_API const char *agp_last_error_detail(void);
+/* Library version as 10000*major + 100*minor + patch. */
+AGP_API int agp_version(void);
+
+/* ---- graph -------------------------------------------------------------------------------- */
+typedef struct agp_graph_s *agp_graph_t;
+
+#define AGP_ADD_SELF_LOOPS 0x1u  /* add one self-loop per node, counted once in its degree        */
+#define AGP_EDGES_ON_DEVICE 0x2u /* src/dst are device pointers (else host pointers)               */
+
+/*
+ * Build the device CSR of an undirected graph: Section 4 "Pre-sorting adjacency list by degrees".
+ * Every input edge (src[e], dst[e]) makes each endpoint a neighbour of the other; repeated edges
+ * are merged and input self-loops dropped. With AGP_ADD_SELF_LOOPS every node then gets exactly
+ * one self-loop (the self-looped graph of SGC/GCN, Section 1). Each adjacency list N_u is stored
+ * in ascending (d_v, v) order, so the neighbours of small degree form a prefix.
+ *   n        number of nodes, 0 <= n < 2^31
+ *   n_edges  number of input edges (>= 0)
+ *   src,dst  n_edges int32 ids each, host or device memory (AGP_EDGES_ON_DEVICE); not retained
+ *   device   CUDA device ordinal that will hold the graph
+ *   stream   stream for the build; the call synchronises it before returning
+ *   out      receives the handle
+ * Errors: AGP_EINVAL (bad n, id out of range), AGP_ENOMEM, AGP_ECUDA.
+ */
+AGP_API int agp_build_graph(int64_t n, int64_t n_edges, const int32_t *src, const int32_t *dst,
+                    uint32_t flags, int device, void *stream, agp_graph_t *out);
+
+/* Sizes and device arrays of a built graph (library-owned, valid until agp_graph_destroy):
+ * rowptr int64[n+1], colidx int32[nnz], deg int32[n]. Any output pointer may be NULL. */
+AGP_API int agp_graph_info(agp_graph_t g, int64_t *n, int64_t *nnz, const int64_t **rowptr,
+                   const int32_t **colidx, const int32_t **deg);
+
+/* Free the graph and every work buffer it owns. Synchronises the device first. */
+AGP_API int agp_graph_destroy(agp_graph_t g);
+
+/* Device memory (bytes) the graph may use for query work buffers; 0 = default (60% of the free
+ * device memory at the first query). Work buffers are sized from it and reused across calls. */
+AGP_API int agp_graph_set_memory_budget(agp_graph_t g, int64_t bytes);
+
+/* ---- propagation parameters ---------------------------------------------------------------- */
+/* Weight sequences of Table 1. FINITE takes w_0..w_L from `w`; the others are generated with
+ * their infinite tails Y_i = sum_{k>=i} w_k (Def. 3.1):
+ *   PPR(param = alpha):  w_i = alpha (1-alpha)^i            (PageRank, PPR, APPNP)
+ *   HKPR(param = t):     w_i = e^-t t^i / i!                (heat kernel PageRank, GDC)
+ *   KATZ(param = beta):  w_i = beta^i, 0 < beta < 1         (Katz; beta < 1/lambda_1 for convergence)
+ *   TRANSITION:          w_L = 1, other w_i = 0             (L-hop transition probability, SGC)   */
+#define AGP_W_FINITE 0
+#define AGP_W_PPR 1
+#define AGP_W_HKPR 2
+#define AGP_W_KATZ 3
+#define AGP_W_TRANSITION 4
+
+#define AGP_MAX_LEVELS 64 /* L <= AGP_MAX_LEVELS - 1 */
+
+typedef struct {
+    double a, b;          /* Laplacian parameters, each in [0, 1] (Eq. 1)                         */
+    int32_t L;            /* number of levels, 0 <= L < AGP_MAX_LEVELS                            */
+    int32_t kind;         /* AGP_W_*                                                              */
+    double param;         /* alpha, t or beta for PPR, HKPR, KATZ                                 */
+    const double *w;      /* FINITE only: host array of L+1 non-negative weights, sum > 0        */
+    double eps;           /* error parameter of Algorithm 2, >= 0; 0 = exact (Algorithm 1)        */
+    uint64_t seed;        /* random stream of this query; results depend only on (inputs, seed) */
+} agp_params_t;
+
+/* Per-query counters (Theorem 4.3 counts cost as deterministic pushes plus accepted samples). */
+typedef struct {
+    int64_t frontier[AGP_MAX_LEVELS]; /* |{u : r^(i)(u) != 0}| per level, summed over sign parts */
+    int64_t det_edge_ops;             /* deterministic pushes (Algorithm 2, push loop)           */
+    int64_t samples_drawn;            /* candidate positions reached by the geometric skips      */
+    int64_t samples_accepted;         /* samples that added eps                                  */
+    /* the same counters split by the kernel that did the work (0 = expand, 1 = push, 2 = sample;
+     * see agp_profile_read): [kernel][0 deterministic pushes, 1 trials, 2 accepted, 3 frontier
+     * appends]                                                                                   */
+    int64_t by_kernel[3][4];
+    int32_t levels;                   /* L + 1 entries of `frontier` are meaningful              */
+    int32_t reserved;
+} agp_stats_t;
+
+/* Memory-location flags of the query entry points. */
+#define AGP_INPUT_ON_DEVICE 0x1u  /* x_off / x_idx / x_val are device pointers                */
+#define AGP_OUTPUT_ON_DEVICE 0x2u /* pi_out is a device pointer                                */
+#define AGP_PLAIN 0x4u            /* plain path: one query per launch sequence, host-synchronised
+                                     frontier sizes (the baseline the batched path is measured
+                                     against); same kernels, same results                      */
+#define AGP_COLLECT_STATS 0x8u    /* fill `stats` (adds counter atomics to the kernels)        */
+#define AGP_PROFILE 0x10u         /* record CUDA events around every kernel of the level loop
+                                     (inside the captured graph as well); read the per-kernel
+                                     device time with agp_profile_read                          */
+
+/*
+ * Batched queries (Algorithm 2 per query). Query q has the sparse signal
+ *     x_q = sum_{t = x_off[q] .. x_off[q+1]-1} x_val[t] * e_{x_idx[t]}
+ * (x_val == NULL means all ones; repeated indices add up). Negative entries are handled as
+ * Section 3 states: x = x+ + x-, each part normalised to unit L1 norm and propagated with its own
+ * random stream, pi = ||x+||_1 pi(x+/||x+||_1) - ||x-||_1 pi(x-/||x-||_1). Weights are normalised
+ * by Y_0 and the result rescaled (Section 3, "Assumptions on w_i"). eps applies to the normalised
+ * residues.
+ *   params    n_params == 1: shared by all queries; n_params == Q: one per query (host memory)
+ *   x_off     Q+1 int64 offsets; x_idx / x_val as above; host or device (AGP_INPUT_ON_DEVICE)
+ *   pi_out    Q rows of ld_out >= n floats, row q = estimate of pi for query q (dense FP32);
+ *             host or device (AGP_OUTPUT_ON_DEVICE). Every entry of each row [0, n) is written.
+ *   stats     NULL or Q entries (host memory; needs AGP_COLLECT_STATS)
+ * The call synchronises `stream` when pi_out or stats are host memory.
+ * Errors: AGP_EINVAL (parameter out of range, index out of range when inputs are on the host),
+ * AGP_ENOMEM / AGP_EBUDGET (work buffers), AGP_ECUDA, AGP_EINTERNAL (device-side check).
+ */
+AGP_API int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q,
+                    const int64_t *x_off, const int32_t *x_idx, const float *x_val,
+                    float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats,
+                    void *stream);
+
+/* One query: agp_query_batch with Q = 1. */
+AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, const int32_t *x_idx,
+              const float *x_val, float *pi_out, uint32_t flags, agp_stats_t *stats,
+              void *stream);
+
+/*
+ * Feature propagation for GNNs (Section 5.2; SGC, APPNP and GDC rows of Table 1): every column
+ * c of X is a graph signal, Z[:, c] = estimate of sum_i w_i (D^-a A D^-b)^i X[:, c]. Columns are
+ * split into sign parts and normalised as in agp_query_batch; eps applies per normalised part.
+ *   X       device, n rows x d columns of bfloat16 (raw 16-bit patterns), row stride ldx >= d
+ *   Z       device, n rows x d columns of FP32, row stride ldz >= d; fully written
+ *   seed    of params: column c part s uses the stream (seed, c, s)
+ * Errors as agp_query_batch.
+ */
+AGP_API int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, const uint16_t *X,
+                          int64_t d, int64_t ldx, float *Z, int64_t ldz, uint32_t flags,
+                          void *stream);
+
+/*
+ * Katz spectral bound (Table 1, Katz row; the experiments use beta = 0.85 / lambda_1): lambda_1
+ * of A by FP64 power iteration on the device (iterating A + I so that bipartite graphs converge),
+ * stopping when the Rayleigh quotient changes by <= tol relatively or after `iters` steps.
+ * beta = fraction / lambda_1. Synchronises `stream`. Outputs are host pointers (may be NULL).
+ */
+AGP_API int agp_katz_beta(agp_graph_t g, double fraction, int32_t iters, double tol, double *beta,
+                  double *lambda1, void *stream);
+
+/*
+ * Kernel accounting of a graph handle since the last reset.
+ *   ms[4], launches[4]  (host, may be NULL): device time in milliseconds and number of launches of
+ *                       the level-loop kernels measured under AGP_PROFILE, in the order
+ *                       0 = expand (frontier, reserve, threshold, short pushes, light sampling),
+ *                       1 = push (long deterministic prefixes), 2 = sample (heavy tails),
+ *                       3 = level end (frontier swap)
+ *   kernel_launches     (host, may be NULL): every kernel the library launched for this graph
+ *                       (graph nodes included), with or without AGP_PROFILE
+ *   reset               non-zero: clear the counters after reading
+ */
+AGP_API int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64_t *kernel_launches,
+                             int reset);
+
+/*
+ * Threshold of the deterministic prefix (Algorithm 2 push condition, Section 4 pre-sorting):
+ * for each t < count, k_out[t] = #{ j : c[t] / d_{v_j}^a >= eps } over the degree-sorted
+ * N_{nodes[t]} = {v_1, ...}, with the comparison taken in FP64 from the FP32 value c[t]
+ * (c = (Y_{i+1}/Y_i) r(u) / d_u^b as the push kernel computes it). a == 0 gives d_u or 0.
+ * Exposes the step the push kernel uses, for parity checks. nodes, c, k_out: device arrays.
+ */
+AGP_API int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes,
+                  const float *c, int32_t *k_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGP_H */

@@ -1,0 +1,303 @@
+"""GB300 library for Approximate Graph Propagation (Wang et al., KDD'21, arXiv:2106.03058).
+
+Thin Python binding of the C ABI declared in ``include/agp.h``: every function below only
+marshals arguments (pointers, sizes, flags) and calls the entry point of the same name in
+``libagp.so``; every step of the propagation runs in the library's CUDA kernels. PyTorch is used
+for device memory and streams only.
+
+If ``libagp.so`` is missing it is built from ``csrc/`` with nvcc; if that is impossible, loading
+fails with an error (there is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
+    "feature_propagate", "katz_beta", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
+    "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
+]
+
+W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
+INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE = 0x1, 0x2, 0x4, 0x8, 0x10
+KERNELS = ("expand", "push", "sample", "level_end")
+ADD_SELF_LOOPS, EDGES_ON_DEVICE = 0x1, 0x2
+MAX_LEVELS = 64
+
+
+class AgpError(RuntimeError):
+    def __init__(self, func, code, detail):
+        self.code = code
+        self.detail = detail
+        super().__init__(f"{func}: {_strerror(code)}: {detail}")
+
+
+class Params(C.Structure):
+    """``agp_params_t``: a, b, L, weight kind and parameter, eps, seed (Eq. 1, Algorithm 2)."""
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("L", C.c_int32), ("kind", C.c_int32),
+                ("param", C.c_double), ("w", C.POINTER(C.c_double)), ("eps", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    """``agp_stats_t``: per-query frontier sizes and cost counters."""
+    _fields_ = [("frontier", C.c_int64 * MAX_LEVELS), ("det_edge_ops", C.c_int64),
+                ("samples_drawn", C.c_int64), ("samples_accepted", C.c_int64),
+                ("by_kernel", (C.c_int64 * 4) * 3), ("levels", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {"frontier": list(self.frontier)[: self.levels], "det_edge_ops": self.det_edge_ops,
+                "samples_drawn": self.samples_drawn, "samples_accepted": self.samples_accepted,
+                "by_kernel": [list(r) for r in self.by_kernel]}
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i32, _i64, _u32, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+
+
+def lib():
+    """Load ``libagp.so`` (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = C.CDLL(path)
+            L.agp_strerror.restype = C.c_char_p
+            L.agp_strerror.argtypes = [C.c_int]
+            L.agp_last_error_detail.restype = C.c_char_p
+            L.agp_last_error_detail.argtypes = []
+            L.agp_version.restype = C.c_int
+            L.agp_build_graph.argtypes = [_i64, _i64, _vp, _vp, _u32, C.c_int, _vp, C.POINTER(_vp)]
+            L.agp_graph_info.argtypes = [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]
+            L.agp_graph_destroy.argtypes = [_vp]
+            L.agp_graph_set_memory_budget.argtypes = [_vp, _i64]
+            L.agp_query_batch.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp, _i64, _u32,
+                                          C.POINTER(Stats), _vp]
+            L.agp_query.argtypes = [_vp, C.POINTER(Params), _i64, _vp, _vp, _vp, _u32, C.POINTER(Stats), _vp]
+            L.agp_feature_propagate.argtypes = [_vp, C.POINTER(Params), _vp, _i64, _i64, _vp, _i64, _u32, _vp]
+            L.agp_katz_beta.argtypes = [_vp, _dbl, _i32, _dbl, C.POINTER(_dbl), C.POINTER(_dbl), _vp]
+            L.agp_threshold.argtypes = [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp]
+            L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
+            for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
+                      "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
+                      "agp_profile_read"):
+                getattr(L, f).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _strerror(code):
+    return lib().agp_strerror(code).decode()
+
+
+def _check(func, rc):
+    if rc != 0:
+        raise AgpError(func, rc, lib().agp_last_error_detail().decode())
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------- parameter presets (Table 1)
+def _params(a, b, L, kind, param=0.0, w=None, eps=0.0, seed=0):
+    p = Params(float(a), float(b), int(L), int(kind), float(param), None, float(eps), int(seed) & (2**64 - 1))
+    if w is not None:
+        arr = np.ascontiguousarray(w, np.float64)
+        p._w_keep = arr  # keep the host array alive with the struct
+        p.w = arr.ctypes.data_as(C.POINTER(C.c_double))
+    return p
+
+
+def ppr(alpha, L, eps, seed=0, a=0.0, b=1.0):
+    """Personalized PageRank w_i = alpha (1-alpha)^i (APPNP with a = b = 1/2)."""
+    return _params(a, b, L, W_PPR, alpha, eps=eps, seed=seed)
+
+
+def hkpr(t, L, eps, seed=0, a=0.0, b=1.0):
+    """Heat kernel PageRank w_i = e^-t t^i / i! (GDC with a = b = 1/2)."""
+    return _params(a, b, L, W_HKPR, t, eps=eps, seed=seed)
+
+
+def katz(beta, L, eps, seed=0):
+    """Katz w_i = beta^i, a = b = 0."""
+    return _params(0.0, 0.0, L, W_KATZ, beta, eps=eps, seed=seed)
+
+
+def transition(L, eps, seed=0, a=0.0, b=1.0):
+    """L-hop transition probability (SGC with a = b = 1/2): w_L = 1."""
+    return _params(a, b, L, W_TRANSITION, eps=eps, seed=seed)
+
+
+def finite(w, a, b, eps, seed=0):
+    """Explicit weights w_0..w_L."""
+    w = np.asarray(w, np.float64)
+    return _params(a, b, w.size - 1, W_FINITE, w=w, eps=eps, seed=seed)
+
+
+# ---------------------------------------------------------------- graph
+class Graph:
+    """Handle of a device CSR built by ``agp_build_graph``."""
+
+    def __init__(self, handle, n, nnz, device):
+        self.handle = handle
+        self.n = n
+        self.nnz = nnz
+        self.device = device
+
+    def destroy(self):
+        if self.handle:
+            lib().agp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def set_memory_budget(self, nbytes):
+        _check("agp_graph_set_memory_budget", lib().agp_graph_set_memory_budget(self.handle, int(nbytes)))
+
+    def csr(self):
+        """Copies of (rowptr int64[n+1], colidx int32[nnz], deg int32[n]) as CUDA torch tensors."""
+        import torch
+        n, nnz = _i64(), _i64()
+        rp, ci, dg = _vp(), _vp(), _vp()
+        _check("agp_graph_info", lib().agp_graph_info(self.handle, C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci), C.byref(dg)))
+
+        def view(ptr, count, typestr, dtype):
+            out = torch.empty(max(count, 0), dtype=dtype, device=f"cuda:{self.device}")
+            if count > 0:
+                src = _CudaArray(ptr.value, count, typestr)
+                out.copy_(torch.as_tensor(src, device=f"cuda:{self.device}"))
+            return out
+
+        return (view(rp, n.value + 1, "<i8", torch.int64), view(ci, nnz.value, "<i4", torch.int32),
+                view(dg, n.value, "<i4", torch.int32))
+
+
+class _CudaArray:
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def build_graph(n, src, dst, add_self_loops=False, device=0, stream=None):
+    """``agp_build_graph``: src/dst are int32 numpy arrays (host) or CUDA tensors (device)."""
+    flags = ADD_SELF_LOOPS if add_self_loops else 0
+    on_dev = not isinstance(src, np.ndarray)
+    if on_dev:
+        flags |= EDGES_ON_DEVICE
+    else:
+        src = np.ascontiguousarray(src, np.int32)
+        dst = np.ascontiguousarray(dst, np.int32)
+    h = _vp()
+    m = int(src.shape[0])
+    _check("agp_build_graph", lib().agp_build_graph(int(n), m, _ptr(src), _ptr(dst), flags, int(device),
+                                                     _stream(stream), C.byref(h)))
+    nn, nnz = _i64(), _i64()
+    _check("agp_graph_info", lib().agp_graph_info(h, C.byref(nn), C.byref(nnz), None, None, None))
+    return Graph(h, nn.value, nnz.value, device)
+
+
+# ---------------------------------------------------------------- queries
+def _params_array(params, Q):
+    if isinstance(params, Params):
+        arr = (Params * 1)(params)
+        return arr, 1, [params]
+    params = list(params)
+    if len(params) != Q:
+        raise ValueError("need one Params or Q of them")
+    arr = (Params * Q)(*params)
+    return arr, Q, params
+
+
+def query_batch(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=0, stats=None, stream=None):
+    """``agp_query_batch`` with raw arrays (numpy = host, torch CUDA = device)."""
+    Q = int(x_off.shape[0]) - 1
+    parr, np_, keep = _params_array(params, Q)
+    st = (Stats * Q)() if (flags & COLLECT_STATS) and stats is None else stats
+    ld = int(ld_out if ld_out is not None else g.n)
+    _check("agp_query_batch", lib().agp_query_batch(g.handle, parr, np_, Q, _ptr(x_off), _ptr(x_idx), _ptr(x_val),
+                                                     _ptr(out), ld, int(flags), st, _stream(stream)))
+    return st
+
+
+def profile_read(g, reset=False):
+    """``agp_profile_read``: ({kernel: ms}, {kernel: launches}, all kernel launches)."""
+    ms = (_dbl * 4)()
+    ln = (_i64 * 4)()
+    tot = _i64()
+    _check("agp_profile_read", lib().agp_profile_read(g.handle, ms, ln, C.byref(tot), int(bool(reset))))
+    return dict(zip(KERNELS, list(ms))), dict(zip(KERNELS, list(ln))), tot.value
+
+
+def query_sources(g, params, sources, out=None, plain=False, collect_stats=False, stream=None, profile=False):
+    """One query per source node (x = e_s). Inputs/outputs on the device; returns (out, stats)."""
+    import torch
+    dev = f"cuda:{g.device}"
+    src = torch.as_tensor(np.asarray(sources, np.int32), device=dev) if not torch.is_tensor(sources) else sources.to(dev, torch.int32)
+    Q = int(src.numel())
+    off = torch.arange(Q + 1, dtype=torch.int64, device=dev)
+    if out is None:
+        out = torch.empty((Q, g.n), dtype=torch.float32, device=dev)
+    flags = (INPUT_ON_DEVICE | OUTPUT_ON_DEVICE | (PLAIN if plain else 0) | (COLLECT_STATS if collect_stats else 0)
+             | (PROFILE if profile else 0))
+    st = query_batch(g, params, off, src, None, out, out.stride(0), flags, None, stream)
+    return out, st
+
+
+def feature_propagate(g, params, X, Z=None, plain=False, stream=None):
+    """``agp_feature_propagate``: X CUDA bfloat16 [n, d] (row stride X.stride(0)), Z CUDA float32 [n, d]."""
+    import torch
+    if X.dtype != torch.bfloat16 or not X.is_cuda:
+        raise TypeError("X must be a CUDA bfloat16 tensor")
+    n, d = X.shape
+    if Z is None:
+        Z = torch.empty((n, d), dtype=torch.float32, device=X.device)
+    _check("agp_feature_propagate", lib().agp_feature_propagate(g.handle, C.byref(params), X.data_ptr(), d, X.stride(0),
+                                                                 Z.data_ptr(), Z.stride(0), PLAIN if plain else 0, _stream(stream)))
+    return Z
+
+
+def katz_beta(g, fraction=0.85, iters=1000, tol=1e-12, stream=None):
+    """``agp_katz_beta``: returns (beta, lambda_1)."""
+    beta, lam = _dbl(), _dbl()
+    _check("agp_katz_beta", lib().agp_katz_beta(g.handle, float(fraction), int(iters), float(tol), C.byref(beta),
+                                                 C.byref(lam), _stream(stream)))
+    return beta.value, lam.value
+
+
+def threshold(g, a, eps, nodes, c, k_out, stream=None):
+    """``agp_threshold`` on CUDA tensors nodes (int32), c (float32), k_out (int32)."""
+    _check("agp_threshold", lib().agp_threshold(g.handle, float(a), float(eps), int(nodes.numel()), nodes.data_ptr(),
+                                                 c.data_ptr(), k_out.data_ptr(), _stream(stream)))
+    return k_out

@@ -1,0 +1,246 @@
+// api.cu -- the extern "C" entry points of include/agp.h, error reporting and the Katz bound.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "agp_internal.cuh"
+
+namespace agp {
+
+namespace {
+thread_local std::string g_detail;
+}
+
+void set_error_detail(const std::string &msg) { g_detail = msg; }
+
+int fail(int code, const std::string &msg)
+{
+    g_detail = msg;
+    return code;
+}
+
+// ---- Katz spectral bound: lambda_1(A) by FP64 power iteration on A + I --------------------------
+namespace {
+
+__global__ void k_spmv_shift(DevGraph g, const double *x, double *y)
+{
+    // one warp per row: y(u) = x(u) + sum_{v in N_u} x(v)
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < g.n; u += nw) {
+        double s = 0.0;
+        for (int64_t e = g.rowptr[u] + lane; e < g.rowptr[u + 1]; e += 32) s += x[g.colidx[e]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) y[u] = x[u] + s;
+    }
+}
+
+__global__ void k_dots(const double *x, const double *y, int64_t n, double *acc)
+{
+    __shared__ double s_yy[kBlock / 32], s_xy[kBlock / 32];
+    double yy = 0.0, xy = 0.0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        yy += y[u] * y[u];
+        xy += x[u] * y[u];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        yy += __shfl_down_sync(0xffffffffu, yy, o);
+        xy += __shfl_down_sync(0xffffffffu, xy, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_yy[threadIdx.x >> 5] = yy; s_xy[threadIdx.x >> 5] = xy; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) { a += s_yy[w]; b += s_xy[w]; }
+        atomicAdd(&acc[0], a);
+        atomicAdd(&acc[1], b);
+    }
+}
+
+__global__ void k_fill(double *x, int64_t n, double v)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) x[u] = v;
+}
+
+__global__ void k_scale(const double *y, double *x, int64_t n, const double *acc)
+{
+    const double nrm = sqrt(acc[0]);
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) x[u] = y[u] * inv;
+}
+
+}  // namespace
+
+int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *beta, double *lambda1,
+              cudaStream_t s)
+{
+    if (!g) return fail(AGP_EINVAL, "graph is NULL");
+    if (!(fraction > 0.0) || iters < 1 || !(tol >= 0.0)) return fail(AGP_EINVAL, "need fraction > 0, iters >= 1, tol >= 0");
+    AGP_CUDA_TRY(cudaSetDevice(g->device));
+    const int64_t n = g->n;
+    if (n == 0) return fail(AGP_EINVAL, "empty graph");
+    double *x = nullptr, *y = nullptr, *acc = nullptr;
+    auto cleanup = [&]() { cudaFree(x); cudaFree(y); cudaFree(acc); };
+    if (cudaMalloc(&x, sizeof(double) * n) != cudaSuccess || cudaMalloc(&y, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&acc, sizeof(double) * 2) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(AGP_ENOMEM, "katz_beta: device allocation");
+    }
+    k_fill<<<kGridStrideBlocks, kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
+    double lam = 0.0, prev = 0.0, h[2];
+    int rc = AGP_OK;
+    for (int it = 0; it < iters; ++it) {
+        k_spmv_shift<<<kGridStrideBlocks, kBlock, 0, s>>>(g->dev(), x, y);
+        cudaMemsetAsync(acc, 0, sizeof(double) * 2, s);
+        k_dots<<<kGridStrideBlocks, kBlock, 0, s>>>(x, y, n, acc);
+        k_scale<<<kGridStrideBlocks, kBlock, 0, s>>>(y, x, n, acc);
+        if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = fail(AGP_ECUDA, std::string("katz_beta: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        prev = lam;
+        lam = h[1] - 1.0;  // Rayleigh quotient of A + I at the unit iterate, minus the shift
+        if (it > 0 && std::fabs(lam - prev) <= tol * std::fabs(lam)) break;
+    }
+    cleanup();
+    if (rc != AGP_OK) return rc;
+    if (!(lam > 0.0)) return fail(AGP_EINVAL, "graph has no edges (lambda_1 = 0)");
+    if (lambda1) *lambda1 = lam;
+    if (beta) *beta = fraction / lam;
+    return AGP_OK;
+}
+
+}  // namespace agp
+
+// ------------------------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *agp_strerror(int code)
+{
+    switch (code) {
+    case AGP_OK: return "AGP_OK";
+    case AGP_EINVAL: return "AGP_EINVAL";
+    case AGP_ENOMEM: return "AGP_ENOMEM";
+    case AGP_ECUDA: return "AGP_ECUDA";
+    case AGP_EBUDGET: return "AGP_EBUDGET";
+    case AGP_EAGAIN: return "AGP_EAGAIN";
+    case AGP_ETIMEDOUT: return "AGP_ETIMEDOUT";
+    case AGP_ECANCELED: return "AGP_ECANCELED";
+    case AGP_EINTERNAL: return "AGP_EINTERNAL";
+    default: return "AGP_UNKNOWN";
+    }
+}
+
+const char *agp_last_error_detail(void) { return agp::g_detail.c_str(); }
+
+int agp_version(void) { return 10000; }
+
+int agp_build_graph(int64_t n, int64_t n_edges, const int32_t *src, const int32_t *dst, uint32_t flags,
+                    int device, void *stream, agp_graph_t *out)
+{
+    return agp::build_graph(n, n_edges, src, dst, flags, device, (cudaStream_t)stream, out);
+}
+
+int agp_graph_info(agp_graph_t g, int64_t *n, int64_t *nnz, const int64_t **rowptr, const int32_t **colidx,
+                   const int32_t **deg)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (rowptr) *rowptr = g->rowptr;
+    if (colidx) *colidx = g->colidx;
+    if (deg) *deg = g->deg;
+    return AGP_OK;
+}
+
+int agp_graph_destroy(agp_graph_t g)
+{
+    if (!g) return AGP_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    agp::free_workspace(g->ws);
+    cudaFree(g->rowptr);
+    cudaFree(g->colidx);
+    cudaFree(g->deg);
+    cudaFree(g->in_stage);
+    delete g;
+    return AGP_OK;
+}
+
+int agp_graph_set_memory_budget(agp_graph_t g, int64_t bytes)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (bytes < 0) return agp::fail(AGP_EINVAL, "budget < 0");
+    g->mem_budget = bytes;
+    return AGP_OK;
+}
+
+int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
+                    const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
+                    agp_stats_t *stats, void *stream)
+{
+    return agp::query_batch(g, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, stats,
+                            (cudaStream_t)stream);
+}
+
+int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, const int32_t *x_idx, const float *x_val,
+              float *pi_out, uint32_t flags, agp_stats_t *stats, void *stream)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (x_nnz < 0) return agp::fail(AGP_EINVAL, "x_nnz < 0");
+    if (flags & AGP_INPUT_ON_DEVICE) {
+        // offsets must live where the signal lives: stage them through the graph's input buffer
+        int64_t *d_off = nullptr;
+        if (cudaMalloc(&d_off, 2 * sizeof(int64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return agp::fail(AGP_ENOMEM, "agp_query: offsets");
+        }
+        const int64_t h_off[2] = {0, x_nnz};
+        cudaMemcpy(d_off, h_off, sizeof(h_off), cudaMemcpyHostToDevice);
+        const int rc = agp::query_batch(g, params, 1, 1, d_off, x_idx, x_val, pi_out, g->n, flags, stats,
+                                        (cudaStream_t)stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(d_off);
+        return rc;
+    }
+    const int64_t h_off[2] = {0, x_nnz};
+    return agp::query_batch(g, params, 1, 1, h_off, x_idx, x_val, pi_out, g->n, flags, stats, (cudaStream_t)stream);
+}
+
+int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, const uint16_t *X, int64_t d, int64_t ldx,
+                          float *Z, int64_t ldz, uint32_t flags, void *stream)
+{
+    return agp::feature_propagate(g, params, X, d, ldx, Z, ldz, flags, (cudaStream_t)stream);
+}
+
+int agp_katz_beta(agp_graph_t g, double fraction, int32_t iters, double tol, double *beta, double *lambda1,
+                  void *stream)
+{
+    return agp::katz_beta(g, fraction, iters, tol, beta, lambda1, (cudaStream_t)stream);
+}
+
+int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64_t *kernel_launches, int reset)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = g->prof_ms[k];
+        if (launches) launches[k] = g->prof_launches[k];
+    }
+    if (kernel_launches) *kernel_launches = g->kernel_launches;
+    if (reset) {
+        for (int k = 0; k < 4; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
+        g->kernel_launches = 0;
+    }
+    return AGP_OK;
+}
+
+int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes, const float *c,
+                  int32_t *k_out, void *stream)
+{
+    return agp::threshold(g, a, eps, count, nodes, c, k_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,365 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: integer and index results (CSR, frontier sets, thresholds) bit-exact; eps = 0 results
+within relative 1e-5 per entry (FP32 residues against FP64); eps > 0 results are random, so they
+are checked the way the paper characterises them: unbiased over 200 seeds (Lemma 4.1), variance
+within Lemma 4.2, and the relative-error guarantee of Definition 1.1 at the Chebyshev threshold
+delta = 5000 L(L+1) eps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import graphs as SG
+from tests import _graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def agp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_03058_gb300 as agp
+    agp.lib()
+    return agp
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    """Workload of the small configuration: R-MAT 2^14 nodes, 131072 edges."""
+    u, v = SG.rmat_edges(16384, 131072, seed=20210604)
+    return 16384, u, v
+
+
+def _assert_rel(got, want, rel=REL, scale=None):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    ref = np.abs(want) if scale is None else scale
+    err = np.abs(got - want)
+    bad = err > rel * ref + 1e-30
+    assert not bad.any(), f"{bad.sum()} entries off, worst rel {np.max(err / np.maximum(ref, 1e-300)):.3e}"
+
+
+def _csr_equal(agp, n, u, v, loops):
+    g = agp.build_graph(n, u, v, add_self_loops=loops)
+    o = oracle.build_csr(n, u, v, add_self_loops=loops)
+    rp, ci, dg = (t.cpu().numpy() for t in g.csr())
+    np.testing.assert_array_equal(rp, o.rowptr)
+    np.testing.assert_array_equal(ci, o.colidx)
+    np.testing.assert_array_equal(dg, o.deg)
+    return g, o
+
+
+# ---------------------------------------------------------------- a0: CSR builder
+@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("loops", [False, True])
+def test_csr_bit_exact_small(agp, seed, loops):
+    n, src, dst = G.random_multigraph(300, 2000, seed)
+    _csr_equal(agp, n, src, dst, loops)
+
+
+def test_csr_bit_exact_rmat(agp, rmat14):
+    _csr_equal(agp, *rmat14, False)
+
+
+def test_csr_edge_cases(agp):
+    g = agp.build_graph(7, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    rp, ci, dg = (t.cpu().numpy() for t in g.csr())
+    assert rp.tolist() == [0] * 8 and ci.size == 0 and dg.tolist() == [0] * 7
+    _csr_equal(agp, 5, np.array([2, 2], np.int32), np.array([2, 2], np.int32), False)   # loops only
+    _csr_equal(agp, 1, np.zeros(0, np.int32), np.zeros(0, np.int32), True)              # one node
+    with pytest.raises(agp.AgpError) as e:
+        agp.build_graph(4, np.array([0], np.int32), np.array([4], np.int32))
+    assert e.value.code == 1
+
+
+# ---------------------------------------------------------------- eps = 0 exactness
+def _oracle_params(kind, L, param, w=None):
+    return oracle.tail_sums(kind, L, param, w)
+
+
+PRESETS = [
+    # name, a, b, kind, L, param
+    ("ppr", 0.0, 1.0, oracle.PPR, 20, 0.2),
+    ("hkpr", 0.0, 1.0, oracle.HKPR, 30, 5.0),
+    ("transition", 0.0, 1.0, oracle.TRANSITION, 4, 0.0),
+    ("appnp", 0.5, 0.5, oracle.PPR, 10, 0.1),
+    ("sgc", 0.5, 0.5, oracle.TRANSITION, 4, 0.0),
+    ("single_target", 1.0, 0.0, oracle.PPR, 12, 0.2),
+    ("general_ab", 0.3, 0.7, oracle.HKPR, 8, 2.0),
+]
+
+
+def _agp_params(agp, a, b, kind, L, param, eps, seed=0, w=None):
+    return agp._params(a, b, L, kind, param, w=w, eps=eps, seed=seed)
+
+
+@pytest.mark.parametrize("preset", PRESETS, ids=[p[0] for p in PRESETS])
+def test_eps0_matches_oracle(agp, rmat14, preset):
+    name, a, b, kind, L, param = preset
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    rng = np.random.default_rng(7)
+    srcs = rng.choice(np.flatnonzero(og.deg > 0), 6, replace=False)
+    out, _ = agp.query_sources(g, _agp_params(agp, a, b, kind, L, param, 0.0), srcs)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    w, Y = oracle.tail_sums(kind, L, param)
+    for q, s in enumerate(srcs):
+        x = np.zeros(n); x[s] = 1.0
+        _assert_rel(got[q], oracle.basic(og, a, b, L, w, Y, x))
+
+
+def test_eps0_katz_and_lambda(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    beta_g, lam_g = agp.katz_beta(g, 0.85, iters=5000, tol=1e-13)
+    lam_o = oracle.power_lambda(og, iters=5000, tol=1e-13)
+    assert abs(lam_g - lam_o) <= 1e-9 * lam_o
+    beta = 0.85 / lam_o
+    srcs = np.argsort(-og.deg)[:3]
+    out, _ = agp.query_sources(g, agp.katz(beta, 20, 0.0), srcs)
+    w, Y = oracle.tail_sums(oracle.KATZ, 20, beta)
+    got = out.cpu().numpy()
+    for q, s in enumerate(srcs):
+        x = np.zeros(n); x[s] = 1.0
+        _assert_rel(got[q], oracle.basic(og, 0, 0, 20, w, Y, x))
+
+
+def test_eps0_signed_sparse_signal_and_finite_weights(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    rng = np.random.default_rng(3)
+    Q = 5
+    sizes = [1, 7, 0, 40, 3]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    idx = rng.integers(0, n, off[-1]).astype(np.int32)
+    idx[9] = idx[8]  # a repeated index adds up
+    val = rng.standard_normal(off[-1]).astype(np.float32)
+    wts = np.array([0.1, 0.0, 0.5, 0.3, 0.25])
+    p = agp.finite(wts, 0.5, 0.5, 0.0)
+    out = np.zeros((Q, n), np.float32)
+    agp.query_batch(g, p, off, idx, val, out)
+    wl, Y = oracle.tail_sums(oracle.FINITE, 4, w=wts)
+    for q in range(Q):
+        x = np.zeros(n)
+        np.add.at(x, idx[off[q]:off[q + 1]], val[off[q]:off[q + 1]].astype(np.float64))
+        xp, xm = np.maximum(x, 0), np.maximum(-x, 0)
+        pp = oracle.basic(og, 0.5, 0.5, 4, wl, Y, xp) if xp.any() else np.zeros(n)
+        pm = oracle.basic(og, 0.5, 0.5, 4, wl, Y, xm) if xm.any() else np.zeros(n)
+        _assert_rel(out[q], pp - pm, scale=np.abs(pp) + np.abs(pm))
+
+
+def test_frontier_sets_bit_exact(agp, rmat14):
+    """eps = 0: the support of r^(i) is {v : (A D^-1)^i e_s (v) != 0}; the L-hop transition
+    output is exactly r^(L), so its support is the level-L frontier."""
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    s = int(np.argsort(og.deg)[-50])
+    for L in (1, 2, 3):
+        out, st = agp.query_sources(g, agp.transition(L, 0.0), [s], collect_stats=True)
+        w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+        x = np.zeros(n); x[s] = 1.0
+        ref, fronts = oracle.basic(og, 0, 1, L, w, Y, x, frontier_sizes=True)
+        np.testing.assert_array_equal(np.flatnonzero(out[0].cpu().numpy()), np.flatnonzero(ref))
+        assert list(st[0].frontier)[: L + 1] == fronts[0].tolist()
+
+
+# ---------------------------------------------------------------- a5: threshold
+@pytest.mark.parametrize("a", [0.0, 0.5, 1.0])
+def test_threshold_bit_exact(agp, rmat14, a):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    rng = np.random.default_rng(11)
+    eps = 1e-4
+    nodes = rng.choice(np.flatnonzero(og.deg > 0), 3000).astype(np.int32)
+    # c spread around the boundaries eps * d^a of each row, including exact boundary values
+    dv = og.deg[og.colidx[og.rowptr[nodes] + rng.integers(0, og.deg[nodes])]].astype(np.float64)
+    c = (eps * dv ** a * np.exp(rng.uniform(-0.3, 0.3, nodes.size))).astype(np.float32)
+    c[::7] = np.float32(eps * dv[::7] ** a)
+    k = torch.zeros(nodes.size, dtype=torch.int32, device="cuda")
+    agp.threshold(g, a, eps, torch.as_tensor(nodes, device="cuda"), torch.as_tensor(c, device="cuda"), k)
+    got = k.cpu().numpy()
+    want = np.empty_like(got)
+    for t, s in enumerate(nodes):
+        row = og.colidx[og.rowptr[s]:og.rowptr[s + 1]]
+        d = og.deg[row].astype(np.float64)
+        cd = np.float64(c[t])
+        if a == 0.0:
+            ok = np.full(d.size, cd >= eps)
+        elif a == 1.0:
+            ok = cd / d >= eps
+        else:
+            ok = cd / np.sqrt(d) >= eps
+        assert np.all(ok[:-1] >= ok[1:])  # a prefix of the degree-sorted row
+        want[t] = ok.sum()
+    np.testing.assert_array_equal(got, want)
+
+
+# ---------------------------------------------------------------- eps > 0: statistics
+STAT_CASES = [
+    # a, b, kind, L, param, eps
+    (0.0, 1.0, oracle.PPR, 10, 0.2, 2e-6),
+    (0.5, 0.5, oracle.PPR, 10, 0.1, 1e-6),
+    (0.0, 0.0, oracle.KATZ, 8, None, 1e-6),
+]
+
+
+@pytest.mark.parametrize("case", STAT_CASES, ids=["ppr", "appnp", "katz"])
+def test_unbiased_variance_guarantee(agp, rmat14, case):
+    a, b, kind, L, param, eps = case
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    if kind == oracle.KATZ:
+        param = 0.85 / oracle.power_lambda(og)
+    s = int(np.argsort(og.deg)[-200])
+    N = 200
+    params = [_agp_params(agp, a, b, kind, L, param, eps, seed=1000 + k) for k in range(N)]
+    out, _ = agp.query_sources(g, params, np.full(N, s))
+    runs = out.cpu().numpy().astype(np.float64)
+    w, Y = oracle.tail_sums(kind, L, param)
+    x = np.zeros(n); x[s] = 1.0
+    exact = oracle.basic(og, a, b, L, w, Y, x)
+    mean, var = runs.mean(0), runs.var(0, ddof=1)
+    sd = np.sqrt(var / N)
+    live = sd > 0
+    z = (mean[live] - exact[live]) / sd[live]
+    assert np.mean(np.abs(z) > 2.576) <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / max(live.sum(), 1)) + 1e-9
+    assert np.abs(z).max() < 6.0
+    # Lemma 4.2 (normalised problem: ||x||_1 = 1, pi / Y_0), sampling noise allowance 35%
+    y0 = Y[0]
+    bound = L * (L + 1) * eps * (exact / y0) / 2 * y0 * y0
+    assert np.all(var <= 1.35 * bound + 1e-24)
+    # Definition 1.1 at delta = 5000 L(L+1) eps (Chebyshev on Lemma 4.2, <= 1% failures)
+    delta = 5000 * L * (L + 1) * eps * y0
+    big = exact >= delta
+    if big.any():
+        fails = np.mean(np.abs(runs[:, big] - exact[big]) > 0.1 * exact[big], axis=0)
+        assert np.all(fails <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / N))
+
+
+def test_sampler_star_binomial(agp):
+    """Star K_{1,N}, a = 0, one level: the number of sampled leaves is Binomial(N, p)."""
+    from scipy import stats
+    leaves = 500
+    n, src, dst = G.star(leaves)
+    g = agp.build_graph(n, src, dst)
+    p = 0.05
+    eps = (1.0 / leaves) / p
+    N = 2000
+    params = [agp.transition(1, eps, seed=k) for k in range(N)]
+    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32))
+    k = out[:, 1:].cpu().numpy() / np.float32(eps)
+    assert np.allclose(k, np.round(k))
+    counts = np.round(k).sum(1).astype(int)
+    pmf = stats.binom.pmf(np.arange(leaves + 1), leaves, p)
+    exp = pmf * N
+    keep = exp >= 5
+    obs = np.bincount(counts, minlength=leaves + 1)
+    o = np.concatenate([obs[keep], [obs[~keep].sum()]])
+    e = np.concatenate([exp[keep], [exp[~keep].sum()]])
+    chi2 = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi2, o.size - 1) > 1e-3
+
+
+@pytest.mark.parametrize("a", [0.5, 1.0])
+def test_sampler_inclusion_across_degree_groups(agp, a):
+    degrees = [1, 2, 3, 5, 8, 9, 15, 17, 30, 33, 60, 64, 100, 129, 250]
+    n, src, dst = G.graded_fan(degrees)
+    g = agp.build_graph(n, src, dst)
+    og = oracle.build_csr(n, src, dst)
+    eps = 1.0 / 3.0 ** a
+    hubs = np.arange(1, len(degrees) + 1)
+    inc = 1.0 / og.deg[hubs].astype(float) ** a
+    p = np.minimum(1.0, inc / eps)
+    N = 4000
+    params = [agp._params(a, 0.0, 1, agp.W_TRANSITION, eps=eps, seed=k) for k in range(N)]
+    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32))
+    hit = (out[:, hubs].cpu().numpy() > 0).mean(0)
+    samp = p < 1
+    z = (hit[samp] - p[samp]) / np.sqrt(p[samp] * (1 - p[samp]) / N)
+    assert np.abs(z).max() < 4.0 and np.all(hit[~samp] == 1.0)
+
+
+# ---------------------------------------------------------------- batching equivalence
+def test_alone_equals_batched_and_plain(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    rng = np.random.default_rng(5)
+    srcs = rng.choice(np.flatnonzero(og.deg > 0), 40, replace=False)
+    params = [agp.ppr(0.2, 20, 1e-7, seed=int(s)) for s in srcs]
+    batched, _ = agp.query_sources(g, params, srcs)
+    plain, _ = agp.query_sources(g, params, srcs, plain=True)
+    alone = torch.stack([agp.query_sources(g, params[i], srcs[i:i + 1])[0][0] for i in (0, 17, 39)])
+    b = batched.cpu().numpy()
+    scale = np.abs(b).max(1, keepdims=True)
+    assert np.all(np.abs(plain.cpu().numpy() - b) <= 1e-5 * scale)
+    for k, i in enumerate((0, 17, 39)):
+        assert np.abs(alone[k].cpu().numpy() - b[i]).max() <= 1e-5 * scale[i, 0]
+
+
+# ---------------------------------------------------------------- features
+def test_feature_propagation_eps0(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v, add_self_loops=True)
+    og = oracle.build_csr(n, u, v, add_self_loops=True)
+    d = 12
+    X = torch.randn(n, d, generator=torch.Generator().manual_seed(0)).to(torch.bfloat16)
+    Xd = X.cuda()
+    for kind, L, param in ((oracle.PPR, 10, 0.1), (oracle.TRANSITION, 4, 0.0)):
+        p = agp._params(0.5, 0.5, L, kind, param, eps=0.0)
+        Z = agp.feature_propagate(g, p, Xd).cpu().numpy()
+        w, Y = oracle.tail_sums(kind, L, param)
+        Xf = X.float().numpy().astype(np.float64)
+        for c in range(d):
+            xp, xm = np.maximum(Xf[:, c], 0), np.maximum(-Xf[:, c], 0)
+            pp = oracle.basic(og, 0.5, 0.5, L, w, Y, xp)
+            pm = oracle.basic(og, 0.5, 0.5, L, w, Y, xm)
+            _assert_rel(Z[:, c], pp - pm, scale=np.abs(pp) + np.abs(pm))
+
+
+def test_feature_propagation_unbiased(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v, add_self_loops=True)
+    og = oracle.build_csr(n, u, v, add_self_loops=True)
+    X = torch.randn(n, 1, generator=torch.Generator().manual_seed(1)).to(torch.bfloat16)
+    Xr = X.repeat(1, 64).contiguous()  # 64 copies of one column: independent streams per column
+    p = agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=1e-6, seed=9)
+    Z = agp.feature_propagate(g, p, Xr.cuda()).cpu().numpy().astype(np.float64)
+    w, Y = oracle.tail_sums(oracle.TRANSITION, 4)
+    xf = X.float().numpy()[:, 0].astype(np.float64)
+    exact = oracle.basic(og, 0.5, 0.5, 4, w, Y, xf)
+    assert not np.allclose(Z[:, 0], Z[:, 1])  # columns use different random streams
+    mean, sd = Z.mean(1), Z.std(1, ddof=1) / np.sqrt(64)
+    live = sd > 0
+    z = (mean[live] - exact[live]) / sd[live]
+    assert np.mean(np.abs(z) > 2.576) <= 0.02
+
+
+# ---------------------------------------------------------------- error paths
+def test_errors(agp, rmat14):
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    with pytest.raises(agp.AgpError) as e:
+        agp.query_sources(g, agp.ppr(0.2, 99, 1e-6), [0])
+    assert e.value.code == 1
+    with pytest.raises(agp.AgpError):
+        agp.query_sources(g, agp._params(1.5, 0, 3, agp.W_PPR, 0.2, eps=0.0), [0])
+    with pytest.raises(agp.AgpError):
+        agp.query_sources(g, agp.ppr(0.2, 5, 1e-6), [n])  # index out of range
+    with pytest.raises(agp.AgpError):
+        agp.query_sources(g, agp.katz(1.5, 5, 1e-6), [0])
+    # the handle is still usable afterwards
+    out, _ = agp.query_sources(g, agp.ppr(0.2, 3, 0.0), [int(np.argmax(np.bincount(u)))])
+    assert torch.isfinite(out).all()
