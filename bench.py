@@ -35,13 +35,14 @@ from synth import graphs as SG  # noqa: E402
 S = 20210603
 HBM_FALLBACK_GBS = 6800.0
 
-# Algorithmic bytes per unit of work (roofline numerator), per kernel:
-#   frontier item (expand): item id 4 + r read 4 + r clear 4 + reserve RMW 8 + degree 4 + row start 8
+# Algorithmic bytes per unit of work (roofline numerator), per level-loop step:
+#   compaction:             two reads of every active lane's residue vector (4 B per node each) +
+#                           per frontier item: item id 4 + r value 4 + clearing 4
+#   frontier item (expand): item id 4 + r value 4 + reserve RMW 8 + degree 4 + row start 8
 #   deterministic push:     colidx 4 + residue atomic RMW 8 (+ neighbour degree 4 when a > 0)
 #   sampler trial:          colidx 4 (+ neighbour degree 4 when a > 0)
 #   accepted sample:        residue atomic RMW 8
-#   frontier append:        item id write 4
-B_ITEM, B_DET, B_TRIAL, B_ACC, B_APPEND, B_DEG = 32, 12, 4, 8, 4, 4
+B_ITEM, B_DET, B_TRIAL, B_ACC, B_DEG, B_COMPACT_ITEM, B_SCAN = 28, 12, 4, 8, 4, 12, 8
 
 
 def log(*a):
@@ -191,6 +192,136 @@ def run_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------- multi-rank
+def rank_reduce(x: float, op: str, world: int, device: str = "cpu") -> float:
+    """max / sum of a scalar over all ranks (identity for a single process)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(local_ms: float, local_units: float, world: int, device: str = "cpu"):
+    """Whole-job rate: units summed over ranks / the slowest rank's time. Returns (ms, units, rate)."""
+    ms = rank_reduce(local_ms, "max", world, device)
+    units = rank_reduce(local_units, "sum", world, device)
+    return ms, units, units / (ms / 1e3)
+
+
+def end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev):
+    """The same steps through host buffers: H2D of the sources and D2H of all results timed."""
+    import torch
+    h_srcs = srcs.copy()
+    h_off = np.arange(Q + 1, dtype=np.int64)
+    h_out_k = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
+    h_out_t = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
+    e2e_times = []
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        pk, pt = all_params[args.warmup + k]
+        base = (args.warmup + k) * 2 * Q
+        t0 = time.perf_counter()
+        agp.query_batch(g, pk, h_off, h_srcs[base:base + Q], None, h_out_k, n, 0)
+        agp.query_batch(g, pt, h_off, h_srcs[base + Q:base + 2 * Q], None, h_out_t, n, 0)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    _, _, e2e_value = job_throughput(1e3 * sum(e2e_times), 2 * Q * args.steps, world, dev)
+    h2d = 2 * (h_off.nbytes + Q * 4)
+    d2h = 2 * Q * n * 4
+
+    return e2e_value, h2d, d2h
+
+
+# ------------------------------------------------------------------------------- serving
+def serve_trace(n, u, v, rate, duration, seed, beta):
+    """Seeded Poisson trace of the serving mix: PPR / Katz / HKPR / transition (22.5% each) and
+    BF16 feature blocks of 1-64 columns (10%, log-uniform); eps in {1e-6, 1e-7, 1e-8, 1e-9};
+    L uniform in 5..40; sources uniform (50%) or degree-weighted (50%)."""
+    rng = np.random.default_rng(seed)
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    live = np.flatnonzero(deg > 0)
+    p_deg = deg / deg.sum()
+    t, trace = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        r = rng.random()
+        kind = "features" if r < 0.10 else ("ppr", "katz", "hkpr", "transition")[min(3, int((r - 0.10) / 0.225))]
+        eps = float(rng.choice([1e-6, 1e-7, 1e-8, 1e-9]))
+        L = int(rng.integers(5, 41))
+        src = int(rng.choice(live)) if rng.random() < 0.5 else int(rng.choice(n, p=p_deg))
+        cols = int(np.clip(np.round(np.exp(rng.uniform(0, np.log(64)))), 1, 64))
+        trace.append((t, kind, eps, L, src, cols, int(rng.integers(0, 2**62))))
+    return trace
+
+
+def run_serve(args, wl):
+    import torch
+    import paper_2106_03058_gb300 as agp
+    u, v = make_edges(wl)
+    n = wl["n"]
+    g = agp.build_graph(n, u, v)
+    beta, lam = agp.katz_beta(g, 0.85, iters=1000, tol=1e-12)
+    trace = serve_trace(n, u, v, args.rate, args.duration, S + 500, beta)
+    X = torch.randn(n, 64, generator=torch.Generator().manual_seed(S + 200)).to(torch.bfloat16).cuda()
+
+    def params_of(kind, eps, L, seed):
+        if kind == "ppr":
+            return agp.ppr(0.2, L, eps, seed=seed)
+        if kind == "katz":
+            return agp.katz(beta, L, eps, seed=seed)
+        if kind == "hkpr":
+            return agp.hkpr(5.0, L, eps, seed=seed)
+        if kind == "transition":
+            return agp.transition(L, eps, seed=seed)
+        return agp._params(0.5, 0.5, L, agp.W_PPR, 0.1, eps=eps, seed=seed)
+
+    def replay(mode):
+        srv = agp.Server(g, mode=mode, max_lanes=args.lanes if args.lanes > 0 else 0)
+        tickets = []
+        t0 = time.perf_counter()
+        for (ta, kind, eps, L, src, cols, seed) in trace:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            p = params_of(kind, eps, L, seed)
+            tk = srv.submit(p, X=X[:, :cols]) if kind == "features" else srv.submit(p, source=src)
+            tickets.append((tk, kind))
+        submitted_by = time.perf_counter() - t0
+        deadline = t0 + args.duration + args.drain
+        lat, done = [], 0
+        for tk, kind in tickets:
+            left = max(0.0, deadline - time.perf_counter())
+            r = srv.wait(tk, timeout_us=int(left * 1e6))
+            if r is None:
+                continue
+            if r.status == 0:
+                done += 1
+                lat.append(r.latency_us / 1e3)
+            srv.release(tk)
+        elapsed = min(time.perf_counter(), deadline) - t0
+        st = srv.stats()
+        srv.destroy()
+        lat = np.array(lat) if lat else np.array([np.nan])
+        return {"offered": len(trace), "completed": done, "queries_per_s": done / elapsed,
+                "p50_ms": float(np.nanpercentile(lat, 50)), "p99_ms": float(np.nanpercentile(lat, 99)),
+                "elapsed_s": elapsed, "submit_s": submitted_by, "sweeps": st["sweeps"]}
+
+    batched = replay(agp.SERVE_BATCHED)
+    fifo = replay(agp.SERVE_FIFO_PLAIN) if not args.no_fifo else None
+    line = {"metric": "served queries/s (continuous batching)", "value": batched["queries_per_s"], "unit": "queries/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"] + " | serving trace", "rate": args.rate, "duration_s": args.duration,
+                       "drain_s": args.drain, "lambda_1": lam},
+            "batched": batched, "fifo_plain": fifo}
+    print(json.dumps(line), flush=True)
+    g.destroy()
+
+
 # ------------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -201,13 +332,25 @@ def main():
     ap.add_argument("--small", action="store_true", help="small R-MAT workload (quick check)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-queries", type=int, default=16)
+    ap.add_argument("--queries", type=int, default=0, help="sources per launch (default: the workload's 256)")
+    ap.add_argument("--lanes", type=int, default=0, help="wave width; 0 = autotune")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving trace instead of the batched step")
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--drain", type=float, default=20.0)
+    ap.add_argument("--no-fifo", action="store_true")
     args = ap.parse_args()
     wl = workload(args.small)
+    if args.queries:
+        wl["Q"] = args.queries
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, wl, rank)
+    if args.serve:
+        return run_serve(args, wl)
 
     import torch
     import torch.distributed as dist
@@ -223,13 +366,6 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     t0 = time.perf_counter()
     u, v = make_edges(wl)
@@ -268,6 +404,20 @@ def main():
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
+    # wave width: given, or tuned on a sample of the first step's Katz launch (cached)
+    tuned_ms = None
+    if args.lanes > 0:
+        g.set_wave_lanes(args.lanes)
+        lanes = args.lanes
+    else:
+        qs = min(Q, 32)
+        pk, _ = all_params[0]
+        t0 = time.perf_counter()
+        lanes, tuned_ms = agp.autotune(g, pk[:qs], off[:qs + 1], d_srcs[:qs], None, out_k, n,
+                                       candidates=[c for c in (1, 2, 4, 8, 16, 32) if c <= 2 * qs])
+        log(f"[bench] autotuned wave width {lanes} lanes ({tuned_ms:.1f} ms for {qs} Katz queries, "
+            f"{time.perf_counter() - t0:.1f}s)")
+
     for k in range(args.warmup):
         run_step(k)
     barrier_sync()
@@ -288,9 +438,7 @@ def main():
         barrier_sync()
     clk = clocks.summary()
     kern_ms, kern_launches, total_launches = agp.profile_read(g, reset=True)
-    total_ms = max_over_ranks(sum(step_ms))
-    queries = 2 * Q * args.steps * world
-    value = queries / (total_ms / 1e3)
+    total_ms, queries, value = job_throughput(sum(step_ms), 2 * Q * args.steps, world, dev)
 
     # per-kernel work of the timed steps (same sources and seeds, counted in a separate pass)
     work = np.zeros((3, 4))
@@ -301,12 +449,14 @@ def main():
             work += np.array([list(r) for r in s_.by_kernel], dtype=np.float64)
             items += sum(s_.frontier[: s_.levels])
     # a = 0 for both query types: no neighbour-degree gathers
+    scanned = args.steps * Q * n * ((wl["L_katz"] + 1) + (4 + 1))  # lane-levels x nodes
     bytes_k = {
-        "expand": items * B_ITEM + work[0, 0] * B_DET + work[0, 1] * B_TRIAL + work[0, 2] * B_ACC + work[0, 3] * B_APPEND,
-        "push": work[1, 0] * B_DET + work[1, 3] * B_APPEND,
-        "sample": work[2, 1] * B_TRIAL + work[2, 2] * B_ACC + work[2, 3] * B_APPEND,
+        "compact": items * B_COMPACT_ITEM + scanned * B_SCAN,
+        "expand": items * B_ITEM + work[0, 0] * B_DET + work[0, 1] * B_TRIAL + work[0, 2] * B_ACC,
+        "push": work[1, 0] * B_DET,
+        "sample": work[2, 1] * B_TRIAL + work[2, 2] * B_ACC,
     }
-    dom = max(("expand", "push", "sample"), key=lambda k_: kern_ms[k_])
+    dom = max(("compact", "expand", "push", "sample"), key=lambda k_: kern_ms[k_])
     launches = max(kern_launches[dom], 1)
     avg_ms = kern_ms[dom] / launches
     achieved = (bytes_k[dom] / launches) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
@@ -342,25 +492,11 @@ def main():
                      "queries": 2 * half}
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
-    h_srcs = srcs.copy()
-    h_off = np.arange(Q + 1, dtype=np.int64)
-    h_out_k = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
-    h_out_t = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
-    e2e_times = []
-    barrier_sync()
-    for k in range(args.steps):
-        pk, pt = all_params[args.warmup + k]
-        base = (args.warmup + k) * 2 * Q
-        t0 = time.perf_counter()
-        agp.query_batch(g, pk, h_off, h_srcs[base:base + Q], None, h_out_k, n, 0)
-        agp.query_batch(g, pt, h_off, h_srcs[base + Q:base + 2 * Q], None, h_out_t, n, 0)
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_total = max_over_ranks(sum(e2e_times))
-    e2e_value = queries / e2e_total
-    h2d = 2 * (h_off.nbytes + Q * 4)
-    d2h = 2 * Q * n * 4
+    e2e_value, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        e2e_value, h2d, d2h = end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev)
 
+    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -378,11 +514,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "parallelism": f"replicas{world}", "queries_per_step": 2 * Q,
+                       "wave_lanes": lanes, "autotune_ms": tuned_ms,
                        "lambda_1": lam, "beta": beta,
                        "l2": "flushed before every timed step (256 MB write); CSR 0.96 GB and 8 GB of residues exceed L2"},
             "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)), "p99_step": float(np.percentile(step_ms, 99)),
                            "note": "a query's latency is its launch's completion time"},
-            "edges_pushed_per_s": edge_ops * world / (total_ms / 1e3),
+            "edges_pushed_per_s": rank_reduce(edge_ops, "sum", world, dev) / (total_ms / 1e3),
             "plain_path": plain_qps,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
@@ -391,7 +528,8 @@ def main():
             "gpu_launches": int(total_launches),
             "clocks": clk,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": None if e2e_value is None else {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                                                   "d2h_bytes_per_step": d2h},
         }
         print(json.dumps(line), flush=True)
     g.destroy()

@@ -96,6 +96,10 @@ AGP_API int agp_graph_destroy(agp_graph_t g);
  * device memory at the first query). Work buffers are sized from it and reused across calls. */
 AGP_API int agp_graph_set_memory_budget(agp_graph_t g, int64_t bytes);
 
+/* Lanes (sign parts of queries or feature columns) propagated together in one wave; 0 = automatic:
+ * as many as keep their residue vectors within ~96 MB of L2. agp_autotune picks it by timing. */
+AGP_API int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes);
+
 /* ---- propagation parameters ---------------------------------------------------------------- */
 /* Weight sequences of Table 1. FINITE takes w_0..w_L from `w`; the others are generated with
  * their infinite tails Y_i = sum_{k>=i} w_k (Def. 3.1):
@@ -195,13 +199,92 @@ AGP_API int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, con
 AGP_API int agp_katz_beta(agp_graph_t g, double fraction, int32_t iters, double tol, double *beta,
                   double *lambda1, void *stream);
 
+/* ---- serving ----------------------------------------------------------------------------------- */
+/*
+ * Continuous-batching server over a resident graph. Requests (single-source proximity queries or
+ * BF16 feature blocks) are admitted into lanes ("slots") as lanes and result memory free up; every
+ * sweep advances every admitted lane by one level of Algorithm 2 in shared launches, so requests
+ * that arrive while others run join the next sweep. Each lane keeps its own level, coefficients and
+ * random stream, so a request's result does not depend on what it shares sweeps with (up to FP32
+ * atomic summation order). A host thread owned by the server drives the device on its own stream.
+ */
+typedef struct agp_server_s *agp_server_t;
+
+#define AGP_SERVE_BATCHED 0     /* continuous batching (default)                                     */
+#define AGP_SERVE_FIFO_PLAIN 1  /* baseline: one request at a time on the plain path, arrival order  */
+
+typedef struct {
+    int32_t mode;             /* AGP_SERVE_*                                                        */
+    int32_t max_lanes;        /* slots (lanes) in flight; 0 = the graph's automatic wave width x 8  */
+    int64_t result_budget;    /* bytes of result buffers of admitted, unreleased requests; 0 = 4 GiB */
+    int32_t results_on_host;  /* 1: results are copied to library-owned pinned host memory          */
+    int32_t reserved;
+} agp_serve_config_t;
+
+#define AGP_REQ_X_ON_DEVICE 0x1u /* X is a device pointer that stays valid until the request is done */
+
+typedef struct {
+    agp_params_t params;      /* a, b, L, weights, eps, seed                                         */
+    int32_t source;           /* >= 0: x = e_source; -1: feature request                            */
+    int32_t cols;             /* feature request: number of columns (1..1024)                        */
+    const uint16_t *X;        /* feature request: BF16 matrix n x cols, row stride ldx; host memory
+                                 is copied by agp_serve_submit, device memory (AGP_REQ_X_ON_DEVICE)
+                                 is read in place                                                    */
+    int64_t ldx;
+    int64_t deadline_us;      /* > 0: a request not admitted within this many microseconds of its
+                                 submission finishes with AGP_ETIMEDOUT                              */
+    uint32_t flags;           /* AGP_REQ_*                                                           */
+    int32_t reserved;
+} agp_request_t;
+
+typedef struct {
+    int32_t status;           /* AGP_OK, AGP_ETIMEDOUT, AGP_ECANCELED or an error code               */
+    int32_t on_host;          /* 1: `pi` is host memory, 0: device memory                           */
+    const float *pi;          /* library-owned: n floats (query) or n x cols row-major (features);  */
+    int64_t n, cols;          /*   valid until agp_serve_release                                     */
+    double queue_us;          /* submission -> admission                                             */
+    double latency_us;        /* submission -> result ready                                          */
+} agp_result_t;
+
+/* Create a server over graph g (which must outlive it). Errors: AGP_EINVAL, AGP_ENOMEM, AGP_ECUDA. */
+AGP_API int agp_serve_create(agp_graph_t g, const agp_serve_config_t *config, agp_server_t *out);
+/* Queue a request; thread-safe. Validation errors are returned immediately (AGP_EINVAL). */
+AGP_API int agp_serve_submit(agp_server_t s, const agp_request_t *req, uint64_t *ticket);
+/* AGP_OK and *out filled when done (out->status tells how it ended), AGP_EAGAIN while pending. */
+AGP_API int agp_serve_poll(agp_server_t s, uint64_t ticket, agp_result_t *out);
+/* Wait up to timeout_us (< 0: no limit) for a result; AGP_ETIMEDOUT if it is still pending. */
+AGP_API int agp_serve_wait(agp_server_t s, uint64_t ticket, int64_t timeout_us, agp_result_t *out);
+/* Free the result buffer of a finished request (pending requests: AGP_EINVAL). */
+AGP_API int agp_serve_release(agp_server_t s, uint64_t ticket);
+/* Cancel: a queued request finishes at once, an admitted one at the next sweep, with AGP_ECANCELED. */
+AGP_API int agp_serve_cancel(agp_server_t s, uint64_t ticket);
+/* Counters: completed requests, sweeps run, lanes in flight now, requests queued now. */
+AGP_API int agp_serve_stats(agp_server_t s, int64_t *completed, int64_t *sweeps, int32_t *lanes_active,
+                            int32_t *queued);
+/* Stop the server thread (finishing nothing further), free everything. */
+AGP_API int agp_serve_destroy(agp_server_t s);
+
+/*
+ * Autotuner of the wave width: runs the given batch (arguments as agp_query_batch, output on the
+ * device) once per candidate lane count in `candidates` (n_candidates > 0; NULL = powers of two up
+ * to the batch's lane count), times each second run with CUDA events, keeps the fastest on the
+ * graph (agp_graph_set_wave_lanes) and returns it. With the environment variable AGP_TUNE_CACHE
+ * naming a file, results are cached there, keyed by graph size and parameter signature, and a
+ * cached entry is used without timing. best_lanes / best_ms: host pointers (may be NULL).
+ */
+AGP_API int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q,
+                         const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
+                         int64_t ld_out, uint32_t flags, const int32_t *candidates, int32_t n_candidates,
+                         int32_t *best_lanes, double *best_ms, void *stream);
+
 /*
  * Kernel accounting of a graph handle since the last reset.
- *   ms[4], launches[4]  (host, may be NULL): device time in milliseconds and number of launches of
- *                       the level-loop kernels measured under AGP_PROFILE, in the order
- *                       0 = expand (frontier, reserve, threshold, short pushes, light sampling),
- *                       1 = push (long deterministic prefixes), 2 = sample (heavy tails),
- *                       3 = level end (frontier swap)
+ *   ms[5], launches[5]  (host, may be NULL): device time in milliseconds and number of launches of
+ *                       the level-loop steps measured under AGP_PROFILE, in the order
+ *                       0 = compact (next-frontier bitmaps -> ascending item list, 3 kernels),
+ *                       1 = expand (reserve, threshold, short pushes, light sampling),
+ *                       2 = push (long deterministic prefixes), 3 = sample (heavy tails),
+ *                       4 = level end
  *   kernel_launches     (host, may be NULL): every kernel the library launched for this graph
  *                       (graph nodes included), with or without AGP_PROFILE
  *   reset               non-zero: clear the counters after reading

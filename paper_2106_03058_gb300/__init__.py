@@ -22,12 +22,13 @@ __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
     "feature_propagate", "katz_beta", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
-    "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
+    "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
+    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
 ]
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE = 0x1, 0x2, 0x4, 0x8, 0x10
-KERNELS = ("expand", "push", "sample", "level_end")
+KERNELS = ("compact", "expand", "push", "sample", "level_end")
 ADD_SELF_LOOPS, EDGES_ON_DEVICE = 0x1, 0x2
 MAX_LEVELS = 64
 
@@ -57,6 +58,26 @@ class Stats(C.Structure):
                 "samples_drawn": self.samples_drawn, "samples_accepted": self.samples_accepted,
                 "by_kernel": [list(r) for r in self.by_kernel]}
 
+
+class ServeConfig(C.Structure):
+    """``agp_serve_config_t``."""
+    _fields_ = [("mode", C.c_int32), ("max_lanes", C.c_int32), ("result_budget", C.c_int64),
+                ("results_on_host", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Request(C.Structure):
+    """``agp_request_t``: a single-source query (source >= 0) or a BF16 feature block (source = -1)."""
+    _fields_ = [("params", Params), ("source", C.c_int32), ("cols", C.c_int32), ("X", C.c_void_p),
+                ("ldx", C.c_int64), ("deadline_us", C.c_int64), ("flags", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    """``agp_result_t``."""
+    _fields_ = [("status", C.c_int32), ("on_host", C.c_int32), ("pi", C.c_void_p), ("n", C.c_int64),
+                ("cols", C.c_int64), ("queue_us", C.c_double), ("latency_us", C.c_double)]
+
+
+SERVE_BATCHED, SERVE_FIFO_PLAIN, REQ_X_ON_DEVICE = 0, 1, 0x1
 
 _lib = None
 _lock = threading.Lock()
@@ -88,9 +109,23 @@ def lib():
             L.agp_katz_beta.argtypes = [_vp, _dbl, _i32, _dbl, C.POINTER(_dbl), C.POINTER(_dbl), _vp]
             L.agp_threshold.argtypes = [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp]
             L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
+            L.agp_graph_set_wave_lanes.argtypes = [_vp, _i32]
+            L.agp_autotune.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _i32,
+                                       C.POINTER(_i32), C.POINTER(_dbl), _vp]
+            L.agp_serve_create.argtypes = [_vp, C.POINTER(ServeConfig), C.POINTER(_vp)]
+            L.agp_serve_submit.argtypes = [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+            L.agp_serve_poll.argtypes = [_vp, C.c_uint64, C.POINTER(Result)]
+            L.agp_serve_wait.argtypes = [_vp, C.c_uint64, _i64, C.POINTER(Result)]
+            L.agp_serve_release.argtypes = [_vp, C.c_uint64]
+            L.agp_serve_cancel.argtypes = [_vp, C.c_uint64]
+            L.agp_serve_stats.argtypes = [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32)]
+            L.agp_serve_destroy.argtypes = [_vp]
+            for f in ("agp_serve_create", "agp_serve_submit", "agp_serve_poll", "agp_serve_wait", "agp_serve_release",
+                      "agp_serve_cancel", "agp_serve_stats", "agp_serve_destroy"):
+                getattr(L, f).restype = C.c_int
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
-                      "agp_profile_read"):
+                      "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -184,6 +219,10 @@ class Graph:
     def __exit__(self, *exc):
         self.destroy()
 
+    def set_wave_lanes(self, lanes):
+        """``agp_graph_set_wave_lanes`` (0 = automatic)."""
+        _check("agp_graph_set_wave_lanes", lib().agp_graph_set_wave_lanes(self.handle, int(lanes)))
+
     def set_memory_budget(self, nbytes):
         _check("agp_graph_set_memory_budget", lib().agp_graph_set_memory_budget(self.handle, int(nbytes)))
 
@@ -251,10 +290,109 @@ def query_batch(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=0, stats
     return st
 
 
+def autotune(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=INPUT_ON_DEVICE | OUTPUT_ON_DEVICE,
+             candidates=None, stream=None):
+    """``agp_autotune``: returns (best lanes, best ms or -1 when taken from the cache)."""
+    Q = int(x_off.shape[0]) - 1
+    parr, np_, keep = _params_array(params, Q)
+    cand = None if candidates is None else (C.c_int32 * len(candidates))(*candidates)
+    best, ms = _i32(), _dbl()
+    _check("agp_autotune", lib().agp_autotune(g.handle, parr, np_, Q, _ptr(x_off), _ptr(x_idx), _ptr(x_val), _ptr(out),
+                                               int(ld_out if ld_out is not None else g.n), int(flags), cand,
+                                               0 if candidates is None else len(candidates), C.byref(best), C.byref(ms),
+                                               _stream(stream)))
+    return best.value, ms.value
+
+
+class Server:
+    """``agp_serve_*``: continuous-batching server over a graph (see include/agp.h)."""
+
+    def __init__(self, g, mode=SERVE_BATCHED, max_lanes=0, result_budget=0, results_on_host=False):
+        self.g = g
+        cfg = ServeConfig(int(mode), int(max_lanes), int(result_budget), int(bool(results_on_host)), 0)
+        h = _vp()
+        _check("agp_serve_create", lib().agp_serve_create(g.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, params, source=None, X=None, deadline_us=0):
+        """Queue a query from `source` or a feature block X (CUDA bf16 [n, cols], read in place)."""
+        if source is not None:
+            req = Request(params, int(source), 0, None, 0, int(deadline_us), 0, 0)
+        else:
+            req = Request(params, -1, int(X.shape[1]), X.data_ptr(), int(X.stride(0)), int(deadline_us),
+                          REQ_X_ON_DEVICE, 0)
+        t = C.c_uint64()
+        _check("agp_serve_submit", lib().agp_serve_submit(self.handle, C.byref(req), C.byref(t)))
+        if X is not None:
+            self._keep[t.value] = X  # the device block must outlive the request
+        return t.value
+
+    def poll(self, ticket):
+        r = Result()
+        rc = lib().agp_serve_poll(self.handle, int(ticket), C.byref(r))
+        if rc == 5:  # AGP_EAGAIN
+            return None
+        _check("agp_serve_poll", rc)
+        return r
+
+    def wait(self, ticket, timeout_us=-1):
+        r = Result()
+        rc = lib().agp_serve_wait(self.handle, int(ticket), int(timeout_us), C.byref(r))
+        if rc == 6:  # AGP_ETIMEDOUT
+            return None
+        _check("agp_serve_wait", rc)
+        return r
+
+    def result_array(self, r):
+        """Copy a finished result into a torch tensor ([n] or [n, cols], on its device or the host)."""
+        import torch
+        count = int(r.n * r.cols)
+        if r.on_host:
+            buf = (C.c_float * count).from_address(r.pi)
+            t = torch.from_numpy(np.ctypeslib.as_array(buf).copy())
+        else:
+            t = torch.empty(count, dtype=torch.float32, device=f"cuda:{self.g.device}")
+            if count:
+                t.copy_(torch.as_tensor(_CudaArray(r.pi, count, "<f4"), device=f"cuda:{self.g.device}"))
+        return t if r.cols == 1 else t.view(int(r.n), int(r.cols))
+
+    def release(self, ticket):
+        _check("agp_serve_release", lib().agp_serve_release(self.handle, int(ticket)))
+        self._keep.pop(ticket, None)
+
+    def cancel(self, ticket):
+        _check("agp_serve_cancel", lib().agp_serve_cancel(self.handle, int(ticket)))
+
+    def stats(self):
+        c, sw = _i64(), _i64()
+        a, q = _i32(), _i32()
+        _check("agp_serve_stats", lib().agp_serve_stats(self.handle, C.byref(c), C.byref(sw), C.byref(a), C.byref(q)))
+        return {"completed": c.value, "sweeps": sw.value, "lanes_active": a.value, "queued": q.value}
+
+    def destroy(self):
+        if self.handle:
+            lib().agp_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 def profile_read(g, reset=False):
     """``agp_profile_read``: ({kernel: ms}, {kernel: launches}, all kernel launches)."""
-    ms = (_dbl * 4)()
-    ln = (_i64 * 4)()
+    ms = (_dbl * 5)()
+    ln = (_i64 * 5)()
     tot = _i64()
     _check("agp_profile_read", lib().agp_profile_read(g.handle, ms, ln, C.byref(tot), int(bool(reset))))
     return dict(zip(KERNELS, list(ms))), dict(zip(KERNELS, list(ln))), tot.value

@@ -88,6 +88,8 @@ struct ServeState; // serving (serve.cu)
 
 }  // namespace agp
 
+struct agp_server_s;
+
 struct agp_graph_s {
     int device = 0;
     int64_t n = 0, nnz = 0;
@@ -97,11 +99,12 @@ struct agp_graph_s {
     int32_t *colidx = nullptr;
     int32_t *deg = nullptr;
     int64_t mem_budget = 0;        // 0 = default
+    int32_t wave_lanes = 0;        // lanes in flight per wave, 0 = automatic (L2 residency)
     agp::Workspace *ws = nullptr;
     void *in_stage = nullptr;      // device staging of per-call inputs (grown on demand)
     size_t in_bytes = 0;
-    double prof_ms[4] = {0, 0, 0, 0};      // AGP_PROFILE: device time per level-loop kernel
-    int64_t prof_launches[4] = {0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};   // AGP_PROFILE: device time per level-loop step
+    int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     int64_t kernel_launches = 0;           // all kernels launched for this graph
     agp::DevGraph dev() const { return agp::DevGraph{n, nnz, rowptr, colidx, deg}; }
 };
@@ -114,11 +117,26 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
               double *lambda1, cudaStream_t stream);
 int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t *nodes,
               const float *c, int32_t *k_out, cudaStream_t stream);
+int wave_lanes(const agp_graph_s *g);
+int autotune(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
+             const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
+             const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, double *best_ms,
+             cudaStream_t s);
 int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q,
                 const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
                 int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d,
                       int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t stream);
+
+// serving (serve.cu)
+int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **out);
+int serve_submit(agp_server_s *s, const agp_request_t *req, uint64_t *ticket);
+int serve_poll(agp_server_s *s, uint64_t ticket, agp_result_t *out);
+int serve_wait(agp_server_s *s, uint64_t ticket, int64_t timeout_us, agp_result_t *out);
+int serve_release(agp_server_s *s, uint64_t ticket);
+int serve_cancel(agp_server_s *s, uint64_t ticket);
+int serve_stats(agp_server_s *s, int64_t *completed, int64_t *sweeps, int32_t *lanes_active, int32_t *queued);
+int serve_destroy(agp_server_s *s);
 
 // device-wide primitives (sort_scan.cu)
 // Exclusive prefix sum of `count` uint32 flags into int64 offsets; total written to *d_total.

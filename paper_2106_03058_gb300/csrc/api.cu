@@ -178,6 +178,22 @@ int agp_graph_set_memory_budget(agp_graph_t g, int64_t bytes)
     return AGP_OK;
 }
 
+int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (lanes < 0) return agp::fail(AGP_EINVAL, "lanes < 0");
+    g->wave_lanes = lanes;
+    return AGP_OK;
+}
+
+int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
+                 const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
+                 const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, double *best_ms, void *stream)
+{
+    return agp::autotune(g, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, candidates, n_candidates,
+                         best_lanes, best_ms, (cudaStream_t)stream);
+}
+
 int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
                     const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
                     agp_stats_t *stats, void *stream)
@@ -225,13 +241,13 @@ int agp_katz_beta(agp_graph_t g, double fraction, int32_t iters, double tol, dou
 int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64_t *kernel_launches, int reset)
 {
     if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = g->prof_ms[k];
         if (launches) launches[k] = g->prof_launches[k];
     }
     if (kernel_launches) *kernel_launches = g->kernel_launches;
     if (reset) {
-        for (int k = 0; k < 4; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
+        for (int k = 0; k < 5; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
         g->kernel_launches = 0;
     }
     return AGP_OK;
@@ -242,5 +258,23 @@ int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int3
 {
     return agp::threshold(g, a, eps, count, nodes, c, k_out, (cudaStream_t)stream);
 }
+
+int agp_serve_create(agp_graph_t g, const agp_serve_config_t *config, agp_server_t *out)
+{
+    return agp::serve_create(g, config, out);
+}
+int agp_serve_submit(agp_server_t s, const agp_request_t *req, uint64_t *ticket) { return agp::serve_submit(s, req, ticket); }
+int agp_serve_poll(agp_server_t s, uint64_t ticket, agp_result_t *out) { return agp::serve_poll(s, ticket, out); }
+int agp_serve_wait(agp_server_t s, uint64_t ticket, int64_t timeout_us, agp_result_t *out)
+{
+    return agp::serve_wait(s, ticket, timeout_us, out);
+}
+int agp_serve_release(agp_server_t s, uint64_t ticket) { return agp::serve_release(s, ticket); }
+int agp_serve_cancel(agp_server_t s, uint64_t ticket) { return agp::serve_cancel(s, ticket); }
+int agp_serve_stats(agp_server_t s, int64_t *completed, int64_t *sweeps, int32_t *lanes_active, int32_t *queued)
+{
+    return agp::serve_stats(s, completed, sweeps, lanes_active, queued);
+}
+int agp_serve_destroy(agp_server_t s) { return agp::serve_destroy(s); }
 
 }  // extern "C"

@@ -1,0 +1,141 @@
+// lanes.cuh -- lane state of the level pipeline, shared by batched queries and the server.
+//
+// A lane is one propagation problem with a non-negative, L1-normalised signal (one sign part of a
+// query or of a feature column, Section 3). Lanes own two dense FP32 residue vectors (level parity)
+// and a coefficient row; their reserves accumulate at out[u * su].
+#pragma once
+
+#include <vector>
+
+#include "agp_internal.cuh"
+
+namespace agp {
+
+constexpr int kMaxLevels = AGP_MAX_LEVELS;
+constexpr int kChunk = 512;          // prefix edges per chunk record (one warp)
+constexpr int kMinBlocks = 4;        // resident CTAs per SM the level kernels are compiled for
+constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
+constexpr float kLightSamples = 4.f; // tails expected to yield at most this many trials stay inline
+constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
+constexpr uint32_t kSampleTag = 0x53414D50u;
+
+struct LaneParam {
+    double eps_d;     // eps (FP64) for the push/sample decision
+    float eps;        // eps (FP32), the sampled increment
+    float a, b;       // FP32 exponents for the increments
+    double a_d;       // FP64 exponent a for the push/sample decision
+    int32_t a_mode;   // 0: a = 0, 1: a = 1, 2: a = 1/2, 3: general
+    int32_t b_mode;
+    int32_t L;
+    int32_t out_row;  // query / column index (statistics and bookkeeping)
+    uint32_t key0, key1;
+    float *out;       // pi(u) of this lane accumulates at out[u * su]
+    int64_t su;
+};
+
+struct LaneStats {
+    unsigned long long frontier[kMaxLevels];
+    unsigned long long by_kernel[3][4];  // [expand, push, sample][det, drawn, accepted, unused]
+};
+
+struct Ctrl {
+    unsigned long long n_items;  // frontier size of the current level (set by the compaction)
+    unsigned long long n_det, n_smp;
+    unsigned int error;          // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 16: bad level
+    unsigned int lanes_used;     // lanes [0, lanes_used) hold work; the compaction scans only those
+};
+
+constexpr int kProfKernels = 5;  // compact, expand, push, sample, level end
+constexpr int kScanUnit = 1024;  // floats of a lane's residue vector scanned by one CTA step (256 x float4)
+
+struct KArgs {
+    DevGraph g;
+    int ubits;
+    uint32_t umask;
+    float *R;                 // [2][G][ldR]
+    size_t par_stride;        // G * ldR
+    uint32_t *items;          // current frontier, ascending (lane << ubits | u)
+    float *rval;              // r^(i)(u) of each frontier item
+    int64_t ldR;              // lane stride of R (n rounded up to kScanUnit floats)
+    int64_t units;            // kScanUnit-float units per lane
+    int64_t *part;            // per-range counts / offsets of the compaction
+    int part_blocks;          // compaction ranges (blocks)
+    float *c_item;
+    int2 *k_item;             // (prefix length, tail segment length)
+    uint2 *det_rec, *smp_rec;
+    unsigned long long cap_items, cap_det, cap_smp;
+    const LaneParam *lanes;
+    const float2 *coef;       // [G][kMaxLevels] (keep_i = scale * w_i/Y_i, push_i = Y_{i+1}/Y_i)
+    int32_t *level;           // [G], -1 = idle
+    LaneStats *stats;
+    int collect;
+    int G;
+    Ctrl *ctrl;
+};
+
+struct Workspace {
+    int device = 0;
+    int G = 0;
+    int64_t n = 0;
+    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0;
+    float *R = nullptr;
+    uint32_t *items = nullptr;
+    float *rval = nullptr;
+    int64_t ldR = 0;
+    int64_t *part = nullptr;
+    int part_blocks = 1;
+    float *c_item = nullptr;
+    int2 *k_item = nullptr;
+    uint2 *det_rec = nullptr, *smp_rec = nullptr;
+    LaneParam *lanes = nullptr;
+    float2 *coef = nullptr;
+    int32_t *level = nullptr;
+    LaneStats *stats = nullptr;
+    Ctrl *ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;            // pinned
+    LaneParam *h_lanes = nullptr;      // pinned
+    // per-call staging (grown on demand)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    float *out_stage = nullptr;
+    size_t out_stage_bytes = 0;
+    // captured wave graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_levels = -1;
+    int graph_collect = -1;
+    int graph_profile = -1;
+    // AGP_PROFILE events: [level][kernel][begin/end]
+    cudaEvent_t ev[kMaxLevels][kProfKernels][2] = {};
+    bool ev_ready = false;
+    size_t bytes = 0;
+};
+
+struct CoefSpec {
+    int32_t lane;      // workspace lane whose coefficient row is written
+    int32_t kind, L;
+    double param;
+    int32_t w_off;     // FINITE: offset of w_0..w_L in the weight array
+    double scale;      // sign * ||x_part||_1 (the Y_0 factor is applied here)
+};
+
+// ---- host helpers of propagate.cu shared with serve.cu -------------------------------------------
+int exponent_mode(double p);
+int validate_params(const agp_params_t &p);
+void lane_key(uint64_t seed, uint64_t stream, int part, uint32_t &k0, uint32_t &k1);
+size_t bytes_per_lane(const agp_graph_s *g);
+int lane_capacity(const agp_graph_s *g);
+int create_workspace(agp_graph_s *g, int G, Workspace **out);
+KArgs make_args(agp_graph_s *g, Workspace *ws, int collect);
+int blocks_for(unsigned long long work, int per_block);
+void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,
+                  cudaEvent_t (*ev)[2] = nullptr);
+void launch_compact(const KArgs &A, cudaStream_t s);
+int capture_levels(const KArgs &A, int levels, cudaGraphExec_t *out);
+void launch_coef(const CoefSpec *spec, const double *wts, float2 *coef, int nspec, cudaStream_t s);
+void launch_seed_sources(const KArgs &A, const int32_t *lanes, const int32_t *sources, int count, cudaStream_t s);
+void launch_colnorms_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ldx, double *norms, cudaStream_t s);
+void launch_seed_dense_bf16(const KArgs &A, const uint16_t *X, int64_t ldx, const int32_t *lane_of,
+                            const int32_t *col_of, const int32_t *part_of, const double *norms, int nl, cudaStream_t s);
+int grow(void **p, size_t *have, size_t need);
+
+}  // namespace agp

@@ -23,6 +23,7 @@
 // test is exact. Sizes stay on the device; kernels are grid-stride loops over device-side counts,
 // so a whole wave can be captured in one CUDA graph.
 #include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
 
 #include <algorithm>
 #include <cfloat>
@@ -31,101 +32,11 @@
 #include <cstring>
 #include <vector>
 
-#include "agp_internal.cuh"
+#include "lanes.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace agp {
-
-constexpr int kMaxLevels = AGP_MAX_LEVELS;
-constexpr int kChunk = 1024;         // prefix edges per chunk record (one warp)
-constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
-constexpr float kLightSamples = 4.f; // tails expected to yield at most this many trials stay inline
-constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
-constexpr uint32_t kSampleTag = 0x53414D50u;
-
-struct LaneParam {
-    double eps_d;     // eps (FP64) for the push/sample decision
-    float eps;        // eps (FP32), the sampled increment
-    float a, b;       // FP32 exponents for the increments
-    double a_d;       // FP64 exponent a for the push/sample decision
-    int32_t a_mode;   // 0: a = 0, 1: a = 1, 2: a = 1/2, 3: general
-    int32_t b_mode;
-    int32_t L;
-    int32_t out_row;
-    uint32_t key0, key1;
-};
-
-struct LaneStats {
-    unsigned long long frontier[kMaxLevels];
-    unsigned long long by_kernel[3][4];  // [expand, push, sample][det, drawn, accepted, appends]
-};
-
-struct OutDesc {
-    float *out;
-    int64_t su, sr;   // pi(lane row, u) lives at out[u * su + row * sr]
-};
-
-struct Ctrl {
-    unsigned long long n_items[2];
-    unsigned long long n_det, n_smp;
-    unsigned int cur;
-    unsigned int error;  // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 8: bad index
-    OutDesc od;
-};
-
-struct KArgs {
-    DevGraph g;
-    int ubits;
-    uint32_t umask;
-    float *R;                 // [2][G][n]
-    size_t par_stride;        // G * n
-    uint32_t *items0, *items1;
-    float *c_item;
-    int2 *k_item;             // (prefix length, tail segment length)
-    uint2 *det_rec, *smp_rec;
-    unsigned long long cap_items, cap_det, cap_smp;
-    const LaneParam *lanes;
-    const float2 *coef;       // [G][kMaxLevels] (keep_i = scale * w_i/Y_i, push_i = Y_{i+1}/Y_i)
-    int32_t *level;           // [G], -1 = idle
-    LaneStats *stats;
-    int collect;
-    int G;
-    Ctrl *ctrl;
-};
-
-struct Workspace {
-    int device = 0;
-    int G = 0;
-    int64_t n = 0;
-    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0;
-    float *R = nullptr;
-    uint32_t *items[2] = {nullptr, nullptr};
-    float *c_item = nullptr;
-    int2 *k_item = nullptr;
-    uint2 *det_rec = nullptr, *smp_rec = nullptr;
-    LaneParam *lanes = nullptr;
-    float2 *coef = nullptr;
-    int32_t *level = nullptr;
-    LaneStats *stats = nullptr;
-    Ctrl *ctrl = nullptr;
-    Ctrl *h_ctrl = nullptr;            // pinned
-    LaneParam *h_lanes = nullptr;      // pinned
-    // per-call staging (grown on demand)
-    void *stage = nullptr;
-    size_t stage_bytes = 0;
-    float *out_stage = nullptr;
-    size_t out_stage_bytes = 0;
-    // captured wave graph
-    cudaGraphExec_t graph = nullptr;
-    int graph_levels = -1;
-    int graph_collect = -1;
-    int graph_profile = -1;
-    // AGP_PROFILE events: [level][kernel][begin/end]
-    cudaEvent_t ev[kMaxLevels][4][2] = {};
-    bool ev_ready = false;
-    size_t bytes = 0;
-};
 
 // ------------------------------------------------------------------------------------ helpers
 __device__ __forceinline__ float deg_pow_neg_f(int32_t d, int mode, float p)
@@ -179,30 +90,24 @@ __device__ __forceinline__ int det_prefix(float c, const LaneParam &P, const int
     return lo;
 }
 
-__device__ __forceinline__ void append_item(const KArgs &A, uint32_t item, unsigned int buf, int lane, int lvl_next,
-                                            int kern)
+// ---- pushes --------------------------------------------------------------------------------------
+// Pushes are fire-and-forget atomic adds (no value returned, so no thread waits on them). The next
+// frontier is not tracked during the pushes: each level starts by scanning the residue vectors of
+// the active lanes (see k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
+__device__ __forceinline__ void push_to(float *Rn, int32_t v, float inc)
 {
-    cg::coalesced_group grp = cg::coalesced_threads();
-    unsigned long long base = 0;
-    if (grp.thread_rank() == 0) base = atomicAdd(&A.ctrl->n_items[buf], (unsigned long long)grp.size());
-    base = grp.shfl(base, 0);
-    const unsigned long long pos = base + grp.thread_rank();
-    uint32_t *dst = buf ? A.items1 : A.items0;
-    if (pos < A.cap_items) dst[pos] = item;
-    else atomicOr(&A.ctrl->error, 1u);
-    if (A.collect) {
-        if (lvl_next < kMaxLevels) atomicAdd(&A.stats[lane].frontier[lvl_next], 1ull);
-        if (kern >= 0) atomicAdd(&A.stats[lane].by_kernel[kern][3], 1ull);
-    }
+    if (inc != 0.f) atomicAdd(Rn + v, inc);
 }
 
-// r^(i+1)(v) += inc, first toucher appends (lane, v) to the next frontier
-__device__ __forceinline__ void push_to(const KArgs &A, float *Rn, int lane, int32_t v, float inc,
-                                        unsigned int nxt, int lvl_next, int kern)
+// Reserve `count` consecutive slots of a record list with one atomic per coalesced group.
+__device__ __forceinline__ unsigned long long reserve_records(unsigned long long *counter, unsigned int count)
 {
-    if (!(inc >= FLT_MIN)) return;
-    const float old = atomicAdd(Rn + v, inc);
-    if (old == 0.f) append_item(A, ((uint32_t)lane << A.ubits) | (uint32_t)v, nxt, lane, lvl_next, kern);
+    cg::coalesced_group grp = cg::coalesced_threads();
+    const unsigned int before = cg::exclusive_scan(grp, count);
+    unsigned long long base = 0;
+    if (grp.thread_rank() == grp.size() - 1) base = atomicAdd(counter, (unsigned long long)(before + count));
+    base = grp.shfl(base, grp.size() - 1);
+    return base + before;
 }
 
 struct Uniforms {
@@ -224,9 +129,9 @@ struct Uniforms {
 };
 
 // Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane.
-__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int lane, int32_t u, int lvl,
-                             uint32_t seg, const int32_t *row, int j0, int j1, float c, unsigned int nxt,
-                             unsigned long long &drawn, unsigned long long &accepted, int kern)
+__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int lane, int32_t u, int lvl, uint32_t seg,
+                             const int32_t *row, int j0, int j1, float c, unsigned long long &drawn,
+                             unsigned long long &accepted, int kern)
 {
     Uniforms U((uint32_t)u, (uint32_t)lvl, seg, P.key0, P.key1);
     const float ce = (float)((double)c / P.eps_d);  // c / eps
@@ -265,7 +170,7 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int 
             }
             if (keep) {
                 ++accepted;
-                push_to(A, Rn, lane, v, P.eps, nxt, lvl + 1, kern);
+                push_to(Rn, v, P.eps);
             }
             if (++j >= gend) break;
         }
@@ -273,103 +178,231 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int 
 }
 
 // ------------------------------------------------------------------------------------ kernels
-__global__ void __launch_bounds__(kBlock) k_expand(KArgs A)
+// ---- frontier compaction: F_i = {u : r^(i)(u) != 0} in ascending (lane, u) order ----------------
+// The residue vectors of lanes [0, lanes_used) are cut into units of kScanUnit floats; the units are
+// split into part_blocks contiguous ranges. Pass 1 counts the non-zeros of every range, pass 2
+// scans the counts, pass 3 writes (lane << ubits | u, r) of every non-zero and clears the vector.
+// Idle lanes (level < 0) are skipped; their vectors are zero.
+__device__ __forceinline__ void compact_range(const KArgs &A, int64_t &begin, int64_t &end)
 {
-    Ctrl *ctrl = A.ctrl;
-    const unsigned int cur = ctrl->cur, nxt = cur ^ 1u;
-    const unsigned long long n_items = min(ctrl->n_items[cur], A.cap_items);
-    const uint32_t *items = cur ? A.items1 : A.items0;
-    const OutDesc od = ctrl->od;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < n_items; idx += stride) {
-        const uint32_t item = items[idx];
-        const int lane = (int)(item >> A.ubits);
-        const int32_t u = (int32_t)(item & A.umask);
-        const int lvl = A.level[lane];
-        if (lvl < 0 || lvl >= kMaxLevels) {
-            atomicOr(&ctrl->error, 16u);
-            continue;
-        }
-        const LaneParam P = A.lanes[lane];
-        float *Rc = A.R + (size_t)(lvl & 1) * A.par_stride + (size_t)lane * A.g.n;
-        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.g.n;
-        const float r = Rc[u];
-        Rc[u] = 0.f;
-        const float2 cf = A.coef[lane * kMaxLevels + lvl];
-        // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
-        atomicAdd(od.out + (int64_t)u * od.su + (int64_t)P.out_row * od.sr, cf.x * r);
-        if (lvl >= P.L) continue;
-        const int32_t d = A.g.deg[u];
-        if (d == 0) continue;
-        const float c = apply_deg(cf.y * r, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
-        if (!(c > 0.f)) continue;
-        const int32_t *row = A.g.colidx + A.g.rowptr[u];
-        const int k = det_prefix(c, P, row, d, A.g.deg);
-        unsigned long long drawn = 0, accepted = 0;
-        if (k > 0) {
-            if (k <= kInlineDet) {
-                for (int j = 0; j < k; ++j) {
-                    const int32_t v = row[j];
-                    const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
-                    push_to(A, Rn, lane, v, inc, nxt, lvl + 1, 0);
-                }
-                if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
-            } else {
-                const int nrec = (k + kChunk - 1) / kChunk;
-                const unsigned long long base = atomicAdd(&ctrl->n_det, (unsigned long long)nrec);
-                for (int t = 0; t < nrec; ++t) {
-                    if (base + t < A.cap_det) A.det_rec[base + t] = make_uint2((uint32_t)idx, (uint32_t)t);
-                    else atomicOr(&ctrl->error, 2u);
-                }
-            }
-        }
-        const int tail = d - k;
-        int seglen = 0;
-        if (tail > 0) {
-            const float ce = (float)((double)c / P.eps_d);
-            const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
-            const float expect = p0 * (float)tail;  // upper bound on the trials reached
-            if (expect <= kLightSamples) {
-                sample_range(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, nxt, drawn, accepted, 0);
-            } else {
-                int nseg = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
-                nseg = max(nseg, 1);
-                seglen = (tail + nseg - 1) / nseg;
-                nseg = (tail + seglen - 1) / seglen;
-                const unsigned long long base = atomicAdd(&ctrl->n_smp, (unsigned long long)nseg);
-                for (int t = 0; t < nseg; ++t) {
-                    if (base + t < A.cap_smp) A.smp_rec[base + t] = make_uint2((uint32_t)idx, (uint32_t)t);
-                    else atomicOr(&ctrl->error, 4u);
-                }
-            }
-        }
-        if (k > kInlineDet || seglen > 0) {
-            A.c_item[idx] = c;
-            A.k_item[idx] = make_int2(k, seglen);
-        }
-        if (A.collect && (drawn | accepted)) {
-            atomicAdd(&A.stats[lane].by_kernel[0][1], drawn);
-            atomicAdd(&A.stats[lane].by_kernel[0][2], accepted);
-        }
+    const int64_t U = (int64_t)min((int)A.ctrl->lanes_used, A.G) * A.units;
+    const int64_t per = (U + A.part_blocks - 1) / A.part_blocks;
+    begin = (int64_t)blockIdx.x * per;
+    end = min(U, begin + per);
+}
+
+__device__ __forceinline__ float4 *unit_ptr(const KArgs &A, int64_t unit, int &lane, bool &live)
+{
+    lane = (int)(unit / A.units);
+    const int lvl = A.level[lane];
+    live = lvl >= 0;
+    const int64_t off = (unit - (int64_t)lane * A.units) * kScanUnit;
+    return (float4 *)(A.R + (size_t)(lvl & 1) * A.par_stride + (size_t)lane * A.ldR + off);
+}
+
+__device__ __forceinline__ int nz4(float4 v)
+{
+    return (v.x != 0.f) + (v.y != 0.f) + (v.z != 0.f) + (v.w != 0.f);
+}
+
+__global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
+{
+    __shared__ unsigned long long red[kBlock / 32];
+    int64_t begin, end;
+    compact_range(A, begin, end);
+    unsigned long long c = 0;
+    for (int64_t unit = begin; unit < end; ++unit) {
+        int lane;
+        bool live;
+        const float4 *p = unit_ptr(A, unit, lane, live);
+        if (live) c += nz4(p[threadIdx.x]);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < kBlock / 32; ++k) t += red[k];
+        A.part[blockIdx.x] = (int64_t)t;
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_push(KArgs A)
+// Pass 2 (one block): exclusive scan of the range counts; the total is the frontier size.
+__global__ void k_compact_scan(KArgs A)
+{
+    __shared__ int64_t sums[1024];
+    const int t = threadIdx.x, nb = A.part_blocks;
+    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
+    int64_t s = 0;
+    for (int b = b0; b < b1; ++b) s += A.part[b];
+    sums[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int64_t v = sums[k];
+            sums[k] = run;
+            run += v;
+        }
+        A.ctrl->n_items = (unsigned long long)run;
+    }
+    __syncthreads();
+    int64_t run = sums[t];
+    for (int b = b0; b < b1; ++b) {
+        const int64_t v = A.part[b];
+        A.part[b] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
+{
+    __shared__ unsigned int wsum[kBlock / 32];
+    __shared__ unsigned long long run_s;
+    int64_t begin, end;
+    compact_range(A, begin, end);
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) run_s = (unsigned long long)A.part[blockIdx.x];
+    __syncthreads();
+    for (int64_t unit = begin; unit < end; ++unit) {
+        int lane;
+        bool live;
+        float4 *p = unit_ptr(A, unit, lane, live);
+        if (!live) continue;  // uniform across the block
+        const float4 v = p[threadIdx.x];
+        const unsigned int c = nz4(v);
+        unsigned int x = c;  // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id >= o) x += y;
+        }
+        if (lane_id == 31) wsum[warp] = x;
+        __syncthreads();
+        unsigned long long off = run_s;
+        for (int k = 0; k < warp; ++k) off += wsum[k];
+        off += x - c;
+        if (c) {
+            const uint32_t u0 = (uint32_t)((unit - (int64_t)lane * A.units) * kScanUnit + 4 * threadIdx.x);
+            const uint32_t hi = (uint32_t)lane << A.ubits;
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e[k] == 0.f) continue;
+                if (off < A.cap_items) {
+                    A.items[off] = hi | (u0 + (uint32_t)k);
+                    A.rval[off] = e[k];
+                } else {
+                    atomicOr(&A.ctrl->error, 1u);
+                }
+                ++off;
+            }
+            p[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (A.collect) atomicAdd(&A.stats[lane].frontier[A.level[lane]], (unsigned long long)c);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int k = 0; k < kBlock / 32; ++k) t += wsum[k];
+            run_s += t;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long idx)
 {
     Ctrl *ctrl = A.ctrl;
-    const unsigned int cur = ctrl->cur, nxt = cur ^ 1u;
-    const unsigned long long n_det = min(ctrl->n_det, A.cap_det);
-    const uint32_t *items = cur ? A.items1 : A.items0;
+    const uint32_t item = A.items[idx];
+    const int lane = (int)(item >> A.ubits);
+    const int32_t u = (int32_t)(item & A.umask);
+    const int lvl = A.level[lane];
+    if (lvl < 0 || lvl >= kMaxLevels) {
+        atomicOr(&ctrl->error, 16u);
+        return;
+    }
+    const LaneParam &P = A.lanes[lane];
+    float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
+    const float r = A.rval[idx];  // the compaction read r^(i)(u) and cleared it
+    const float2 cf = A.coef[lane * kMaxLevels + lvl];
+    // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
+    atomicAdd(P.out + (int64_t)u * P.su, cf.x * r);
+    if (lvl >= P.L) return;
+    const int32_t d = A.g.deg[u];
+    if (d == 0) return;
+    const float c = apply_deg(cf.y * r, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
+    if (!(c > 0.f)) return;
+    const int32_t *row = A.g.colidx + A.g.rowptr[u];
+    const int k = det_prefix(c, P, row, d, A.g.deg);
+    unsigned long long drawn = 0, accepted = 0;
+    if (k > 0) {
+        if (k <= kInlineDet) {
+            for (int j = 0; j < k; ++j) {
+                const int32_t v = row[j];
+                const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
+                push_to(Rn, v, inc);
+            }
+            if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
+        } else {
+            const unsigned int nrec = (unsigned int)((k + kChunk - 1) / kChunk);
+            const unsigned long long base = reserve_records(&ctrl->n_det, nrec);
+            for (unsigned int t = 0; t < nrec; ++t) {
+                if (base + t < A.cap_det) A.det_rec[base + t] = make_uint2((uint32_t)idx, t);
+                else atomicOr(&ctrl->error, 2u);
+            }
+        }
+    }
+    const int tail = d - k;
+    int seglen = 0;
+    if (tail > 0) {
+        const float ce = (float)((double)c / P.eps_d);
+        const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
+        const float expect = p0 * (float)tail;  // upper bound on the trials reached
+        if (expect <= kLightSamples) {
+            sample_range(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, drawn, accepted, 0);
+        } else {
+            int nseg = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
+            nseg = max(nseg, 1);
+            seglen = (tail + nseg - 1) / nseg;
+            nseg = (tail + seglen - 1) / seglen;
+            const unsigned long long base = reserve_records(&ctrl->n_smp, (unsigned int)nseg);
+            for (int t = 0; t < nseg; ++t) {
+                if (base + t < A.cap_smp) A.smp_rec[base + t] = make_uint2((uint32_t)idx, (uint32_t)t);
+                else atomicOr(&ctrl->error, 4u);
+            }
+        }
+    }
+    if (k > kInlineDet || seglen > 0) {
+        A.c_item[idx] = c;
+        A.k_item[idx] = make_int2(k, seglen);
+    }
+    if (A.collect && (drawn | accepted)) {
+        atomicAdd(&A.stats[lane].by_kernel[0][1], drawn);
+        atomicAdd(&A.stats[lane].by_kernel[0][2], accepted);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
+{
+    const unsigned long long n_items = min(A.ctrl->n_items, A.cap_items);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < n_items; idx += stride)
+        expand_item(A, idx);
+}
+
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
+{
+    const unsigned long long n_det = min(A.ctrl->n_det, A.cap_det);
     const int lane_id = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long rec = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; rec < n_det; rec += nwarps) {
         const uint2 R = A.det_rec[rec];
-        const uint32_t item = items[R.x];
+        const uint32_t item = A.items[R.x];
         const int lane = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
         const int lvl = A.level[lane];
-        const LaneParam P = A.lanes[lane];
-        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.g.n;
+        const LaneParam &P = A.lanes[lane];
+        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
         const float c = A.c_item[R.x];
         const int k = A.k_item[R.x].x;
         const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
@@ -377,34 +410,31 @@ __global__ void __launch_bounds__(kBlock) k_push(KArgs A)
         for (int j = j0 + lane_id; j < j1; j += 32) {
             const int32_t v = row[j];
             const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
-            push_to(A, Rn, lane, v, inc, nxt, lvl + 1, 1);
+            push_to(Rn, v, inc);
         }
         if (A.collect && lane_id == 0) atomicAdd(&A.stats[lane].by_kernel[1][0], (unsigned long long)(j1 - j0));
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_sample(KArgs A)
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
 {
-    Ctrl *ctrl = A.ctrl;
-    const unsigned int cur = ctrl->cur, nxt = cur ^ 1u;
-    const unsigned long long n_smp = min(ctrl->n_smp, A.cap_smp);
-    const uint32_t *items = cur ? A.items1 : A.items0;
+    const unsigned long long n_smp = min(A.ctrl->n_smp, A.cap_smp);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long rec = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; rec < n_smp; rec += stride) {
         const uint2 R = A.smp_rec[rec];
-        const uint32_t item = items[R.x];
+        const uint32_t item = A.items[R.x];
         const int lane = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
         const int lvl = A.level[lane];
-        const LaneParam P = A.lanes[lane];
-        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.g.n;
+        const LaneParam &P = A.lanes[lane];
+        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
         const float c = A.c_item[R.x];
         const int2 ks = A.k_item[R.x];
         const int d = A.g.deg[u];
         const int j0 = ks.x + (int)R.y * ks.y, j1 = min(d, j0 + ks.y);
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         unsigned long long drawn = 0, accepted = 0;
-        sample_range(A, P, Rn, lane, u, lvl, R.y, row, j0, j1, c, nxt, drawn, accepted, 2);
+        sample_range(A, P, Rn, lane, u, lvl, R.y, row, j0, j1, c, drawn, accepted, 2);
         if (A.collect && (drawn | accepted)) {
             atomicAdd(&A.stats[lane].by_kernel[2][1], drawn);
             atomicAdd(&A.stats[lane].by_kernel[2][2], accepted);
@@ -415,28 +445,18 @@ __global__ void __launch_bounds__(kBlock) k_sample(KArgs A)
 __global__ void k_level_end(KArgs A)
 {
     Ctrl *ctrl = A.ctrl;
-    const unsigned int cur = ctrl->cur;
     for (int l = threadIdx.x; l < A.G; l += blockDim.x) {
         const int lvl = A.level[l];
         if (lvl >= 0) A.level[l] = (lvl < A.lanes[l].L) ? lvl + 1 : -1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctrl->n_items[cur] = 0;
-        ctrl->cur = cur ^ 1u;
         ctrl->n_det = 0;
         ctrl->n_smp = 0;
     }
 }
 
 // ---- coefficients (Def. 3.1), FP64 on the device -------------------------------------------
-struct CoefSpec {
-    int32_t kind, L;
-    double param;
-    int32_t w_off;     // FINITE: offset of w_0..w_L in the weight array
-    double scale;      // sign * ||x_part||_1 (the Y_0 factor is applied here)
-};
-
 __global__ void k_coef(const CoefSpec *spec, const double *wts, float2 *coef, int nlanes)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -496,7 +516,7 @@ __global__ void k_coef(const CoefSpec *spec, const double *wts, float2 *coef, in
             keep = (float)(S.scale * Y0 * (w[i] / Y[i]));
             push = (i < L) ? (float)(Y[i + 1] / Y[i]) : 0.f;
         }
-        coef[l * kMaxLevels + i] = make_float2(keep, push);
+        coef[S.lane * kMaxLevels + i] = make_float2(keep, push);
     }
 }
 
@@ -529,7 +549,6 @@ __global__ void k_norms_sparse(const int64_t *off, const int32_t *idx, const flo
 __global__ void k_seed_sparse(KArgs A, const int64_t *off, const int32_t *idx, const float *val, int Q,
                               const int32_t *lane_of, const double *norms)
 {
-    const unsigned int cur = A.ctrl->cur;
     const int64_t total = off[Q];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int q = query_of(off, Q, t);
@@ -537,12 +556,21 @@ __global__ void k_seed_sparse(KArgs A, const int64_t *off, const int32_t *idx, c
         if (x == 0.f) continue;
         const int part = x < 0.f ? 1 : 0;
         const int lane = lane_of[2 * q + part];
-        if (lane < 0) continue;
         const int32_t u = idx[t];
-        if (u < 0 || u >= A.g.n) continue;
-        float *R0 = A.R + (size_t)lane * A.g.n;  // level 0 lives in parity 0
+        if (lane < 0 || u < 0 || u >= A.g.n) continue;
+        float *R0 = A.R + (size_t)lane * A.ldR;  // level 0 lives in parity 0
         const float r0 = (float)((double)fabsf(x) / norms[2 * q + part]);
-        push_to(A, R0, lane, u, r0, cur, 0, -1);
+        push_to(R0, u, r0);
+    }
+}
+
+// one-hot seeds x = e_source (already normalised) for lanes[t]
+__global__ void k_seed_sources(KArgs A, const int32_t *lanes, const int32_t *sources, int count)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const int lane = lanes[t];
+        const int32_t u = sources[t];
+        if (u >= 0 && u < A.g.n) push_to(A.R + (size_t)lane * A.ldR, u, 1.f);
     }
 }
 
@@ -562,11 +590,10 @@ __global__ void k_colnorms_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t
     }
 }
 
-// lane l of the wave takes column col_of[l], sign part part_of[l]
-__global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const int32_t *col_of,
+// seed l (lane lane_of[l], or l when lane_of is NULL) takes column col_of[l], sign part part_of[l]
+__global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const int32_t *lane_of, const int32_t *col_of,
                                   const int32_t *part_of, const double *norms, int nl)
 {
-    const unsigned int cur = A.ctrl->cur;
     const int64_t total = A.g.n * nl;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(t % nl);
@@ -575,9 +602,10 @@ __global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const
         const float x = __uint_as_float((uint32_t)X[u * ldx + col] << 16);
         const int part = part_of[l];
         if (!((part == 0 && x > 0.f) || (part == 1 && x < 0.f))) continue;
-        float *R0 = A.R + (size_t)l * A.g.n;
+        const int lane = lane_of ? lane_of[l] : l;
+        float *R0 = A.R + (size_t)lane * A.ldR;
         const float r0 = (float)((double)fabsf(x) / norms[2 * col + part]);
-        push_to(A, R0, l, (int32_t)u, r0, cur, 0, -1);
+        push_to(R0, (int32_t)u, r0);
     }
 }
 
@@ -604,8 +632,6 @@ __global__ void k_threshold(DevGraph g, double a, int a_mode, double eps, int64_
 }
 
 // ------------------------------------------------------------------------------------ host side
-namespace {
-
 int exponent_mode(double p)
 {
     if (p == 0.0) return 0;
@@ -683,7 +709,9 @@ size_t bytes_per_lane(const agp_graph_s *g)
     const double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
     // R (2 x 4) + items (2 x 4) + c (4) + k (8) + chunk and segment records (8 + 8, with the
     // extra records of long rows) per (lane, node)
-    return n * (8 + 8 + 4 + 8) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 4096;
+    // R (2 x 4) + items (4) + r values (4) + c (4) + k (8) + chunk and segment records (8 + 8, with
+    // the extra records of long rows) per (lane, node)
+    return n * (8 + 4 + 4 + 4 + 8) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
 int lane_capacity(const agp_graph_s *g)
@@ -693,19 +721,18 @@ int lane_capacity(const agp_graph_s *g)
     return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)by_bits, by_items, 4096}));
 }
 
-}  // namespace
-
 void free_workspace(Workspace *ws)
 {
     if (!ws) return;
     if (ws->graph) cudaGraphExecDestroy(ws->graph);
     if (ws->ev_ready)
         for (int l = 0; l < kMaxLevels; ++l)
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < kProfKernels; ++k)
                 for (int e = 0; e < 2; ++e) cudaEventDestroy(ws->ev[l][k][e]);
     cudaFree(ws->R);
-    cudaFree(ws->items[0]);
-    cudaFree(ws->items[1]);
+    cudaFree(ws->items);
+    cudaFree(ws->rval);
+    cudaFree(ws->part);
     cudaFree(ws->c_item);
     cudaFree(ws->k_item);
     cudaFree(ws->det_rec);
@@ -722,31 +749,34 @@ void free_workspace(Workspace *ws)
     delete ws;
 }
 
-namespace {
-
-int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
+// Lanes in flight per wave. Every lane scatters atomics into its own dense n-vector r^(i+1); the
+// automatic choice keeps those vectors of all lanes in flight within ~96 MB of the 129 MB L2, so
+// that the random atomics are served by L2 rather than DRAM (measured: 16 lanes of 4M nodes ran
+// slower than one lane at a time).
+int wave_lanes(const agp_graph_s *g)
 {
-    const int cap = lane_capacity(g);
-    int G = std::max(1, std::min(lanes_wanted, cap));
+    if (g->wave_lanes > 0) return g->wave_lanes;
+    const int64_t per_lane = 4 * std::max<int64_t>(g->n, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (96ll << 20) / per_lane));
+}
+
+// Lanes that fit the graph's memory budget (default: 60% of the free device memory, counting the
+// memory already held by the graph's current work buffers).
+int lanes_for_budget(agp_graph_s *g, int64_t held, int *lanes)
+{
     int64_t budget = g->mem_budget;
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
         AGP_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-        const size_t have = g->ws ? g->ws->bytes : 0;
-        budget = (int64_t)((double)(fr + have) * 0.6);
+        budget = (int64_t)((double)(fr + held) * 0.6);
     }
-    const int by_budget = (int)std::min<int64_t>(cap, std::max<int64_t>(0, budget / (int64_t)bytes_per_lane(g)));
-    if (by_budget < 1) return fail(AGP_EBUDGET, "memory budget too small for one propagation lane");
-    G = std::min(G, by_budget);
-    if (g->ws && g->ws->G >= G) {
-        *out = g->ws;
-        return AGP_OK;
-    }
-    if (g->ws) {
-        AGP_CUDA_TRY(cudaDeviceSynchronize());
-        free_workspace(g->ws);
-        g->ws = nullptr;
-    }
+    *lanes = (int)std::min<int64_t>(lane_capacity(g), std::max<int64_t>(0, budget / (int64_t)bytes_per_lane(g)));
+    if (*lanes < 1) return fail(AGP_EBUDGET, "memory budget too small for one propagation lane");
+    return AGP_OK;
+}
+
+int create_workspace(agp_graph_s *g, int G, Workspace **out)
+{
     Workspace *ws = new Workspace();
     ws->device = g->device;
     ws->G = G;
@@ -758,9 +788,13 @@ int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
     size_t acc = 0;
     int rc = AGP_OK;
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
-    A(dev_alloc(&ws->R, (size_t)2 * G * n, acc));
-    A(dev_alloc(&ws->items[0], ws->cap_items, acc));
-    A(dev_alloc(&ws->items[1], ws->cap_items, acc));
+    ws->ldR = ((int64_t)n + kScanUnit - 1) / kScanUnit * kScanUnit;
+    const int64_t units = (int64_t)G * (ws->ldR / kScanUnit);
+    ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kNumSMs * 8, units));
+    A(dev_alloc(&ws->R, (size_t)2 * G * ws->ldR, acc));
+    A(dev_alloc(&ws->items, ws->cap_items, acc));
+    A(dev_alloc(&ws->rval, ws->cap_items, acc));
+    A(dev_alloc(&ws->part, (size_t)ws->part_blocks + 1, acc));
     A(dev_alloc(&ws->c_item, ws->cap_items, acc));
     A(dev_alloc(&ws->k_item, ws->cap_items, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
@@ -773,9 +807,10 @@ int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
     if (rc == AGP_OK && cudaMallocHost((void **)&ws->h_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = fail(AGP_ENOMEM, "cudaMallocHost");
     if (rc == AGP_OK && cudaMallocHost((void **)&ws->h_lanes, sizeof(LaneParam) * G) != cudaSuccess) rc = fail(AGP_ENOMEM, "cudaMallocHost");
     if (rc == AGP_OK) {
-        cudaError_t e = cudaMemset(ws->R, 0, sizeof(float) * (size_t)2 * G * n);
+        cudaError_t e = cudaMemset(ws->R, 0, sizeof(float) * (size_t)2 * G * ws->ldR);
         if (e == cudaSuccess) e = cudaMemset(ws->level, 0xff, sizeof(int32_t) * G);
         if (e == cudaSuccess) e = cudaMemset(ws->ctrl, 0, sizeof(Ctrl));
+        if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(LaneStats) * G);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = fail(AGP_ECUDA, std::string("workspace init: ") + cudaGetErrorString(e));
     }
@@ -784,8 +819,36 @@ int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
         return rc;
     }
     ws->bytes = acc;
-    g->ws = ws;
     *out = ws;
+    return AGP_OK;
+}
+
+// A wave that failed part-way may leave residues or frontier bits behind; its buffers are freed
+// so that the next call starts from freshly zeroed ones.
+void drop_workspace(agp_graph_s *g)
+{
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    free_workspace(g->ws);
+    g->ws = nullptr;
+}
+
+int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
+{
+    int by_budget = 0;
+    AGP_TRY(lanes_for_budget(g, g->ws ? (int64_t)g->ws->bytes : 0, &by_budget));
+    const int G = std::max(1, std::min(lanes_wanted, by_budget));
+    if (g->ws && g->ws->G >= G) {
+        *out = g->ws;
+        return AGP_OK;
+    }
+    if (g->ws) {
+        AGP_CUDA_TRY(cudaDeviceSynchronize());
+        free_workspace(g->ws);
+        g->ws = nullptr;
+    }
+    AGP_TRY(create_workspace(g, G, &g->ws));
+    *out = g->ws;
     return AGP_OK;
 }
 
@@ -813,9 +876,13 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.ubits = g->ubits;
     A.umask = (g->ubits >= 32) ? 0xffffffffu : ((1u << g->ubits) - 1u);
     A.R = ws->R;
-    A.par_stride = (size_t)ws->G * (size_t)std::max<int64_t>(g->n, 1);
-    A.items0 = ws->items[0];
-    A.items1 = ws->items[1];
+    A.par_stride = (size_t)ws->G * (size_t)ws->ldR;
+    A.items = ws->items;
+    A.rval = ws->rval;
+    A.ldR = ws->ldR;
+    A.units = ws->ldR / kScanUnit;
+    A.part = ws->part;
+    A.part_blocks = ws->part_blocks;
     A.c_item = ws->c_item;
     A.k_item = ws->k_item;
     A.det_rec = ws->det_rec;
@@ -837,26 +904,39 @@ int ensure_events(Workspace *ws)
 {
     if (ws->ev_ready) return AGP_OK;
     for (int l = 0; l < kMaxLevels; ++l)
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kProfKernels; ++k)
             for (int e = 0; e < 2; ++e) AGP_CUDA_TRY(cudaEventCreate(&ws->ev[l][k][e]));
     ws->ev_ready = true;
     return AGP_OK;
 }
 
-// One level: expand, push, sample, level end. With `ev` (profiling) every kernel is bracketed by
-// event records on the same stream.
-void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,
-                  cudaEvent_t (*ev)[2] = nullptr)
+// Frontier compaction: bitmaps of the lanes -> ascending item list, size in ctrl->n_items.
+void launch_compact(const KArgs &A, cudaStream_t s)
 {
-    if (ev) cudaEventRecord(ev[0][0], s);
+    k_compact_count<<<A.part_blocks, kBlock, 0, s>>>(A);
+    k_compact_scan<<<1, 1024, 0, s>>>(A);
+    k_compact_emit<<<A.part_blocks, kBlock, 0, s>>>(A);
+}
+
+// One level: compact, expand, push, sample, level end. With `ev` (profiling) every step is
+// bracketed by event records on the same stream.
+void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,
+                  cudaEvent_t (*ev)[2])
+{
+    // External records become event nodes when captured into a graph (plain records during
+    // capture only express dependencies and never fire).
+    auto rec = [&](cudaEvent_t e) { cudaEventRecordWithFlags(e, s, cudaEventRecordExternal); };
+    if (ev) rec(ev[0][0]);
+    launch_compact(A, s);
+    if (ev) { rec(ev[0][1]); rec(ev[1][0]); }
     k_expand<<<expand_blocks, kBlock, 0, s>>>(A);
-    if (ev) { cudaEventRecord(ev[0][1], s); cudaEventRecord(ev[1][0], s); }
+    if (ev) { rec(ev[1][1]); rec(ev[2][0]); }
     k_push<<<push_blocks, kBlock, 0, s>>>(A);
-    if (ev) { cudaEventRecord(ev[1][1], s); cudaEventRecord(ev[2][0], s); }
+    if (ev) { rec(ev[2][1]); rec(ev[3][0]); }
     k_sample<<<sample_blocks, kBlock, 0, s>>>(A);
-    if (ev) { cudaEventRecord(ev[2][1], s); cudaEventRecord(ev[3][0], s); }
+    if (ev) { rec(ev[3][1]); rec(ev[4][0]); }
     k_level_end<<<1, kBlock, 0, s>>>(A);
-    if (ev) cudaEventRecord(ev[3][1], s);
+    if (ev) rec(ev[4][1]);
 }
 
 int blocks_for(unsigned long long work, int per_block)
@@ -869,8 +949,8 @@ int blocks_for(unsigned long long work, int per_block)
 void read_profile(agp_graph_s *g, Workspace *ws, int levels, const bool *ran)
 {
     for (int l = 0; l < levels; ++l)
-        for (int k = 0; k < 4; ++k) {
-            if (ran && !ran[l * 4 + k]) continue;
+        for (int k = 0; k < kProfKernels; ++k) {
+            if (ran && !ran[l * kProfKernels + k]) continue;
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ws->ev[l][k][0], ws->ev[l][k][1]) == cudaSuccess) {
                 g->prof_ms[k] += ms;
@@ -881,34 +961,89 @@ void read_profile(agp_graph_s *g, Workspace *ws, int levels, const bool *ran)
         }
 }
 
+// Capture `levels` consecutive levels (expand, push, sample, level end) into an executable graph.
+int capture_levels_ev(const KArgs &A, int levels, Workspace *ws_events, cudaGraphExec_t *out)
+{
+    cudaStream_t cs;
+    AGP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int lvl = 0; lvl < levels; ++lvl)
+            launch_level(A, cs, kGridStrideBlocks, kGridStrideBlocks, kGridStrideBlocks,
+                         ws_events ? ws_events->ev[lvl] : nullptr);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(out, graph, 0);
+        cudaGraphDestroy(graph);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(AGP_ECUDA, std::string("capturing the level loop: ") + cudaGetErrorString(e));
+    }
+    return AGP_OK;
+}
+
+int capture_levels(const KArgs &A, int levels, cudaGraphExec_t *out) { return capture_levels_ev(A, levels, nullptr, out); }
+
+void launch_coef(const CoefSpec *spec, const double *wts, float2 *coef, int nspec, cudaStream_t s)
+{
+    if (nspec > 0) k_coef<<<(nspec + 127) / 128, 128, 0, s>>>(spec, wts, coef, nspec);
+}
+
+void launch_seed_sources(const KArgs &A, const int32_t *lanes, const int32_t *sources, int count, cudaStream_t s)
+{
+    if (count > 0) k_seed_sources<<<blocks_for((unsigned long long)count, kBlock), kBlock, 0, s>>>(A, lanes, sources, count);
+}
+
+void launch_colnorms_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ldx, double *norms, cudaStream_t s)
+{
+    if (n <= 0 || d <= 0) return;
+    const int64_t rows_per_block = std::max<int64_t>(64, (n + kGridStrideBlocks - 1) / kGridStrideBlocks);
+    k_colnorms_bf16<<<(int)((n + rows_per_block - 1) / rows_per_block), kBlock, 0, s>>>(X, n, d, ldx, rows_per_block, norms);
+}
+
+void launch_seed_dense_bf16(const KArgs &A, const uint16_t *X, int64_t ldx, const int32_t *lane_of,
+                            const int32_t *col_of, const int32_t *part_of, const double *norms, int nl, cudaStream_t s)
+{
+    if (nl > 0) k_seed_dense_bf16<<<kGridStrideBlocks, kBlock, 0, s>>>(A, X, ldx, lane_of, col_of, part_of, norms, nl);
+}
+
 // Run the levels of the current wave (lanes already seeded, level 0 frontier in items[cur]).
 int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool plain, bool profile, cudaStream_t s)
 {
     if (profile) AGP_TRY(ensure_events(ws));
     if (plain) {
-        bool ran[kMaxLevels * 4] = {};
+        bool ran[kMaxLevels * kProfKernels] = {};
         int levels = 0;
         for (int lvl = 0; lvl <= max_L; ++lvl) {
-            AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-            AGP_CUDA_TRY(cudaStreamSynchronize(s));
-            const unsigned long long items = std::min(ws->h_ctrl->n_items[ws->h_ctrl->cur], ws->cap_items);
-            if (items == 0) break;
             auto rec = [&](int k, int e) { if (profile) cudaEventRecord(ws->ev[lvl][k][e], s); };
             rec(0, 0);
-            k_expand<<<blocks_for(items, kBlock), kBlock, 0, s>>>(A);
+            launch_compact(A, s);
             rec(0, 1);
-            ran[lvl * 4 + 0] = true;
+            ran[lvl * kProfKernels + 0] = true;
+            levels = lvl + 1;
+            AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+            AGP_CUDA_TRY(cudaStreamSynchronize(s));
+            g->kernel_launches += 3;
+            const unsigned long long items = std::min(ws->h_ctrl->n_items, ws->cap_items);
+            if (items == 0) break;
+            rec(1, 0);
+            k_expand<<<blocks_for(items, kBlock), kBlock, 0, s>>>(A);
+            rec(1, 1);
+            ran[lvl * kProfKernels + 1] = true;
             AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
             AGP_CUDA_TRY(cudaStreamSynchronize(s));
             const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det), ns = std::min(ws->h_ctrl->n_smp, ws->cap_smp);
             g->kernel_launches += 2 + (nd ? 1 : 0) + (ns ? 1 : 0);
-            if (nd) { rec(1, 0); k_push<<<blocks_for(nd, kBlock / 32), kBlock, 0, s>>>(A); rec(1, 1); ran[lvl * 4 + 1] = true; }
-            if (ns) { rec(2, 0); k_sample<<<blocks_for(ns, kBlock), kBlock, 0, s>>>(A); rec(2, 1); ran[lvl * 4 + 2] = true; }
-            rec(3, 0);
+            if (nd) { rec(2, 0); k_push<<<blocks_for(nd, kBlock / 32), kBlock, 0, s>>>(A); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
+            if (ns) { rec(3, 0); k_sample<<<blocks_for(ns, kBlock), kBlock, 0, s>>>(A); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
+            rec(4, 0);
             k_level_end<<<1, kBlock, 0, s>>>(A);
-            rec(3, 1);
-            ran[lvl * 4 + 3] = true;
-            levels = lvl + 1;
+            rec(4, 1);
+            ran[lvl * kProfKernels + 4] = true;
             AGP_CUDA_TRY(cudaGetLastError());
         }
         if (profile) {
@@ -922,30 +1057,13 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             cudaGraphExecDestroy(ws->graph);
             ws->graph = nullptr;
         }
-        cudaStream_t cs;
-        AGP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            for (int lvl = 0; lvl <= max_L; ++lvl)
-                launch_level(A, cs, kGridStrideBlocks, kGridStrideBlocks, kGridStrideBlocks, profile ? ws->ev[lvl] : nullptr);
-            e = cudaStreamEndCapture(cs, &graph);
-        }
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(&ws->graph, graph, 0);
-            cudaGraphDestroy(graph);
-        }
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) {
-            ws->graph = nullptr;
-            return fail(AGP_ECUDA, std::string("capturing the level loop: ") + cudaGetErrorString(e));
-        }
+        AGP_TRY(capture_levels_ev(A, max_L + 1, profile ? ws : nullptr, &ws->graph));
         ws->graph_levels = max_L;
         ws->graph_collect = A.collect;
         ws->graph_profile = (int)profile;
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
-    g->kernel_launches += 4 * (max_L + 1);
+    g->kernel_launches += 7 * (max_L + 1);
     if (profile) {
         AGP_CUDA_TRY(cudaStreamSynchronize(s));
         read_profile(g, ws, max_L + 1, nullptr);
@@ -970,8 +1088,8 @@ struct LaneSpec {
 };
 
 int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lanes, size_t first, int count,
-                 const agp_params_t *params, uint64_t stream_base_is_query, cudaStream_t s,
-                 std::vector<CoefSpec> &cs, std::vector<double> &wts, int *max_L)
+                 const agp_params_t *params, uint64_t stream_base_is_query, float *out, int64_t su, int64_t sr,
+                 cudaStream_t s, std::vector<CoefSpec> &cs, std::vector<double> &wts, int *max_L)
 {
     cs.assign(count, CoefSpec{});
     wts.clear();
@@ -989,8 +1107,11 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
         P.b_mode = exponent_mode(p.b);
         P.L = p.L;
         P.out_row = ls.query;
+        P.out = out + (int64_t)ls.query * sr;
+        P.su = su;
         lane_key(p.seed, stream_base_is_query ? (uint64_t)ls.query : 0ull, ls.part, P.key0, P.key1);
         CoefSpec &c = cs[l];
+        c.lane = l;
         c.kind = p.kind;
         c.L = p.L;
         c.param = p.param;
@@ -1011,7 +1132,7 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
     AGP_CUDA_TRY(cudaMemcpyAsync(ws->lanes, ws->h_lanes, sizeof(LaneParam) * count, cudaMemcpyHostToDevice, s));
     AGP_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), cs_bytes, cudaMemcpyHostToDevice, s));
     if (!wts.empty()) AGP_CUDA_TRY(cudaMemcpyAsync(d_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, s));
-    k_coef<<<(count + 127) / 128, 128, 0, s>>>(d_cs, d_w, ws->coef, count);
+    launch_coef(d_cs, d_w, ws->coef, count, s);
     // all wave lanes start at level 0, the other lanes idle
     std::vector<int32_t> lv(ws->G, -1);
     for (int l = 0; l < count; ++l) lv[l] = 0;
@@ -1022,13 +1143,11 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
     return AGP_OK;
 }
 
-int set_ctrl(Workspace *ws, float *out, int64_t su, int64_t sr, cudaStream_t s)
+int reset_ctrl(Workspace *ws, int lanes_used, cudaStream_t s)
 {
     Ctrl *h = ws->h_ctrl;
     std::memset(h, 0, sizeof(Ctrl));
-    h->od.out = out;
-    h->od.su = su;
-    h->od.sr = sr;
+    h->lanes_used = (unsigned int)lanes_used;
     AGP_CUDA_TRY(cudaMemcpyAsync(ws->ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     AGP_CUDA_TRY(cudaStreamSynchronize(s));
     return AGP_OK;
@@ -1052,8 +1171,6 @@ int collect_stats(Workspace *ws, const std::vector<LaneSpec> &lanes, size_t firs
     }
     return AGP_OK;
 }
-
-}  // namespace
 
 // ------------------------------------------------------------------------------------ queries
 int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q,
@@ -1135,7 +1252,7 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
         for (int part = 0; part < 2; ++part)
             if (norms[2 * q + part] > 0.0) lanes.push_back(LaneSpec{q, part, norms[2 * q + part], n_params == 1 ? 0 : q});
     Workspace *ws = nullptr;
-    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::max<size_t>(1, lanes.size()), &ws));
+    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<size_t>(std::max<size_t>(1, lanes.size()), (size_t)wave_lanes(g)), &ws));
 
     // --- output rows start at zero
     float *out = pi_out;
@@ -1150,22 +1267,26 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
 
     if (stats) std::memset(stats, 0, sizeof(agp_stats_t) * Q);
     const KArgs A = make_args(g, ws, collect);
-    const int G = plain ? 1 : ws->G;
+    const int G = plain ? 1 : std::min(ws->G, wave_lanes(g));
     std::vector<CoefSpec> cs;
     std::vector<double> wts;
     for (size_t first = 0; first < lanes.size(); first += G) {
         const int count = (int)std::min<size_t>(G, lanes.size() - first);
         int max_L = 0;
-        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 0, s, cs, wts, &max_L));
+        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 0, out, 1, ld, s, cs, wts, &max_L));
         std::vector<int32_t> map(2 * Q, -1);
         for (int l = 0; l < count; ++l) map[2 * lanes[first + l].query + lanes[first + l].part] = l;
         AGP_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), map_b, cudaMemcpyHostToDevice, s));
-        AGP_TRY(set_ctrl(ws, out, 1, ld, s));
+        AGP_TRY(reset_ctrl(ws, count, s));
         k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, s>>>(A, off_src, idx_src, val_src, Q, d_map, d_norm);
         g->kernel_launches += 2;  // coefficients + seed
         AGP_CUDA_TRY(cudaGetLastError());
-        AGP_TRY(run_levels(g, ws, A, max_L, plain, profile, s));
-        AGP_TRY(check_ctrl(ws, s));
+        int rc = run_levels(g, ws, A, max_L, plain, profile, s);
+        if (rc == AGP_OK) rc = check_ctrl(ws, s);
+        if (rc != AGP_OK) {
+            drop_workspace(g);
+            return rc;
+        }
         if (collect) AGP_TRY(collect_stats(ws, lanes, first, count, stats, s));
     }
     if (collect)
@@ -1191,7 +1312,7 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
     const bool plain = flags & AGP_PLAIN;
     const int64_t n = g->n;
     Workspace *ws = nullptr;
-    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>(2 * d, 4096), &ws));
+    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), &ws));
     // column norms of the sign parts
     const size_t norm_b = sizeof(double) * 2 * d, map_b = sizeof(int32_t) * 2 * 4096;
     AGP_TRY(grow(&g->in_stage, &g->in_bytes, norm_b + 2 * map_b + 512));
@@ -1199,8 +1320,7 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
     int32_t *d_col = (int32_t *)((char *)g->in_stage + (norm_b + 255) / 256 * 256);
     int32_t *d_part = d_col + 4096;
     AGP_CUDA_TRY(cudaMemsetAsync(d_norm, 0, norm_b, s));
-    const int64_t rows_per_block = std::max<int64_t>(64, (n + kGridStrideBlocks - 1) / kGridStrideBlocks);
-    k_colnorms_bf16<<<(int)((n + rows_per_block - 1) / rows_per_block), kBlock, 0, s>>>(X, n, d, ldx, rows_per_block, d_norm);
+    launch_colnorms_bf16(X, n, d, ldx, d_norm, s);
     g->kernel_launches += 1;
     AGP_CUDA_TRY(cudaGetLastError());
     std::vector<double> norms(2 * d);
@@ -1212,23 +1332,27 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
         for (int part = 0; part < 2; ++part)
             if (norms[2 * c + part] > 0.0) lanes.push_back(LaneSpec{(int)c, part, norms[2 * c + part], 0});
     const KArgs A = make_args(g, ws, 0);
-    const int G = plain ? 1 : std::min(ws->G, 4096);
+    const int G = plain ? 1 : std::min({ws->G, 4096, wave_lanes(g)});
     std::vector<CoefSpec> cs;
     std::vector<double> wts;
     for (size_t first = 0; first < lanes.size(); first += G) {
         const int count = (int)std::min<size_t>(G, lanes.size() - first);
         int max_L = 0;
-        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 1, s, cs, wts, &max_L));
+        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 1, Z, ldz, 1, s, cs, wts, &max_L));
         std::vector<int32_t> col(count), part(count);
         for (int l = 0; l < count; ++l) { col[l] = lanes[first + l].query; part[l] = lanes[first + l].part; }
         AGP_CUDA_TRY(cudaMemcpyAsync(d_col, col.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
         AGP_CUDA_TRY(cudaMemcpyAsync(d_part, part.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
-        AGP_TRY(set_ctrl(ws, Z, ldz, 1, s));
-        k_seed_dense_bf16<<<kGridStrideBlocks, kBlock, 0, s>>>(A, X, ldx, d_col, d_part, d_norm, count);
+        AGP_TRY(reset_ctrl(ws, count, s));
+        launch_seed_dense_bf16(A, X, ldx, nullptr, d_col, d_part, d_norm, count, s);
         g->kernel_launches += 2;  // coefficients + seed
         AGP_CUDA_TRY(cudaGetLastError());
-        AGP_TRY(run_levels(g, ws, A, max_L, plain, profile, s));
-        AGP_TRY(check_ctrl(ws, s));
+        int rc = run_levels(g, ws, A, max_L, plain, profile, s);
+        if (rc == AGP_OK) rc = check_ctrl(ws, s);
+        if (rc != AGP_OK) {
+            drop_workspace(g);
+            return rc;
+        }
     }
     return AGP_OK;
 }

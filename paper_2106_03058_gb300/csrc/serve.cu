@@ -1,0 +1,665 @@
+// serve.cu -- continuous-batching server: admission into lanes, shared level sweeps, completion.
+//
+// The server owns a lane workspace (its "slots") and a host thread that drives the device on the
+// server's stream. One sweep = one level of Algorithm 2 for every admitted lane (the captured
+// expand/push/sample/level-end graph); lanes carry their own level, coefficients, L and random key,
+// so requests admitted at different times share sweeps. Between sweeps the thread
+//   1. admits queued requests (FIFO) while free slots and result memory allow, seeds them into the
+//      current frontier and starts them at level 0,
+//   2. runs one sweep,
+//   3. reads the lanes' levels back; a lane whose level became -1 has reserved its last level, and
+//      a request whose lanes are all finished completes (its result is copied to the host first
+//      when results live there).
+// Waits of host threads on results are bounded by the caller's timeout.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "lanes.cuh"
+
+namespace agp {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_us()
+{
+    return std::chrono::duration<double, std::micro>(Clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    agp_request_t r{};
+    std::vector<double> w;          // FINITE weights (copied)
+    std::vector<uint16_t> X;        // feature block (copied)
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int status = AGP_OK;
+    bool done = false, cancelled = false, released = false, cut = false, counted = false;
+    int lanes_left = 0;
+    std::vector<int> slots;
+    float *d_out = nullptr;         // device result (n or n * cols floats)
+    float *h_out = nullptr;         // pinned host copy when results live on the host
+    size_t bytes = 0;
+};
+
+}  // namespace
+}  // namespace agp
+
+struct agp_server_s {
+    agp_graph_s *g = nullptr;
+    agp_serve_config_t cfg{};
+    agp::Workspace *ws = nullptr;
+    agp::KArgs A{};
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t sweep = nullptr;
+    std::thread th;
+    std::mutex m;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<agp::Request *> queue;
+    std::unordered_map<uint64_t, agp::Request *> all;
+    std::vector<agp::Request *> slot_owner;
+    std::vector<int> free_slots;
+    std::vector<int32_t> h_level;
+    int64_t result_bytes = 0;
+    int64_t completed = 0, sweeps = 0;
+    int active_lanes = 0;
+    // device staging for seeds
+    int32_t *d_seed_lane = nullptr, *d_seed_src = nullptr;
+    agp::CoefSpec *d_spec = nullptr;
+    double *d_w = nullptr;
+    size_t d_w_cap = 0;
+    uint16_t *d_X = nullptr;
+    size_t d_X_cap = 0;
+    double *d_norm = nullptr;
+    int32_t *d_col = nullptr, *d_part = nullptr, *d_lane_of = nullptr;
+    int fatal = AGP_OK;
+};
+
+namespace agp {
+namespace {
+
+constexpr int kMaxCols = 1024;
+
+void finish(agp_server_s *S, Request *q, int status)
+{
+    q->status = status;
+    q->done = true;
+    q->t_done = now_us();
+    ++S->completed;
+    S->cv_done.notify_all();
+}
+
+int alloc_result(agp_server_s *S, Request *q)
+{
+    const int64_t n = S->g->n;
+    const size_t elems = (size_t)n * (size_t)(q->r.source >= 0 ? 1 : q->r.cols);
+    q->bytes = std::max<size_t>(elems * sizeof(float), 16);
+    if (cudaMalloc((void **)&q->d_out, q->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        q->d_out = nullptr;
+        return fail(AGP_ENOMEM, "server: result buffer");
+    }
+    if (S->cfg.results_on_host && cudaMallocHost((void **)&q->h_out, q->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(q->d_out);
+        q->d_out = nullptr;
+        q->h_out = nullptr;
+        return fail(AGP_ENOMEM, "server: pinned result buffer");
+    }
+    AGP_CUDA_TRY(cudaMemsetAsync(q->d_out, 0, q->bytes, S->stream));
+    return AGP_OK;
+}
+
+void free_result(Request *q)
+{
+    if (q->d_out) cudaFree(q->d_out);
+    if (q->h_out) cudaFreeHost(q->h_out);
+    q->d_out = nullptr;
+    q->h_out = nullptr;
+}
+
+// Fill lane `slot` for request q (column `col` / sign `part`, L1 norm `norm`); returns its CoefSpec.
+CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, double norm, int w_off)
+{
+    const agp_params_t &p = q->r.params;
+    LaneParam P{};
+    P.eps_d = p.eps;
+    P.eps = (float)p.eps;
+    P.a = (float)p.a;
+    P.b = (float)p.b;
+    P.a_d = p.a;
+    P.a_mode = exponent_mode(p.a);
+    P.b_mode = exponent_mode(p.b);
+    P.L = p.L;
+    P.out_row = col;
+    if (q->r.source >= 0) {
+        P.out = q->d_out;
+        P.su = 1;
+    } else {
+        P.out = q->d_out + col;
+        P.su = q->r.cols;
+    }
+    lane_key(p.seed, q->r.source >= 0 ? 0ull : (uint64_t)col, part, P.key0, P.key1);
+    S->ws->h_lanes[slot] = P;
+    CoefSpec c{};
+    c.lane = slot;
+    c.kind = p.kind;
+    c.L = p.L;
+    c.param = p.param;
+    c.w_off = w_off;
+    c.scale = (part ? -1.0 : 1.0) * norm;
+    return c;
+}
+
+// Admit queued requests while slots and result memory allow. Called by the server thread.
+int admit(agp_server_s *S)
+{
+    std::vector<Request *> take;
+    std::vector<int> cut;
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        // cancelled requests in flight: their lanes stop after the next sweep (L lowered to 0, so
+        // the lanes only reserve what they hold and finish)
+        for (int sl = 0; sl < (int)S->slot_owner.size(); ++sl) {
+            Request *q = S->slot_owner[sl];
+            if (q && q->cancelled && !q->cut) cut.push_back(sl);
+        }
+        for (int sl : cut) S->slot_owner[sl]->cut = true;
+        const double t = now_us();
+        while (!S->queue.empty()) {
+            Request *q = S->queue.front();
+            if (q->cancelled) { S->queue.pop_front(); finish(S, q, AGP_ECANCELED); continue; }
+            if (q->r.deadline_us > 0 && t - q->t_submit > (double)q->r.deadline_us) {
+                S->queue.pop_front();
+                finish(S, q, AGP_ETIMEDOUT);
+                continue;
+            }
+            const int need = q->r.source >= 0 ? 1 : 2 * q->r.cols;
+            const int64_t bytes = (int64_t)S->g->n * (q->r.source >= 0 ? 1 : q->r.cols) * (int64_t)sizeof(float);
+            if ((int)S->free_slots.size() < need) break;
+            if (S->result_bytes + bytes > S->cfg.result_budget && S->result_bytes > 0) break;
+            S->queue.pop_front();
+            q->t_admit = t;
+            q->slots.clear();
+            for (int k = 0; k < need; ++k) {
+                q->slots.push_back(S->free_slots.back());
+                S->free_slots.pop_back();
+            }
+            S->result_bytes += bytes;
+            q->counted = true;
+            take.push_back(q);
+        }
+    }
+    static const int32_t zero_L = 0;
+    for (int sl : cut)
+        AGP_CUDA_TRY(cudaMemcpyAsync(&S->ws->lanes[sl].L, &zero_L, sizeof(int32_t), cudaMemcpyHostToDevice, S->stream));
+    if (take.empty()) return AGP_OK;
+    std::vector<CoefSpec> specs;
+    std::vector<double> wts;
+    std::vector<int32_t> seed_lane, seed_src;
+    std::vector<int32_t> start;  // slots that start at level 0
+    std::vector<int> give_back;
+    for (Request *q : take) {
+        int w_off = 0;
+        if (q->r.params.kind == AGP_W_FINITE) {
+            w_off = (int)wts.size();
+            wts.insert(wts.end(), q->w.begin(), q->w.end());
+        }
+        int rc = alloc_result(S, q);
+        if (rc != AGP_OK) {
+            std::lock_guard<std::mutex> lk(S->m);
+            for (int sl : q->slots) S->free_slots.push_back(sl);
+            S->result_bytes -= (int64_t)q->bytes;
+            q->slots.clear();
+            finish(S, q, rc);
+            continue;
+        }
+        if (q->r.source >= 0) {
+            const int slot = q->slots[0];
+            specs.push_back(start_lane(S, q, slot, 0, 0, 1.0, w_off));
+            seed_lane.push_back(slot);
+            seed_src.push_back(q->r.source);
+            start.push_back(slot);
+            S->slot_owner[slot] = q;
+            q->lanes_left = 1;
+            continue;
+        }
+        // feature block: column norms of the sign parts decide which lanes run
+        const int cols = q->r.cols;
+        const bool x_dev = q->r.flags & AGP_REQ_X_ON_DEVICE;
+        const uint16_t *X = x_dev ? q->r.X : S->d_X;
+        const int64_t ldx = x_dev ? q->r.ldx : cols;
+        const size_t xb = x_dev ? 0 : sizeof(uint16_t) * (size_t)S->g->n * cols;
+        if (xb > S->d_X_cap) {
+            cudaFree(S->d_X);
+            S->d_X = nullptr;
+            S->d_X_cap = 0;
+            if (cudaMalloc((void **)&S->d_X, xb) != cudaSuccess) {
+                cudaGetLastError();
+                std::lock_guard<std::mutex> lk(S->m);
+                for (int sl : q->slots) S->free_slots.push_back(sl);
+                S->result_bytes -= (int64_t)q->bytes;
+                free_result(q);
+                finish(S, q, fail(AGP_ENOMEM, "server: feature staging"));
+                continue;
+            }
+            S->d_X_cap = xb;
+        }
+        if (!x_dev) {
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_X, q->X.data(), xb, cudaMemcpyHostToDevice, S->stream));
+            X = S->d_X;
+        }
+        AGP_CUDA_TRY(cudaMemsetAsync(S->d_norm, 0, sizeof(double) * 2 * cols, S->stream));
+        launch_colnorms_bf16(X, S->g->n, cols, ldx, S->d_norm, S->stream);
+        std::vector<double> norms(2 * cols);
+        AGP_CUDA_TRY(cudaMemcpyAsync(norms.data(), S->d_norm, sizeof(double) * 2 * cols, cudaMemcpyDeviceToHost, S->stream));
+        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+        std::vector<int32_t> lane_of, col_of, part_of;
+        size_t used = 0;
+        for (int c = 0; c < cols; ++c)
+            for (int part = 0; part < 2; ++part) {
+                if (!(norms[2 * c + part] > 0.0)) continue;
+                const int slot = q->slots[used++];
+                specs.push_back(start_lane(S, q, slot, c, part, norms[2 * c + part], w_off));
+                lane_of.push_back(slot);
+                col_of.push_back(c);
+                part_of.push_back(part);
+                start.push_back(slot);
+                S->slot_owner[slot] = q;
+            }
+        {
+            std::lock_guard<std::mutex> lk(S->m);
+            for (size_t k = used; k < q->slots.size(); ++k) give_back.push_back(q->slots[k]);
+            q->slots.resize(used);
+        }
+        q->lanes_left = (int)used;
+        if (used == 0) {
+            AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+            if (q->h_out) std::memset(q->h_out, 0, q->bytes);
+            std::lock_guard<std::mutex> lk(S->m);
+            finish(S, q, AGP_OK);
+            continue;
+        }
+        // parameters and coefficients must be on the device before the dense seed
+        for (size_t k = 0; k < lane_of.size(); ++k)
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->lanes + lane_of[k], S->ws->h_lanes + lane_of[k], sizeof(LaneParam),
+                                         cudaMemcpyHostToDevice, S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_lane_of, lane_of.data(), sizeof(int32_t) * lane_of.size(), cudaMemcpyHostToDevice, S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_col, col_of.data(), sizeof(int32_t) * col_of.size(), cudaMemcpyHostToDevice, S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_part, part_of.data(), sizeof(int32_t) * part_of.size(), cudaMemcpyHostToDevice, S->stream));
+        launch_seed_dense_bf16(S->A, X, ldx, S->d_lane_of, S->d_col, S->d_part, S->d_norm, (int)lane_of.size(), S->stream);
+        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));  // d_X and the seed staging are reused
+    }
+    if (!give_back.empty()) {
+        std::lock_guard<std::mutex> lk(S->m);
+        for (int sl : give_back) S->free_slots.push_back(sl);
+    }
+    if (!specs.empty()) {
+        // lane parameters, coefficients and levels
+        for (const CoefSpec &c : specs)
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->lanes + c.lane, S->ws->h_lanes + c.lane, sizeof(LaneParam),
+                                         cudaMemcpyHostToDevice, S->stream));
+        if (wts.size() > S->d_w_cap) {
+            cudaFree(S->d_w);
+            if (cudaMalloc((void **)&S->d_w, sizeof(double) * wts.size()) != cudaSuccess) {
+                cudaGetLastError();
+                S->d_w = nullptr;
+                S->d_w_cap = 0;
+                return fail(AGP_ENOMEM, "server: weight staging");
+            }
+            S->d_w_cap = wts.size();
+        }
+        if (!wts.empty()) AGP_CUDA_TRY(cudaMemcpyAsync(S->d_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_spec, specs.data(), sizeof(CoefSpec) * specs.size(), cudaMemcpyHostToDevice, S->stream));
+        launch_coef(S->d_spec, S->d_w, S->ws->coef, (int)specs.size(), S->stream);
+        const int32_t zero = 0;
+        for (int32_t sl : start)
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->level + sl, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, S->stream));
+        if (!seed_lane.empty()) {
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_seed_lane, seed_lane.data(), sizeof(int32_t) * seed_lane.size(), cudaMemcpyHostToDevice, S->stream));
+            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_seed_src, seed_src.data(), sizeof(int32_t) * seed_src.size(), cudaMemcpyHostToDevice, S->stream));
+            launch_seed_sources(S->A, S->d_seed_lane, S->d_seed_src, (int)seed_lane.size(), S->stream);
+        }
+        AGP_CUDA_TRY(cudaGetLastError());
+        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));  // host staging vectors go out of scope
+        S->active_lanes += (int)start.size();
+    }
+    return AGP_OK;
+}
+
+// Lanes whose level went to -1 are finished; complete requests whose lanes are all finished.
+int retire(agp_server_s *S)
+{
+    AGP_CUDA_TRY(cudaMemcpyAsync(S->h_level.data(), S->ws->level, sizeof(int32_t) * S->ws->G, cudaMemcpyDeviceToHost, S->stream));
+    AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+    std::vector<Request *> ready;
+    for (int sl = 0; sl < S->ws->G; ++sl) {
+        Request *q = S->slot_owner[sl];
+        if (!q || S->h_level[sl] >= 0) continue;
+        S->slot_owner[sl] = nullptr;
+        --S->active_lanes;
+        {
+            std::lock_guard<std::mutex> lk(S->m);
+            S->free_slots.push_back(sl);
+        }
+        if (--q->lanes_left == 0) ready.push_back(q);
+    }
+    for (Request *q : ready)
+        if (q->h_out) AGP_CUDA_TRY(cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, S->stream));
+    if (!ready.empty()) AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+    std::lock_guard<std::mutex> lk(S->m);
+    for (Request *q : ready) finish(S, q, q->cancelled ? AGP_ECANCELED : AGP_OK);
+    return AGP_OK;
+}
+
+void run_fifo_plain(agp_server_s *S, Request *q)
+{
+    int rc = alloc_result(S, q);
+    if (rc == AGP_OK) {
+        q->t_admit = now_us();
+        if (q->r.source >= 0) {
+            const int64_t off[2] = {0, 1};
+            rc = query_batch(S->g, &q->r.params, 1, 1, off, &q->r.source, nullptr, q->d_out, S->g->n,
+                             AGP_OUTPUT_ON_DEVICE | AGP_PLAIN, nullptr, S->stream);
+        } else if (q->r.flags & AGP_REQ_X_ON_DEVICE) {
+            rc = feature_propagate(S->g, &q->r.params, q->r.X, q->r.cols, q->r.ldx, q->d_out, q->r.cols, AGP_PLAIN,
+                                   S->stream);
+        } else {
+            const size_t xb = sizeof(uint16_t) * (size_t)S->g->n * q->r.cols;
+            if (xb > S->d_X_cap) {
+                cudaFree(S->d_X);
+                S->d_X_cap = 0;
+                if (cudaMalloc((void **)&S->d_X, xb) != cudaSuccess) {
+                    cudaGetLastError();
+                    S->d_X = nullptr;
+                    rc = fail(AGP_ENOMEM, "server: feature staging");
+                } else {
+                    S->d_X_cap = xb;
+                }
+            }
+            if (rc == AGP_OK && cudaMemcpyAsync(S->d_X, q->X.data(), xb, cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+                rc = fail(AGP_ECUDA, "server: feature copy");
+            if (rc == AGP_OK)
+                rc = feature_propagate(S->g, &q->r.params, S->d_X, q->r.cols, q->r.cols, q->d_out, q->r.cols, AGP_PLAIN,
+                                       S->stream);
+        }
+        if (rc == AGP_OK && q->h_out && cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, S->stream) != cudaSuccess)
+            rc = fail(AGP_ECUDA, "server: result copy");
+        if (cudaStreamSynchronize(S->stream) != cudaSuccess && rc == AGP_OK) rc = fail(AGP_ECUDA, "server: sync");
+    }
+    std::lock_guard<std::mutex> lk(S->m);
+    finish(S, q, q->cancelled ? AGP_ECANCELED : rc);
+}
+
+void server_main(agp_server_s *S)
+{
+    cudaSetDevice(S->g->device);
+    if (S->cfg.mode == AGP_SERVE_FIFO_PLAIN) {
+        while (true) {
+            Request *q = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(S->m);
+                S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+                if (S->stop) return;
+                q = S->queue.front();
+                S->queue.pop_front();
+                const double t = now_us();
+                if (q->cancelled) { finish(S, q, AGP_ECANCELED); continue; }
+                if (q->r.deadline_us > 0 && t - q->t_submit > (double)q->r.deadline_us) { finish(S, q, AGP_ETIMEDOUT); continue; }
+            }
+            run_fifo_plain(S, q);
+        }
+    }
+    while (true) {
+        {
+            std::unique_lock<std::mutex> lk(S->m);
+            if (S->stop) return;
+            if (S->active_lanes == 0 && S->queue.empty())
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || !S->queue.empty(); });
+            if (S->stop) return;
+        }
+        int rc = admit(S);
+        if (rc == AGP_OK && S->active_lanes > 0) {
+            if (cudaGraphLaunch(S->sweep, S->stream) != cudaSuccess) rc = fail(AGP_ECUDA, "server: sweep launch");
+            ++S->sweeps;
+            if (rc == AGP_OK) rc = retire(S);
+        }
+        if (rc != AGP_OK) {
+            // a device error ends the server: fail everything pending and in flight
+            std::lock_guard<std::mutex> lk(S->m);
+            S->fatal = rc;
+            for (auto &kv : S->all)
+                if (!kv.second->done) finish(S, kv.second, rc);
+            S->queue.clear();
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **out)
+{
+    if (!g || !out) return fail(AGP_EINVAL, "NULL argument");
+    *out = nullptr;
+    agp_serve_config_t c{};
+    if (cfg) c = *cfg;
+    if (c.mode != AGP_SERVE_BATCHED && c.mode != AGP_SERVE_FIFO_PLAIN) return fail(AGP_EINVAL, "unknown serve mode");
+    if (c.max_lanes < 0 || c.result_budget < 0) return fail(AGP_EINVAL, "negative limit");
+    if (c.result_budget == 0) c.result_budget = 4ll << 30;
+    AGP_CUDA_TRY(cudaSetDevice(g->device));
+    agp_server_s *S = new agp_server_s();
+    S->g = g;
+    int lanes = c.max_lanes > 0 ? c.max_lanes : std::min(lane_capacity(g), 8 * wave_lanes(g));
+    lanes = std::max(lanes, 2);
+    if (c.mode == AGP_SERVE_FIFO_PLAIN) lanes = 1;
+    c.max_lanes = lanes;
+    S->cfg = c;
+    int rc = create_workspace(g, lanes, &S->ws);
+    if (rc == AGP_OK && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) rc = fail(AGP_ECUDA, "server stream");
+    if (rc == AGP_OK) {
+        // every slot may hold work: the compaction scans all of them
+        const unsigned int used = (unsigned int)lanes;
+        if (cudaMemcpy(&S->ws->ctrl->lanes_used, &used, sizeof(used), cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fail(AGP_ECUDA, "server control block");
+    }
+    if (rc == AGP_OK) {
+        S->A = make_args(g, S->ws, 0);
+        rc = capture_levels(S->A, 1, &S->sweep);
+    }
+    auto dalloc = [&](void **p, size_t b) {
+        if (rc == AGP_OK && cudaMalloc(p, b) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(AGP_ENOMEM, "server staging");
+        }
+    };
+    dalloc((void **)&S->d_seed_lane, sizeof(int32_t) * lanes);
+    dalloc((void **)&S->d_seed_src, sizeof(int32_t) * lanes);
+    dalloc((void **)&S->d_spec, sizeof(CoefSpec) * lanes);
+    dalloc((void **)&S->d_norm, sizeof(double) * 2 * kMaxCols);
+    dalloc((void **)&S->d_col, sizeof(int32_t) * 2 * kMaxCols);
+    dalloc((void **)&S->d_part, sizeof(int32_t) * 2 * kMaxCols);
+    dalloc((void **)&S->d_lane_of, sizeof(int32_t) * 2 * kMaxCols);
+    if (rc != AGP_OK) {
+        serve_destroy(S);
+        return rc;
+    }
+    S->slot_owner.assign(lanes, nullptr);
+    S->h_level.assign(lanes, -1);
+    for (int sl = lanes - 1; sl >= 0; --sl) S->free_slots.push_back(sl);
+    S->th = std::thread(server_main, S);
+    *out = S;
+    return AGP_OK;
+}
+
+int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
+{
+    if (!S || !req || !ticket) return fail(AGP_EINVAL, "NULL argument");
+    AGP_TRY(validate_params(req->params));
+    const int64_t n = S->g->n;
+    if (req->source >= 0) {
+        if (req->source >= n) return fail(AGP_EINVAL, "source outside [0, n)");
+    } else {
+        if (req->cols < 1 || req->cols > kMaxCols) return fail(AGP_EINVAL, "feature request needs 1..1024 columns");
+        if (!req->X || req->ldx < req->cols) return fail(AGP_EINVAL, "feature request needs X and ldx >= cols");
+        if (S->cfg.mode == AGP_SERVE_BATCHED && 2 * req->cols > S->cfg.max_lanes)
+            return fail(AGP_EBUDGET, "feature request needs more lanes than the server has");
+    }
+    Request *q = new Request();
+    q->r = *req;
+    if (req->params.kind == AGP_W_FINITE) {
+        q->w.assign(req->params.w, req->params.w + req->params.L + 1);
+        q->r.params.w = nullptr;
+    }
+    if (req->flags & ~AGP_REQ_X_ON_DEVICE) {
+        delete q;
+        return fail(AGP_EINVAL, "unknown request flag");
+    }
+    if (req->source < 0 && !(req->flags & AGP_REQ_X_ON_DEVICE)) {
+        q->X.resize((size_t)n * req->cols);
+        for (int64_t u = 0; u < n; ++u)
+            std::memcpy(q->X.data() + (size_t)u * req->cols, req->X + (size_t)u * req->ldx, sizeof(uint16_t) * req->cols);
+        q->r.X = nullptr;
+    }
+    q->t_submit = now_us();
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        if (S->fatal != AGP_OK) {
+            delete q;
+            return fail(S->fatal, "server stopped after a device error");
+        }
+        q->ticket = S->next_ticket++;
+        S->all[q->ticket] = q;
+        S->queue.push_back(q);
+    }
+    S->cv_work.notify_one();
+    *ticket = q->ticket;
+    return AGP_OK;
+}
+
+static void fill_result(const agp_server_s *S, const Request *q, agp_result_t *out)
+{
+    out->status = q->status;
+    out->on_host = q->h_out ? 1 : 0;
+    out->pi = q->h_out ? q->h_out : q->d_out;
+    out->n = S->g->n;
+    out->cols = q->r.source >= 0 ? 1 : q->r.cols;
+    out->queue_us = q->t_admit > 0 ? q->t_admit - q->t_submit : q->t_done - q->t_submit;
+    out->latency_us = q->t_done - q->t_submit;
+}
+
+int serve_poll(agp_server_s *S, uint64_t ticket, agp_result_t *out)
+{
+    if (!S || !out) return fail(AGP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->m);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end() || it->second->released) return fail(AGP_EINVAL, "unknown ticket");
+    if (!it->second->done) return AGP_EAGAIN;
+    fill_result(S, it->second, out);
+    return AGP_OK;
+}
+
+int serve_wait(agp_server_s *S, uint64_t ticket, int64_t timeout_us, agp_result_t *out)
+{
+    if (!S || !out) return fail(AGP_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->m);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end() || it->second->released) return fail(AGP_EINVAL, "unknown ticket");
+    Request *q = it->second;
+    auto ready = [&] { return q->done; };
+    if (timeout_us < 0) {
+        S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        return AGP_ETIMEDOUT;
+    }
+    fill_result(S, q, out);
+    return AGP_OK;
+}
+
+int serve_release(agp_server_s *S, uint64_t ticket)
+{
+    if (!S) return fail(AGP_EINVAL, "NULL argument");
+    Request *q = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        auto it = S->all.find(ticket);
+        if (it == S->all.end()) return fail(AGP_EINVAL, "unknown ticket");
+        if (!it->second->done) return fail(AGP_EINVAL, "request still pending");
+        q = it->second;
+        S->all.erase(it);
+        if (q->counted) S->result_bytes -= (int64_t)(q->r.source >= 0 ? 1 : q->r.cols) * S->g->n * (int64_t)sizeof(float);
+    }
+    free_result(q);
+    delete q;
+    S->cv_work.notify_one();
+    return AGP_OK;
+}
+
+int serve_cancel(agp_server_s *S, uint64_t ticket)
+{
+    if (!S) return fail(AGP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->m);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(AGP_EINVAL, "unknown ticket");
+    Request *q = it->second;
+    if (q->done) return AGP_OK;
+    q->cancelled = true;  // the server thread stops its lanes before the next sweep
+    S->cv_work.notify_one();
+    return AGP_OK;
+}
+
+int serve_stats(agp_server_s *S, int64_t *completed, int64_t *sweeps, int32_t *lanes_active, int32_t *queued)
+{
+    if (!S) return fail(AGP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->m);
+    if (completed) *completed = S->completed;
+    if (sweeps) *sweeps = S->sweeps;
+    if (lanes_active) *lanes_active = S->active_lanes;
+    if (queued) *queued = (int32_t)S->queue.size();
+    return AGP_OK;
+}
+
+int serve_destroy(agp_server_s *S)
+{
+    if (!S) return AGP_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        for (auto &kv : S->all) {
+            if (!kv.second->done) finish(S, kv.second, AGP_ECANCELED);
+            free_result(kv.second);
+            delete kv.second;
+        }
+        S->all.clear();
+        S->queue.clear();
+    }
+    if (S->sweep) cudaGraphExecDestroy(S->sweep);
+    free_workspace(S->ws);
+    cudaFree(S->d_seed_lane);
+    cudaFree(S->d_seed_src);
+    cudaFree(S->d_spec);
+    cudaFree(S->d_w);
+    cudaFree(S->d_X);
+    cudaFree(S->d_norm);
+    cudaFree(S->d_col);
+    cudaFree(S->d_part);
+    cudaFree(S->d_lane_of);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    return AGP_OK;
+}
+
+}  // namespace agp

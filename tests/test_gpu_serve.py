@@ -1,0 +1,154 @@
+"""Continuous-batching server (agp_serve_*): every result is the same alone and in the mix.
+
+A request's lanes draw their random numbers from (seed, node, level, segment) counters, never from
+the batch they share sweeps with, so a result computed in the mix equals the same request run
+alone up to FP32 atomic summation order. The tolerance is 1e-5 of the result's largest entry, the
+same bar as the batched queries. At eps = 0 the served results are also checked against the FP64
+oracle (relative 1e-5 per entry).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import graphs as SG
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def agp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_03058_gb300 as agp
+    agp.lib()
+    return agp
+
+
+@pytest.fixture(scope="module")
+def graph(agp):
+    n = 16384
+    u, v = SG.rmat_edges(n, 131072, seed=20210604)
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    yield n, g, og, u, v
+    g.destroy()
+
+
+def _mixed_requests(agp, og, count, seed):
+    rng = np.random.default_rng(seed)
+    beta = 0.85 / oracle.power_lambda(og)
+    live = np.flatnonzero(og.deg > 0)
+    reqs = []
+    for k in range(count):
+        kind = k % 4
+        L = int(rng.integers(5, 21))
+        eps = float(rng.choice([1e-5, 1e-6, 1e-7]))
+        s = int(rng.choice(live))
+        if kind == 0:
+            p = agp.ppr(0.2, L, eps, seed=1000 + k)
+        elif kind == 1:
+            p = agp.katz(beta, L, eps, seed=1000 + k)
+        elif kind == 2:
+            p = agp.hkpr(5.0, L, eps, seed=1000 + k)
+        else:
+            p = agp.transition(min(L, 6), eps, seed=1000 + k)
+        reqs.append((p, s))
+    return reqs
+
+
+def _close(a, b, tol=1e-5):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = max(np.abs(b).max(), 1e-30)
+    return np.abs(a - b).max() <= tol * scale
+
+
+def test_mix_equals_alone(agp, graph):
+    n, g, og, _, _ = graph
+    reqs = _mixed_requests(agp, og, 48, 1)
+    with agp.Server(g, max_lanes=16) as srv:
+        tickets = [srv.submit(p, source=s) for p, s in reqs]
+        results = []
+        for t in tickets:
+            r = srv.wait(t, timeout_us=120_000_000)
+            assert r is not None and r.status == 0
+            results.append(srv.result_array(r).cpu().numpy())
+            srv.release(t)
+        st = srv.stats()
+        assert st["completed"] >= len(reqs) and st["sweeps"] > 0
+    for (p, s), got in zip(reqs, results):
+        alone, _ = agp.query_sources(g, p, [s])
+        assert _close(got, alone[0].cpu().numpy())
+
+
+def test_mix_exact_matches_oracle(agp, graph):
+    n, g, og, _, _ = graph
+    live = np.flatnonzero(og.deg > 0)
+    cases = [(agp.ppr(0.2, 12, 0.0), oracle.PPR, 12, 0.2, 0, 1), (agp.hkpr(3.0, 15, 0.0), oracle.HKPR, 15, 3.0, 0, 1),
+             (agp.transition(3, 0.0, a=0.5, b=0.5), oracle.TRANSITION, 3, 0.0, 0.5, 0.5)]
+    with agp.Server(g, max_lanes=8) as srv:
+        tickets = [(srv.submit(p, source=int(live[7 * i])), kind, L, prm, a, b, int(live[7 * i]))
+                   for i, (p, kind, L, prm, a, b) in enumerate(cases)]
+        for t, kind, L, prm, a, b, s in tickets:
+            r = srv.wait(t, timeout_us=60_000_000)
+            got = srv.result_array(r).cpu().numpy().astype(np.float64)
+            srv.release(t)
+            w, Y = oracle.tail_sums(kind, L, prm)
+            x = np.zeros(n); x[s] = 1.0
+            want = oracle.basic(og, a, b, L, w, Y, x)
+            assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-30)
+
+
+def test_feature_request_in_mix(agp, graph):
+    n, g, og, u, v = graph
+    X = torch.randn(n, 6, generator=torch.Generator().manual_seed(4)).to(torch.bfloat16).cuda()
+    pf = agp._params(0.5, 0.5, 6, agp.W_PPR, 0.1, eps=1e-6, seed=77)
+    reqs = _mixed_requests(agp, og, 12, 2)
+    with agp.Server(g, max_lanes=24) as srv:
+        ts = [srv.submit(p, source=s) for p, s in reqs[:6]]
+        tf = srv.submit(pf, X=X)
+        ts += [srv.submit(p, source=s) for p, s in reqs[6:]]
+        r = srv.wait(tf, timeout_us=120_000_000)
+        assert r.status == 0 and r.cols == 6
+        Zs = srv.result_array(r).cpu().numpy()
+        srv.release(tf)
+        for t in ts:
+            assert srv.wait(t, timeout_us=120_000_000).status == 0
+            srv.release(t)
+    Za = agp.feature_propagate(g, pf, X).cpu().numpy()
+    for c in range(6):
+        assert _close(Zs[:, c], Za[:, c])
+
+
+def test_cancel_deadline_and_release(agp, graph):
+    n, g, og, _, _ = graph
+    reqs = _mixed_requests(agp, og, 40, 3)
+    with agp.Server(g, max_lanes=2) as srv:
+        tickets = [srv.submit(p, source=s) for p, s in reqs]
+        late = srv.submit(reqs[0][0], source=reqs[0][1], deadline_us=1)
+        srv.cancel(tickets[-1])
+        assert srv.wait(tickets[-1], timeout_us=60_000_000).status == 7      # AGP_ECANCELED
+        assert srv.wait(late, timeout_us=60_000_000).status == 6             # AGP_ETIMEDOUT
+        for t in tickets[:-1]:
+            r = srv.wait(t, timeout_us=120_000_000)
+            assert r is not None and r.status == 0
+            srv.release(t)
+        with pytest.raises(agp.AgpError):
+            srv.release(10 ** 9)
+        with pytest.raises(agp.AgpError):
+            srv.submit(reqs[0][0], source=n)  # source outside the graph
+
+
+def test_fifo_plain_mode_matches(agp, graph):
+    n, g, og, _, _ = graph
+    reqs = _mixed_requests(agp, og, 8, 5)
+    with agp.Server(g, mode=agp.SERVE_FIFO_PLAIN, results_on_host=True) as srv:
+        ts = [srv.submit(p, source=s) for p, s in reqs]
+        for (p, s), t in zip(reqs, ts):
+            r = srv.wait(t, timeout_us=120_000_000)
+            assert r.status == 0 and r.on_host == 1
+            got = srv.result_array(r).numpy()
+            srv.release(t)
+            alone, _ = agp.query_sources(g, p, [s])
+            assert _close(got, alone[0].cpu().numpy())
