@@ -17,7 +17,9 @@ constexpr int kMinBlocks = 4;        // resident CTAs per SM the level kernels a
 constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
 constexpr float kLightSamples = 4.f; // tails expected to yield at most this many trials stay inline
 constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
-constexpr uint32_t kSampleTag = 0x53414D50u;
+constexpr float kDenseP = 0.125f;    // tails whose largest probability is >= this are sampled per position
+constexpr uint32_t kSampleTag = 0x53414D50u;  // Philox counter word of the skip sampler
+constexpr uint32_t kDenseTag = 0x44534E53u;   // Philox counter word of the per-position sampler
 
 struct LaneParam {
     double eps_d;     // eps (FP64) for the push/sample decision
@@ -35,12 +37,13 @@ struct LaneParam {
 
 struct LaneStats {
     unsigned long long frontier[kMaxLevels];
-    unsigned long long by_kernel[3][4];  // [expand, push, sample][det, drawn, accepted, unused]
+    unsigned long long by_kernel[3][4];  // [expand, push, sample][det, drawn, accepted, unused];
+                                         // push counts the per-position tail sampler too
 };
 
 struct Ctrl {
     unsigned long long n_items;  // frontier size of the current level (set by the compaction)
-    unsigned long long n_det, n_smp;
+    unsigned long long n_det, n_smp, n_dns;
     unsigned int error;          // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 16: bad level
     unsigned int lanes_used;     // lanes [0, lanes_used) hold work; the compaction scans only those
 };
@@ -62,8 +65,8 @@ struct KArgs {
     int part_blocks;          // compaction ranges (blocks)
     float *c_item;
     int2 *k_item;             // (prefix length, tail segment length)
-    uint2 *det_rec, *smp_rec;
-    unsigned long long cap_items, cap_det, cap_smp;
+    uint2 *det_rec, *smp_rec, *dns_rec;
+    unsigned long long cap_items, cap_det, cap_smp, cap_dns;
     const LaneParam *lanes;
     const float2 *coef;       // [G][kMaxLevels] (keep_i = scale * w_i/Y_i, push_i = Y_{i+1}/Y_i)
     int32_t *level;           // [G], -1 = idle
@@ -77,7 +80,7 @@ struct Workspace {
     int device = 0;
     int G = 0;
     int64_t n = 0;
-    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0;
+    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0, cap_dns = 0;
     float *R = nullptr;
     uint32_t *items = nullptr;
     float *rval = nullptr;
@@ -86,7 +89,7 @@ struct Workspace {
     int part_blocks = 1;
     float *c_item = nullptr;
     int2 *k_item = nullptr;
-    uint2 *det_rec = nullptr, *smp_rec = nullptr;
+    uint2 *det_rec = nullptr, *smp_rec = nullptr, *dns_rec = nullptr;
     LaneParam *lanes = nullptr;
     float2 *coef = nullptr;
     int32_t *level = nullptr;
@@ -118,7 +121,20 @@ struct CoefSpec {
     double scale;      // sign * ||x_part||_1 (the Y_0 factor is applied here)
 };
 
+// Where a query call takes its work buffers: the graph's own (ws == nullptr) or a fixed workspace
+// (the server's), with the staging buffer of its per-call inputs.
+struct ExecCtx {
+    Workspace *ws;
+    void **stage;
+    size_t *stage_bytes;
+};
+
 // ---- host helpers of propagate.cu shared with serve.cu -------------------------------------------
+int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_t n_params, int32_t Q,
+                    const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
+                    int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s);
+int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, const uint16_t *X, int64_t d,
+                          int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t s);
 int exponent_mode(double p);
 int validate_params(const agp_params_t &p);
 void lane_key(uint64_t seed, uint64_t stream, int part, uint32_t &k0, uint32_t &k1);

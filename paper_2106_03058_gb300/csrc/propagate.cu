@@ -354,12 +354,22 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
     }
     const int tail = d - k;
     int seglen = 0;
+    bool dense = false;
     if (tail > 0) {
         const float ce = (float)((double)c / P.eps_d);
         const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
         const float expect = p0 * (float)tail;  // upper bound on the trials reached
         if (expect <= kLightSamples) {
             sample_range(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, drawn, accepted, 0);
+        } else if (p0 >= kDenseP) {
+            // most positions are kept: one Bernoulli per position, by warps, coalesced colidx reads
+            dense = true;
+            const unsigned int nrec = (unsigned int)((tail + kChunk - 1) / kChunk);
+            const unsigned long long base = reserve_records(&ctrl->n_dns, nrec);
+            for (unsigned int t = 0; t < nrec; ++t) {
+                if (base + t < A.cap_dns) A.dns_rec[base + t] = make_uint2((uint32_t)idx, t);
+                else atomicOr(&ctrl->error, 8u);
+            }
         } else {
             int nseg = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
             nseg = max(nseg, 1);
@@ -372,7 +382,7 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
             }
         }
     }
-    if (k > kInlineDet || seglen > 0) {
+    if (k > kInlineDet || seglen > 0 || dense) {
         A.c_item[idx] = c;
         A.k_item[idx] = make_int2(k, seglen);
     }
@@ -390,13 +400,44 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
         expand_item(A, idx);
 }
 
+// Per-position subset sampling of tail positions [k + chunk * kChunk, ...) of a dense tail: every
+// position is an independent Bernoulli trial with its own probability p_v = (c / eps) / d_v^a. Lane
+// l takes positions 4 l .. 4 l + 3 of every 128, with the 4 uniforms of Philox block
+// (u, level, (position - k) / 4, kDenseTag).
+__device__ __forceinline__ void dense_tail_chunk(const KArgs &A, const LaneParam &P, float *Rn, int32_t u, int lvl,
+                                                 const int32_t *row, int k, int d, int chunk, float c, int lane_id,
+                                                 unsigned long long &drawn, unsigned long long &accepted)
+{
+    const float ce = (float)((double)c / P.eps_d);
+    const int r0 = chunk * kChunk, r1 = min(d - k, r0 + kChunk);
+    for (int rel = r0 + 4 * lane_id; rel < r1; rel += 128) {
+        const Philox4 q = philox4x32_10((uint32_t)u, (uint32_t)lvl, (uint32_t)(rel >> 2), kDenseTag, P.key0, P.key1);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (rel + t >= r1) break;
+            const int32_t v = row[k + rel + t];
+            const float p = (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
+            ++drawn;
+            if (u01_open(w[t]) < p) {
+                ++accepted;
+                push_to(Rn, v, P.eps);
+            }
+        }
+    }
+}
+
+// One warp per record: 512-edge chunks of long deterministic prefixes, then 512-position chunks of
+// dense tails.
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
 {
     const unsigned long long n_det = min(A.ctrl->n_det, A.cap_det);
+    const unsigned long long n_all = n_det + min(A.ctrl->n_dns, A.cap_dns);
     const int lane_id = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long rec = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; rec < n_det; rec += nwarps) {
-        const uint2 R = A.det_rec[rec];
+    for (unsigned long long rec = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; rec < n_all; rec += nwarps) {
+        const bool det = rec < n_det;
+        const uint2 R = det ? A.det_rec[rec] : A.dns_rec[rec - n_det];
         const uint32_t item = A.items[R.x];
         const int lane = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
@@ -405,14 +446,23 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
         const float c = A.c_item[R.x];
         const int k = A.k_item[R.x].x;
-        const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
-        for (int j = j0 + lane_id; j < j1; j += 32) {
-            const int32_t v = row[j];
-            const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
-            push_to(Rn, v, inc);
+        if (det) {
+            const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
+            for (int j = j0 + lane_id; j < j1; j += 32) {
+                const int32_t v = row[j];
+                const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
+                push_to(Rn, v, inc);
+            }
+            if (A.collect && lane_id == 0) atomicAdd(&A.stats[lane].by_kernel[1][0], (unsigned long long)(j1 - j0));
+        } else {
+            unsigned long long drawn = 0, accepted = 0;
+            dense_tail_chunk(A, P, Rn, u, lvl, row, k, A.g.deg[u], (int)R.y, c, lane_id, drawn, accepted);
+            if (A.collect) {
+                atomicAdd(&A.stats[lane].by_kernel[1][1], drawn);
+                atomicAdd(&A.stats[lane].by_kernel[1][2], accepted);
+            }
         }
-        if (A.collect && lane_id == 0) atomicAdd(&A.stats[lane].by_kernel[1][0], (unsigned long long)(j1 - j0));
     }
 }
 
@@ -453,6 +503,7 @@ __global__ void k_level_end(KArgs A)
     if (threadIdx.x == 0) {
         ctrl->n_det = 0;
         ctrl->n_smp = 0;
+        ctrl->n_dns = 0;
     }
 }
 
@@ -709,9 +760,9 @@ size_t bytes_per_lane(const agp_graph_s *g)
     const double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
     // R (2 x 4) + items (2 x 4) + c (4) + k (8) + chunk and segment records (8 + 8, with the
     // extra records of long rows) per (lane, node)
-    // R (2 x 4) + items (4) + r values (4) + c (4) + k (8) + chunk and segment records (8 + 8, with
-    // the extra records of long rows) per (lane, node)
-    return n * (8 + 4 + 4 + 4 + 8) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
+    // R (2 x 4) + items (4) + r values (4) + c (4) + k (8) + prefix-chunk, dense-tail-chunk and
+    // segment records (8 each, with the extra records of long rows) per (lane, node)
+    return n * (8 + 4 + 4 + 4 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
 int lane_capacity(const agp_graph_s *g)
@@ -737,6 +788,7 @@ void free_workspace(Workspace *ws)
     cudaFree(ws->k_item);
     cudaFree(ws->det_rec);
     cudaFree(ws->smp_rec);
+    cudaFree(ws->dns_rec);
     cudaFree(ws->lanes);
     cudaFree(ws->coef);
     cudaFree(ws->level);
@@ -785,6 +837,7 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     ws->cap_items = (unsigned long long)G * n;
     ws->cap_det = ws->cap_items + (unsigned long long)G * (unsigned long long)g->nnz / kChunk + 1;
     ws->cap_smp = ws->cap_items + (unsigned long long)G * (unsigned long long)g->nnz / kMinSeg + 1;
+    ws->cap_dns = ws->cap_det;
     size_t acc = 0;
     int rc = AGP_OK;
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
@@ -799,6 +852,7 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     A(dev_alloc(&ws->k_item, ws->cap_items, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
+    A(dev_alloc(&ws->dns_rec, ws->cap_dns, acc));
     A(dev_alloc(&ws->lanes, (size_t)G, acc));
     A(dev_alloc(&ws->coef, (size_t)G * kMaxLevels, acc));
     A(dev_alloc(&ws->level, (size_t)G, acc));
@@ -887,9 +941,11 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.k_item = ws->k_item;
     A.det_rec = ws->det_rec;
     A.smp_rec = ws->smp_rec;
+    A.dns_rec = ws->dns_rec;
     A.cap_items = ws->cap_items;
     A.cap_det = ws->cap_det;
     A.cap_smp = ws->cap_smp;
+    A.cap_dns = ws->cap_dns;
     A.lanes = ws->lanes;
     A.coef = ws->coef;
     A.level = ws->level;
@@ -1027,7 +1083,7 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             levels = lvl + 1;
             AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
             AGP_CUDA_TRY(cudaStreamSynchronize(s));
-            g->kernel_launches += 3;
+            __atomic_fetch_add(&g->kernel_launches, (int64_t)(3), __ATOMIC_RELAXED);
             const unsigned long long items = std::min(ws->h_ctrl->n_items, ws->cap_items);
             if (items == 0) break;
             rec(1, 0);
@@ -1036,8 +1092,9 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             ran[lvl * kProfKernels + 1] = true;
             AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
             AGP_CUDA_TRY(cudaStreamSynchronize(s));
-            const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det), ns = std::min(ws->h_ctrl->n_smp, ws->cap_smp);
-            g->kernel_launches += 2 + (nd ? 1 : 0) + (ns ? 1 : 0);
+            const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det) + std::min(ws->h_ctrl->n_dns, ws->cap_dns),
+                                     ns = std::min(ws->h_ctrl->n_smp, ws->cap_smp);
+            __atomic_fetch_add(&g->kernel_launches, (int64_t)(2 + (nd ? 1 : 0) + (ns ? 1 : 0)), __ATOMIC_RELAXED);
             if (nd) { rec(2, 0); k_push<<<blocks_for(nd, kBlock / 32), kBlock, 0, s>>>(A); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
             if (ns) { rec(3, 0); k_sample<<<blocks_for(ns, kBlock), kBlock, 0, s>>>(A); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
             rec(4, 0);
@@ -1063,7 +1120,7 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         ws->graph_profile = (int)profile;
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
-    g->kernel_launches += 7 * (max_L + 1);
+    __atomic_fetch_add(&g->kernel_launches, (int64_t)(7 * (max_L + 1)), __ATOMIC_RELAXED);
     if (profile) {
         AGP_CUDA_TRY(cudaStreamSynchronize(s));
         read_profile(g, ws, max_L + 1, nullptr);
@@ -1178,6 +1235,15 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
                 int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s)
 {
     if (!g) return fail(AGP_EINVAL, "graph is NULL");
+    ExecCtx ctx{nullptr, &g->in_stage, &g->in_bytes};
+    return query_batch_ctx(g, &ctx, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, stats, s);
+}
+
+int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_t n_params, int32_t Q,
+                    const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
+                    int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s)
+{
+    if (!g) return fail(AGP_EINVAL, "graph is NULL");
     if (Q < 0) return fail(AGP_EINVAL, "Q < 0");
     if (Q == 0) return AGP_OK;
     if (!params || !(n_params == 1 || n_params == Q)) return fail(AGP_EINVAL, "n_params must be 1 or Q");
@@ -1212,8 +1278,8 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
                  map_b = sizeof(int32_t) * 2 * Q;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t need = al(off_b) + al(idx_b) + al(val_b) + al(norm_b) + al(map_b) + al(sizeof(unsigned int));
-    AGP_TRY(grow(&g->in_stage, &g->in_bytes, need));
-    char *p = (char *)g->in_stage;
+    AGP_TRY(grow(ctx->stage, ctx->stage_bytes, need));
+    char *p = (char *)*ctx->stage;
     int64_t *d_off = (int64_t *)p; p += al(off_b);
     int32_t *d_idx = (int32_t *)p; p += al(idx_b);
     float *d_val = x_val ? (float *)p : nullptr; p += al(val_b);
@@ -1236,7 +1302,7 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
     AGP_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), s));
     if (total) {
         k_norms_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, s>>>(off_src, idx_src, val_src, Q, n, d_norm, d_bad);
-        g->kernel_launches += 1;
+        __atomic_fetch_add(&g->kernel_launches, (int64_t)(1), __ATOMIC_RELAXED);
     }
     AGP_CUDA_TRY(cudaGetLastError());
     std::vector<double> norms(2 * Q);
@@ -1251,8 +1317,8 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
     for (int q = 0; q < Q; ++q)
         for (int part = 0; part < 2; ++part)
             if (norms[2 * q + part] > 0.0) lanes.push_back(LaneSpec{q, part, norms[2 * q + part], n_params == 1 ? 0 : q});
-    Workspace *ws = nullptr;
-    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<size_t>(std::max<size_t>(1, lanes.size()), (size_t)wave_lanes(g)), &ws));
+    Workspace *ws = ctx->ws;
+    if (!ws) AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<size_t>(std::max<size_t>(1, lanes.size()), (size_t)wave_lanes(g)), &ws));
 
     // --- output rows start at zero
     float *out = pi_out;
@@ -1267,7 +1333,7 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
 
     if (stats) std::memset(stats, 0, sizeof(agp_stats_t) * Q);
     const KArgs A = make_args(g, ws, collect);
-    const int G = plain ? 1 : std::min(ws->G, wave_lanes(g));
+    const int G = plain ? 1 : std::min(ws->G, ctx->ws ? ws->G : wave_lanes(g));
     std::vector<CoefSpec> cs;
     std::vector<double> wts;
     for (size_t first = 0; first < lanes.size(); first += G) {
@@ -1279,12 +1345,12 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
         AGP_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), map_b, cudaMemcpyHostToDevice, s));
         AGP_TRY(reset_ctrl(ws, count, s));
         k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, s>>>(A, off_src, idx_src, val_src, Q, d_map, d_norm);
-        g->kernel_launches += 2;  // coefficients + seed
+        __atomic_fetch_add(&g->kernel_launches, (int64_t)(2), __ATOMIC_RELAXED);  // coefficients + seed
         AGP_CUDA_TRY(cudaGetLastError());
         int rc = run_levels(g, ws, A, max_L, plain, profile, s);
         if (rc == AGP_OK) rc = check_ctrl(ws, s);
         if (rc != AGP_OK) {
-            drop_workspace(g);
+            if (!ctx->ws) drop_workspace(g);
             return rc;
         }
         if (collect) AGP_TRY(collect_stats(ws, lanes, first, count, stats, s));
@@ -1302,6 +1368,14 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d, int64_t ldx,
                       float *Z, int64_t ldz, uint32_t flags, cudaStream_t s)
 {
+    if (!g) return fail(AGP_EINVAL, "graph is NULL");
+    ExecCtx ctx{nullptr, &g->in_stage, &g->in_bytes};
+    return feature_propagate_ctx(g, &ctx, params, X, d, ldx, Z, ldz, flags, s);
+}
+
+int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, const uint16_t *X, int64_t d,
+                          int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t s)
+{
     if (!g || !params || !X || !Z) return fail(AGP_EINVAL, "NULL argument");
     if (d < 0 || ldx < d || ldz < d) return fail(AGP_EINVAL, "need d >= 0, ldx >= d, ldz >= d");
     if (flags & ~(AGP_PLAIN | AGP_PROFILE)) return fail(AGP_EINVAL, "unknown flag");
@@ -1311,17 +1385,17 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     const bool plain = flags & AGP_PLAIN;
     const int64_t n = g->n;
-    Workspace *ws = nullptr;
-    AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), &ws));
+    Workspace *ws = ctx->ws;
+    if (!ws) AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), &ws));
     // column norms of the sign parts
     const size_t norm_b = sizeof(double) * 2 * d, map_b = sizeof(int32_t) * 2 * 4096;
-    AGP_TRY(grow(&g->in_stage, &g->in_bytes, norm_b + 2 * map_b + 512));
-    double *d_norm = (double *)g->in_stage;
-    int32_t *d_col = (int32_t *)((char *)g->in_stage + (norm_b + 255) / 256 * 256);
+    AGP_TRY(grow(ctx->stage, ctx->stage_bytes, norm_b + 2 * map_b + 512));
+    double *d_norm = (double *)*ctx->stage;
+    int32_t *d_col = (int32_t *)((char *)*ctx->stage + (norm_b + 255) / 256 * 256);
     int32_t *d_part = d_col + 4096;
     AGP_CUDA_TRY(cudaMemsetAsync(d_norm, 0, norm_b, s));
     launch_colnorms_bf16(X, n, d, ldx, d_norm, s);
-    g->kernel_launches += 1;
+    __atomic_fetch_add(&g->kernel_launches, (int64_t)(1), __ATOMIC_RELAXED);
     AGP_CUDA_TRY(cudaGetLastError());
     std::vector<double> norms(2 * d);
     AGP_CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm, norm_b, cudaMemcpyDeviceToHost, s));
@@ -1332,7 +1406,7 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
         for (int part = 0; part < 2; ++part)
             if (norms[2 * c + part] > 0.0) lanes.push_back(LaneSpec{(int)c, part, norms[2 * c + part], 0});
     const KArgs A = make_args(g, ws, 0);
-    const int G = plain ? 1 : std::min({ws->G, 4096, wave_lanes(g)});
+    const int G = plain ? 1 : std::min({ws->G, 4096, ctx->ws ? ws->G : wave_lanes(g)});
     std::vector<CoefSpec> cs;
     std::vector<double> wts;
     for (size_t first = 0; first < lanes.size(); first += G) {
@@ -1345,12 +1419,12 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
         AGP_CUDA_TRY(cudaMemcpyAsync(d_part, part.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
         AGP_TRY(reset_ctrl(ws, count, s));
         launch_seed_dense_bf16(A, X, ldx, nullptr, d_col, d_part, d_norm, count, s);
-        g->kernel_launches += 2;  // coefficients + seed
+        __atomic_fetch_add(&g->kernel_launches, (int64_t)(2), __ATOMIC_RELAXED);  // coefficients + seed
         AGP_CUDA_TRY(cudaGetLastError());
         int rc = run_levels(g, ws, A, max_L, plain, profile, s);
         if (rc == AGP_OK) rc = check_ctrl(ws, s);
         if (rc != AGP_OK) {
-            drop_workspace(g);
+            if (!ctx->ws) drop_workspace(g);
             return rc;
         }
     }

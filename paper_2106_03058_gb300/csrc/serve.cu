@@ -79,6 +79,8 @@ struct agp_server_s {
     size_t d_X_cap = 0;
     double *d_norm = nullptr;
     int32_t *d_col = nullptr, *d_part = nullptr, *d_lane_of = nullptr;
+    void *fifo_stage = nullptr;  // input staging of the FIFO-plain path (never the graph's own)
+    size_t fifo_stage_bytes = 0;
     int fatal = AGP_OK;
 };
 
@@ -364,13 +366,15 @@ void run_fifo_plain(agp_server_s *S, Request *q)
     int rc = alloc_result(S, q);
     if (rc == AGP_OK) {
         q->t_admit = now_us();
+        // the server's own one-lane workspace and staging: the graph's buffers stay the caller's
+        ExecCtx ctx{S->ws, &S->fifo_stage, &S->fifo_stage_bytes};
         if (q->r.source >= 0) {
             const int64_t off[2] = {0, 1};
-            rc = query_batch(S->g, &q->r.params, 1, 1, off, &q->r.source, nullptr, q->d_out, S->g->n,
-                             AGP_OUTPUT_ON_DEVICE | AGP_PLAIN, nullptr, S->stream);
+            rc = query_batch_ctx(S->g, &ctx, &q->r.params, 1, 1, off, &q->r.source, nullptr, q->d_out, S->g->n,
+                                 AGP_OUTPUT_ON_DEVICE | AGP_PLAIN, nullptr, S->stream);
         } else if (q->r.flags & AGP_REQ_X_ON_DEVICE) {
-            rc = feature_propagate(S->g, &q->r.params, q->r.X, q->r.cols, q->r.ldx, q->d_out, q->r.cols, AGP_PLAIN,
-                                   S->stream);
+            rc = feature_propagate_ctx(S->g, &ctx, &q->r.params, q->r.X, q->r.cols, q->r.ldx, q->d_out, q->r.cols,
+                                       AGP_PLAIN, S->stream);
         } else {
             const size_t xb = sizeof(uint16_t) * (size_t)S->g->n * q->r.cols;
             if (xb > S->d_X_cap) {
@@ -387,8 +391,8 @@ void run_fifo_plain(agp_server_s *S, Request *q)
             if (rc == AGP_OK && cudaMemcpyAsync(S->d_X, q->X.data(), xb, cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
                 rc = fail(AGP_ECUDA, "server: feature copy");
             if (rc == AGP_OK)
-                rc = feature_propagate(S->g, &q->r.params, S->d_X, q->r.cols, q->r.cols, q->d_out, q->r.cols, AGP_PLAIN,
-                                       S->stream);
+                rc = feature_propagate_ctx(S->g, &ctx, &q->r.params, S->d_X, q->r.cols, q->r.cols, q->d_out, q->r.cols,
+                                           AGP_PLAIN, S->stream);
         }
         if (rc == AGP_OK && q->h_out && cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, S->stream) != cudaSuccess)
             rc = fail(AGP_ECUDA, "server: result copy");
@@ -657,6 +661,7 @@ int serve_destroy(agp_server_s *S)
     cudaFree(S->d_col);
     cudaFree(S->d_part);
     cudaFree(S->d_lane_of);
+    cudaFree(S->fifo_stage);
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
     return AGP_OK;

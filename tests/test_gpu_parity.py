@@ -248,13 +248,15 @@ def test_unbiased_variance_guarantee(agp, rmat14, case):
         assert np.all(fails <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / N))
 
 
-def test_sampler_star_binomial(agp):
-    """Star K_{1,N}, a = 0, one level: the number of sampled leaves is Binomial(N, p)."""
+@pytest.mark.parametrize("p", [0.02, 0.05, 0.3, 0.9])
+def test_sampler_star_binomial(agp, p):
+    """Star K_{1,N}, a = 0, one level: the number of sampled leaves is Binomial(N, p). p = 0.02 and
+    0.05 exercise the geometric-skip samplers (thread inline and segment records), p = 0.3 and 0.9
+    the per-position sampler of dense tails."""
     from scipy import stats
     leaves = 500
     n, src, dst = G.star(leaves)
     g = agp.build_graph(n, src, dst)
-    p = 0.05
     eps = (1.0 / leaves) / p
     N = 2000
     params = [agp.transition(1, eps, seed=k) for k in range(N)]
