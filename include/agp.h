@@ -293,6 +293,26 @@ AGP_API int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64
                              int reset);
 
 /*
+ * lambda_1 of A without any allocation. The paper has no counterpart: this is a deployment variant
+ * of agp_katz_beta's power iteration for callers that may not allocate device memory while they
+ * run (their device memory belongs to another allocator, or they avoid cudaMalloc/cudaFree
+ * because those synchronise the device). It reads a CSR owned by the caller and keeps its iterate
+ * vectors in a fixed array compiled into the library (64 MiB on every GPU that loads it, until the
+ * process exits); it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   n       number of nodes, 1 <= n <= 4194304 (larger graphs: AGP_EINVAL; use agp_katz_beta)
+ *   rowptr  device int64[n+1], colidx device int32[rowptr[n]] (undirected CSR as agp_graph_info
+ *           returns it); caller-owned, only read
+ *   iters, tol as agp_katz_beta; lambda1: host output
+ *   stream  the call enqueues on it and synchronises it every iteration
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls share the one array and each starts by
+ * re-initialising it, so calls that overlap on the GPU (other threads or streams) race: callers
+ * must serialise them.
+ */
+AGP_API int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int32_t iters,
+                                    double tol, double *lambda1, void *stream);
+
+/*
  * Threshold of the deterministic prefix (Algorithm 2 push condition, Section 4 pre-sorting):
  * for each t < count, k_out[t] = #{ j : c[t] / d_{v_j}^a >= eps } over the degree-sorted
  * N_{nodes[t]} = {v_1, ...}, with the comparison taken in FP64 from the FP32 value c[t]

@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
-    "feature_propagate", "katz_beta", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "feature_propagate", "katz_beta", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
     "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
@@ -110,6 +110,8 @@ def lib():
             L.agp_threshold.argtypes = [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp]
             L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
             L.agp_graph_set_wave_lanes.argtypes = [_vp, _i32]
+            L.agp_katz_lambda_noalloc.argtypes = [_i64, _vp, _vp, _i32, _dbl, C.POINTER(_dbl), _vp]
+            L.agp_katz_lambda_noalloc.restype = C.c_int
             L.agp_autotune.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _i32,
                                        C.POINTER(_i32), C.POINTER(_dbl), _vp]
             L.agp_serve_create.argtypes = [_vp, C.POINTER(ServeConfig), C.POINTER(_vp)]
@@ -432,6 +434,14 @@ def katz_beta(g, fraction=0.85, iters=1000, tol=1e-12, stream=None):
     _check("agp_katz_beta", lib().agp_katz_beta(g.handle, float(fraction), int(iters), float(tol), C.byref(beta),
                                                  C.byref(lam), _stream(stream)))
     return beta.value, lam.value
+
+
+def katz_lambda_noalloc(n, rowptr, colidx, iters=1000, tol=1e-12, stream=None):
+    """``agp_katz_lambda_noalloc``: lambda_1 of a caller-owned device CSR (CUDA tensors), no allocation."""
+    lam = _dbl()
+    _check("agp_katz_lambda_noalloc", lib().agp_katz_lambda_noalloc(int(n), rowptr.data_ptr(), colidx.data_ptr(), int(iters),
+                                                                     float(tol), C.byref(lam), _stream(stream)))
+    return lam.value
 
 
 def threshold(g, a, eps, nodes, c, k_out, stream=None):

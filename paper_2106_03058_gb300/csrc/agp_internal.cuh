@@ -115,6 +115,8 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
 void free_workspace(Workspace *ws);
 int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *beta,
               double *lambda1, cudaStream_t stream);
+int katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int iters, double tol,
+                        double *lambda1, cudaStream_t stream);
 int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t *nodes,
               const float *c, int32_t *k_out, cudaStream_t stream);
 int wave_lanes(const agp_graph_s *g);

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points of include/agp.h, error reporting and the Katz bound.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -110,6 +111,78 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
     if (!(lam > 0.0)) return fail(AGP_EINVAL, "graph has no edges (lambda_1 = 0)");
     if (lambda1) *lambda1 = lam;
     if (beta) *beta = fraction / lam;
+    return AGP_OK;
+}
+
+// ---- lambda_1 without allocations ----------------------------------------------------------------
+// Some callers cannot allocate device memory once they are running: processes whose device memory
+// is owned by another allocator (a framework's caching pool or a fixed arena that must account for
+// every byte), and latency-critical services that avoid cudaMalloc/cudaFree because those calls
+// synchronise the device and stall the other streams. For them, agp_katz_lambda_noalloc runs the
+// same FP64 power iteration as agp_katz_beta on a CSR the caller owns, with its two iterate vectors
+// and accumulators in the fixed device array below instead of freshly allocated buffers.
+//
+// The array is part of the loaded library: every GPU that loads it holds these 64 MiB until the
+// process exits. Host code must not use the symbol as an address (on the host it names a stand-in
+// variable); the device address is looked up once per device with cudaGetSymbolAddress.
+constexpr int64_t kNoAllocMaxNodes = 4194304;  // 2^22 nodes: x and y of 32 MiB each
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxNodes + 64];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[64] = {};  // device address of g_noalloc_scratch, per device ordinal
+
+// Called with `device` current. The first call on a device does the lookup.
+int noalloc_scratch(int device, double **out)
+{
+    if (device < 0 || device >= 64) return fail(AGP_EINVAL, "device ordinal outside [0, 64)");
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(AGP_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = (double *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return AGP_OK;
+}
+
+}  // namespace
+
+int katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int iters, double tol,
+                        double *lambda1, cudaStream_t s)
+{
+    if (n <= 0) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: n must be >= 1");
+    if (n > kNoAllocMaxNodes)
+        return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: n = " + std::to_string(n) +
+                                    " exceeds the fixed scratch of 4194304 nodes; use agp_katz_beta");
+    if (!rowptr || !colidx || !lambda1) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: NULL argument");
+    if (iters < 1 || !(tol >= 0.0)) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: need iters >= 1, tol >= 0");
+    int device = 0;
+    AGP_CUDA_TRY(cudaGetDevice(&device));
+    double *base = nullptr;
+    AGP_TRY(noalloc_scratch(device, &base));
+    double *x = base, *y = base + kNoAllocMaxNodes, *acc = base + 2 * kNoAllocMaxNodes;
+    DevGraph g{n, 0, rowptr, colidx, nullptr};
+    // the scratch keeps the previous call's contents: x is re-initialised, acc cleared per step
+    k_fill<<<kGridStrideBlocks, kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
+    AGP_CUDA_TRY(cudaGetLastError());
+    double lam = 0.0, prev = 0.0, h[2] = {0.0, 0.0};
+    for (int it = 0; it < iters; ++it) {
+        k_spmv_shift<<<kGridStrideBlocks, kBlock, 0, s>>>(g, x, y);
+        AGP_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 2, s));
+        k_dots<<<kGridStrideBlocks, kBlock, 0, s>>>(x, y, n, acc);
+        k_scale<<<kGridStrideBlocks, kBlock, 0, s>>>(y, x, n, acc);
+        AGP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        AGP_CUDA_TRY(cudaStreamSynchronize(s));
+        prev = lam;
+        lam = h[1] - 1.0;  // Rayleigh quotient of A + I at the unit iterate, minus the shift
+        if (it > 0 && std::fabs(lam - prev) <= tol * std::fabs(lam)) break;
+    }
+    if (!(lam > 0.0)) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: graph has no edges (lambda_1 = 0)");
+    *lambda1 = lam;
     return AGP_OK;
 }
 
@@ -251,6 +324,12 @@ int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64_t *kern
         g->kernel_launches = 0;
     }
     return AGP_OK;
+}
+
+int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int32_t iters, double tol,
+                            double *lambda1, void *stream)
+{
+    return agp::katz_lambda_noalloc(n, rowptr, colidx, iters, tol, lambda1, (cudaStream_t)stream);
 }
 
 int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes, const float *c,
