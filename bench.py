@@ -65,6 +65,38 @@ def make_edges(wl):
     return SG.cached("chunglu", SG.chung_lu_edges, wl["n"], wl["m"], 2.1, wl["seed_graph"])
 
 
+def atomic_ceiling(g, lanes, n, count=1 << 27, reps=5):
+    """Random FP32 atomic-add throughput (adds/s) into a buffer the size of one wave's residue
+    vectors (lanes x n floats, which fit in L2), measured with torch's index_add_ (a library scatter
+    kernel: one atomic add per element). Two target laws: uniform, and endpoints of uniformly drawn
+    edges (probability proportional to degree, as the pushes of a propagation land)."""
+    import torch
+    _, colidx, _ = g.csr()
+    lanes = max(int(lanes), 1)
+    size = lanes * n
+    buf = torch.zeros(size, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(S + 300)
+    vals = torch.full((count,), 1e-8, dtype=torch.float32, device="cuda")
+    targets = {"uniform": torch.randint(0, size, (count,), generator=gen, device="cuda")}
+    pos = torch.randint(0, colidx.numel(), (count,), generator=gen, device="cuda")
+    lane_of = torch.randint(0, lanes, (count,), generator=gen, device="cuda")
+    targets["degree_weighted"] = colidx[pos].long() + lane_of * n
+    del pos, lane_of
+    out = {}
+    for name, idx in targets.items():
+        for _ in range(2):
+            buf.index_add_(0, idx, vals)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            buf.index_add_(0, idx, vals)
+        e1.record()
+        e1.synchronize()
+        out[name] = count * reps / (e0.elapsed_time(e1) / 1e3)
+    return out
+
+
 def degree_weighted_sources(n, u, v, count, seed):
     deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
     p = deg / deg.sum()
@@ -235,6 +267,158 @@ def end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev):
     return e2e_value, h2d, d2h
 
 
+# ------------------------------------------------------------------------------- features
+def run_features(args):
+    """GNN feature propagation: every column of a BF16 feature matrix is a graph signal."""
+    import torch
+    import paper_2106_03058_gb300 as agp
+    n, m, d = 2_500_000, 60_000_000, 128
+    if args.small:
+        n, m, d = 16384, 131072, 32
+    u, v = SG.cached("rmat", SG.rmat_edges, n, m, S + 3)
+    g = agp.build_graph(n, u, v, add_self_loops=True)
+    X = torch.randn(n, d, generator=torch.Generator().manual_seed(S + 203)).to(torch.bfloat16).cuda()
+    Z = torch.empty((n, d), dtype=torch.float32, device="cuda")
+    eps = args.eps if args.eps > 0 else 1e-6
+    models = {"appnp": agp._params(0.5, 0.5, 10, agp.W_PPR, 0.1, eps=eps, seed=S + 7),
+              "sgc": agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=eps, seed=S + 8)}
+    # the accuracy / time trade-off of eps (the configuration's eps plus tighter ones and exact)
+    sweep_eps = [eps, eps / 10, eps / 100, 0.0] if not args.small else [eps, 0.0]
+    for name in ("appnp", "sgc"):
+        base = models[name]
+        for e in sweep_eps[1:]:
+            models[f"{name}_eps{e:g}"] = agp._params(0.5, 0.5, base.L, base.kind, base.param, eps=e, seed=base.seed)
+    out = {}
+    for name, p in models.items():
+        for _ in range(args.warmup):
+            agp.feature_propagate(g, p, X, Z)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            agp.feature_propagate(g, p, X, Z)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        out[name] = {"ms_per_matrix": ms, "columns_per_s": d / (ms / 1e3), "L": p.L}
+    # error of two sampled columns against the FP64 oracle (exact propagation of the same BF16 inputs)
+    if not args.no_cpu_baseline:
+        import oracle
+        og = oracle.build_csr(n, u, v, add_self_loops=True)
+        Xh = X[:, :2].float().cpu().numpy().astype(np.float64)
+        exact_cache = {}
+        for name, p in models.items():
+            agp.feature_propagate(g, p, X, Z)
+            Zh = Z[:, :2].cpu().numpy().astype(np.float64)
+            kind = oracle.PPR if p.kind == agp.W_PPR else oracle.TRANSITION
+            w, Y = oracle.tail_sums(kind, p.L, p.param)
+            errs = []
+            t0 = time.perf_counter()
+            for c in range(2):
+                key = (kind, p.L, c)
+                if key not in exact_cache:
+                    exact_cache[key] = oracle.basic(og, 0.5, 0.5, p.L, w, Y, Xh[:, c])
+                exact = exact_cache[key]
+                scale = np.abs(exact).sum()
+                errs.append({"rel_l1": float(np.abs(Zh[:, c] - exact).sum() / scale),
+                             "max_abs_over_max": float(np.abs(Zh[:, c] - exact).max() / np.abs(exact).max())})
+            out[name]["error_vs_fp64_oracle"] = errs
+            out[name]["oracle_s_per_column"] = (time.perf_counter() - t0) / 2
+    total_cols = 2 * d  # headline: the configuration's two models at the configuration's eps
+    total_ms = out["appnp"]["ms_per_matrix"] + out["sgc"]["ms_per_matrix"]
+    line = {"metric": "feature columns/s", "value": total_cols / (total_ms / 1e3), "unit": "columns/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16-in/f32", "data": "synthetic",
+            "config": {"workload": f"rmat n={n} m={m} + self-loops, X {n}x{d} bf16 N(0,1), eps={eps} per column part",
+                       "models": {k: {"a": 0.5, "b": 0.5, "L": models[k].L, "eps": models[k].eps} for k in models}},
+            "models": out}
+    print(json.dumps(line), flush=True)
+    g.destroy()
+
+
+# ------------------------------------------------------------------------------- large graph
+def run_large(args):
+    """Large single-source PPR and heat-kernel PPR: Chung-Lu exponent 2.0, 65M nodes, 1.8B edges
+    (a synthetic stand-in for Friendster), 64 uniform sources, eps = 1e-8, L = 30."""
+    import torch
+    import paper_2106_03058_gb300 as agp
+    n, m, Q = 65_000_000, 1_800_000_000, 64
+    if args.small:
+        n, m, Q = 1_000_000, 20_000_000, 16
+    t0 = time.perf_counter()
+    log(f"[large] drawing a Chung-Lu graph n={n} m={m} on the GPU")
+    u, v = SG.chung_lu_edges_cuda(n, m, 2.0, S + 4, log=log)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    torch.cuda.empty_cache()  # the builder allocates with cudaMalloc, outside torch's cache
+    deg_expected = torch.zeros(n, dtype=torch.int64, device="cuda")
+    for s0 in range(0, m, 1 << 28):  # chunks below 2^31 elements
+        deg_expected += torch.bincount(u[s0:s0 + (1 << 28)].long(), minlength=n)
+        deg_expected += torch.bincount(v[s0:s0 + (1 << 28)].long(), minlength=n)
+    log(f"[large] generated in {t_gen:.1f}s; building the CSR")
+    t0 = time.perf_counter()
+    g = agp.build_graph(n, u, v)
+    t_build = time.perf_counter() - t0
+    del u, v
+    torch.cuda.empty_cache()
+    log(f"[large] generated {m} edges in {t_gen:.1f}s, built the CSR (nnz={g.nnz}) in {t_build:.1f}s")
+    # structural checks at full size: degrees, row order by (degree, id), symmetry on sampled edges
+    rowptr, colidx, deg = g.csr()
+    checks = {"degrees_match_edge_list": bool(torch.equal(deg.long(), deg_expected)),
+              "rowptr_matches_degrees": bool(torch.equal(rowptr[1:] - rowptr[:-1], deg.long()))}
+    gen = torch.Generator().manual_seed(S + 104)
+    live = torch.nonzero(deg > 0).flatten().cpu()
+    rows = live[torch.randint(live.numel(), (512,), generator=gen)]
+    ok_sorted, ok_sym = True, True
+    for s_ in rows.tolist():
+        a, b = int(rowptr[s_]), int(rowptr[s_ + 1])
+        nb = colidx[a:b].long()
+        key = deg[nb].long() * n + nb
+        ok_sorted &= bool((key[1:] > key[:-1]).all()) and not bool((nb == s_).any())
+        t = int(nb[torch.randint(nb.numel(), (1,), generator=gen)].item())
+        ta, tb = int(rowptr[t]), int(rowptr[t + 1])
+        ok_sym &= bool((colidx[ta:tb] == s_).any())
+    checks["sampled_rows_sorted_no_loops"] = ok_sorted
+    checks["sampled_edges_symmetric"] = ok_sym
+    del rowptr, colidx, deg, deg_expected
+    torch.cuda.empty_cache()
+    srcs = live[torch.randint(live.numel(), (Q * (args.warmup + args.steps),), generator=gen)].to(torch.int32)
+    d_srcs = srcs.cuda()
+    off = torch.arange(Q + 1, dtype=torch.int64, device="cuda")
+    out = torch.empty((Q, n), dtype=torch.float32, device="cuda")
+    w_ppr = 1.0 - 0.8 ** 31
+    w_hk = float(sum(np.exp(-5.0) * 5.0 ** i / np.prod(np.arange(1, i + 1)) for i in range(31)))
+    flags = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
+    res = {}
+    for name, mk, mass in (("ppr", lambda sd: agp.ppr(0.2, 30, 1e-8, seed=sd), w_ppr),
+                           ("hkpr", lambda sd: agp.hkpr(5.0, 30, 1e-8, seed=sd), w_hk)):
+        times, masses = [], []
+        for k in range(args.warmup + args.steps):
+            params = [mk(S + 10000 * k + q) for q in range(Q)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            agp.query_batch(g, params, off, d_srcs[k * Q:(k + 1) * Q], None, out, n, flags)
+            e1.record()
+            e1.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+                masses.append(np.array([float(out[q].sum(dtype=torch.float64)) for q in range(Q)]))
+        ms = float(np.mean(times))
+        mm = np.concatenate(masses)
+        log(f"[large] {name}: {ms:.1f} ms per launch of {Q} queries")
+        res[name] = {"ms_per_launch": ms, "queries_per_s": Q / (ms / 1e3),
+                     "mass_expected": mass, "mass_mean": float(mm.mean()), "mass_std": float(mm.std())}
+    line = {"metric": "queries/s", "value": 2 * Q / ((res["ppr"]["ms_per_launch"] + res["hkpr"]["ms_per_launch"]) / 1e3),
+            "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"chung-lu-2.0 n={n} m={m} ppr(0.2)+hkpr(5), L=30, eps=1e-8, {Q} uniform sources per launch",
+                       "generate_s": t_gen, "build_s": t_build},
+            "checks": checks, "models": res,
+            "note": "a = 0, b = 1 keeps mass: E[sum pi] = sum_{i<=L} w_i for every source with degree >= 1"}
+    print(json.dumps(line), flush=True)
+    g.destroy()
+
+
 # ------------------------------------------------------------------------------- serving
 def serve_trace(n, u, v, rate, duration, seed, beta):
     """Seeded Poisson trace of the serving mix: PPR / Katz / HKPR / transition (22.5% each) and
@@ -280,9 +464,10 @@ def run_serve(args, wl):
             return agp.transition(L, eps, seed=seed)
         return agp._params(0.5, 0.5, L, agp.W_PPR, 0.1, eps=eps, seed=seed)
 
-    def replay(mode):
-        srv = agp.Server(g, mode=mode, max_lanes=args.lanes if args.lanes > 0 else 0)
+    def replay(mode, admission=agp.ADMIT_COST):
+        srv = agp.Server(g, mode=mode, max_lanes=args.lanes if args.lanes > 0 else 0, admission=admission)
         tickets = []
+        log(f"[serve] mode {mode}: replaying {len(trace)} requests over {args.duration}s")
         t0 = time.perf_counter()
         for (ta, kind, eps, L, src, cols, seed) in trace:
             dt = ta - (time.perf_counter() - t0)
@@ -305,19 +490,29 @@ def run_serve(args, wl):
             srv.release(tk)
         elapsed = min(time.perf_counter(), deadline) - t0
         st = srv.stats()
+        log(f"[serve] mode {mode}: {done} done in {elapsed:.1f}s, stats {st}; stopping the server")
+        for tk, _ in tickets:  # requests still queued are dropped, the running ones end their sweep
+            try:
+                srv.cancel(tk)
+            except Exception:
+                pass
         srv.destroy()
+        log(f"[serve] mode {mode}: stopped after {time.perf_counter() - t0:.1f}s")
         lat = np.array(lat) if lat else np.array([np.nan])
-        return {"offered": len(trace), "completed": done, "queries_per_s": done / elapsed,
+        return {"offered": len(trace), "completed": done, "incomplete": len(trace) - done, "queries_per_s": done / elapsed,
                 "p50_ms": float(np.nanpercentile(lat, 50)), "p99_ms": float(np.nanpercentile(lat, 99)),
                 "elapsed_s": elapsed, "submit_s": submitted_by, "sweeps": st["sweeps"]}
 
     batched = replay(agp.SERVE_BATCHED)
+    batched_fifo = replay(agp.SERVE_BATCHED, agp.ADMIT_FIFO)
     fifo = replay(agp.SERVE_FIFO_PLAIN) if not args.no_fifo else None
     line = {"metric": "served queries/s (continuous batching)", "value": batched["queries_per_s"], "unit": "queries/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"] + " | serving trace", "rate": args.rate, "duration_s": args.duration,
                        "drain_s": args.drain, "lambda_1": lam},
-            "batched": batched, "fifo_plain": fifo}
+            "batched": batched, "batched_fifo_admission": batched_fifo, "fifo_plain": fifo,
+            "note": "latency percentiles over the requests completed inside the window; 'incomplete' were still "
+                    "queued or running when it closed"}
     print(json.dumps(line), flush=True)
     g.destroy()
 
@@ -340,6 +535,9 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--drain", type=float, default=20.0)
     ap.add_argument("--no-fifo", action="store_true")
+    ap.add_argument("--features", action="store_true", help="GNN feature propagation workload")
+    ap.add_argument("--large", action="store_true", help="65M-node, 1.8B-edge PPR / HKPR workload")
+    ap.add_argument("--eps", type=float, default=0.0)
     args = ap.parse_args()
     wl = workload(args.small)
     if args.queries:
@@ -351,6 +549,10 @@ def main():
         return run_reference(args, wl, rank)
     if args.serve:
         return run_serve(args, wl)
+    if args.features:
+        return run_features(args)
+    if args.large:
+        return run_large(args)
 
     import torch
     import torch.distributed as dist
@@ -453,7 +655,7 @@ def main():
     bytes_k = {
         "compact": items * B_COMPACT_ITEM + scanned * B_SCAN,
         "expand": items * B_ITEM + work[0, 0] * B_DET + work[0, 1] * B_TRIAL + work[0, 2] * B_ACC,
-        "push": work[1, 0] * B_DET,
+        "push": work[1, 0] * B_DET + work[1, 1] * B_TRIAL + work[1, 2] * B_ACC,
         "sample": work[2, 1] * B_TRIAL + work[2, 2] * B_ACC,
     }
     dom = max(("compact", "expand", "push", "sample"), key=lambda k_: kern_ms[k_])
@@ -467,6 +669,17 @@ def main():
     else:
         peak, peak_src = HBM_FALLBACK_GBS, "fallback"
     edge_ops = work[:, 0].sum() + work[:, 2].sum()
+    # k_push is bound by random FP32 atomic adds into residue vectors that stay in L2, not by HBM:
+    # its adds per second against a library scatter-add of the same shape on this GPU
+    atomics = None
+    if rank == 0 and kern_ms["push"] > 0:
+        ceil = atomic_ceiling(g, lanes, n)
+        push_adds = (work[1, 0] + work[1, 2]) / args.steps
+        rate = push_adds / (kern_ms["push"] / args.steps / 1e3)
+        atomics = {"push_adds_per_step": push_adds, "push_adds_per_s": rate,
+                   "ceiling_adds_per_s": ceil, "frac_of_degree_weighted": rate / ceil["degree_weighted"],
+                   "note": "push time from CUDA events around every k_push of the timed steps, which "
+                           "include the other wave's kernels sharing the GPU (an upper bound on its time)"}
 
     # ---- plain path: one query per launch sequence, host-synchronised frontier sizes
     plain_qps = None
@@ -520,10 +733,17 @@ def main():
             "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)), "p99_step": float(np.percentile(step_ms, 99)),
                            "note": "a query's latency is its launch's completion time"},
             "edges_pushed_per_s": rank_reduce(edge_ops, "sum", world, dev) / (total_ms / 1e3),
+            "work_per_step": {"frontier_items": items / args.steps,
+                              "deterministic_pushes": float(work[:, 0].sum()) / args.steps,
+                              "sampler_trials": float(work[:, 1].sum()) / args.steps,
+                              "samples_accepted": float(work[:, 2].sum()) / args.steps,
+                              "by_kernel_det_trials_accepted": {k_: [float(x) / args.steps for x in work[i_, :3]]
+                                                                for i_, k_ in enumerate(("expand", "push", "sample"))}},
             "plain_path": plain_qps,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": bytes_k[dom] / launches, "avg_launch_ms": avg_ms},
+            "l2_atomics": atomics,
             "kernel_ms": kern_ms, "kernel_launches_profiled": kern_launches,
             "gpu_launches": int(total_launches),
             "clocks": clk,

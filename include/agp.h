@@ -213,12 +213,21 @@ typedef struct agp_server_s *agp_server_t;
 #define AGP_SERVE_BATCHED 0     /* continuous batching (default)                                     */
 #define AGP_SERVE_FIFO_PLAIN 1  /* baseline: one request at a time on the plain path, arrival order  */
 
+#define AGP_ADMIT_COST 0  /* cheapest estimated cost first, with aging (default)                     */
+#define AGP_ADMIT_FIFO 1  /* arrival order                                                           */
+
 typedef struct {
     int32_t mode;             /* AGP_SERVE_*                                                        */
-    int32_t max_lanes;        /* slots (lanes) in flight; 0 = the graph's automatic wave width x 8  */
+    int32_t max_lanes;        /* slots (lanes) in flight; 0 = max(8 x automatic wave width, 128)    */
     int64_t result_budget;    /* bytes of result buffers of admitted, unreleased requests; 0 = 4 GiB */
     int32_t results_on_host;  /* 1: results are copied to library-owned pinned host memory          */
-    int32_t reserved;
+    int32_t admission;        /* AGP_ADMIT_* (batched mode). The cost estimate is the bound of the
+                                 proof of Theorem 4.3, (1/eps) sum_{i=1..L} (Y_i/Y_0) ||P^i x||_1,
+                                 with the mass ||P^i x||_1 bounded per weight kind; a request's
+                                 priority is cost / (1 + seconds waited); requests above 1e8
+                                 estimated operations use at most 3/4 of the slots while another
+                                 such request holds slots; a request that has waited over 30 s is
+                                 admitted next, nothing else starting until its slots are free      */
 } agp_serve_config_t;
 
 #define AGP_REQ_X_ON_DEVICE 0x1u /* X is a device pointer that stays valid until the request is done */

@@ -23,7 +23,7 @@ __all__ = [
     "feature_propagate", "katz_beta", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
-    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
+    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
 ]
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
@@ -62,7 +62,7 @@ class Stats(C.Structure):
 class ServeConfig(C.Structure):
     """``agp_serve_config_t``."""
     _fields_ = [("mode", C.c_int32), ("max_lanes", C.c_int32), ("result_budget", C.c_int64),
-                ("results_on_host", C.c_int32), ("reserved", C.c_int32)]
+                ("results_on_host", C.c_int32), ("admission", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -78,6 +78,7 @@ class Result(C.Structure):
 
 
 SERVE_BATCHED, SERVE_FIFO_PLAIN, REQ_X_ON_DEVICE = 0, 1, 0x1
+ADMIT_COST, ADMIT_FIFO = 0, 1
 
 _lib = None
 _lock = threading.Lock()
@@ -309,9 +310,9 @@ def autotune(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=INPUT_ON_DE
 class Server:
     """``agp_serve_*``: continuous-batching server over a graph (see include/agp.h)."""
 
-    def __init__(self, g, mode=SERVE_BATCHED, max_lanes=0, result_budget=0, results_on_host=False):
+    def __init__(self, g, mode=SERVE_BATCHED, max_lanes=0, result_budget=0, results_on_host=False, admission=ADMIT_COST):
         self.g = g
-        cfg = ServeConfig(int(mode), int(max_lanes), int(result_budget), int(bool(results_on_host)), 0)
+        cfg = ServeConfig(int(mode), int(max_lanes), int(result_budget), int(bool(results_on_host)), int(admission))
         h = _vp()
         _check("agp_serve_create", lib().agp_serve_create(g.handle, C.byref(cfg), C.byref(h)))
         self.handle = h

@@ -101,6 +101,9 @@ struct agp_graph_s {
     int64_t mem_budget = 0;        // 0 = default
     int32_t wave_lanes = 0;        // lanes in flight per wave, 0 = automatic (L2 residency)
     agp::Workspace *ws = nullptr;
+    agp::Workspace *ws2 = nullptr; // second workspace: two waves in flight on two streams
+    cudaStream_t side = nullptr;   // stream of the second wave slot
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *in_stage = nullptr;      // device staging of per-call inputs (grown on demand)
     size_t in_bytes = 0;
     double prof_ms[5] = {0, 0, 0, 0, 0};   // AGP_PROFILE: device time per level-loop step

@@ -235,6 +235,10 @@ int agp_graph_destroy(agp_graph_t g)
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
     agp::free_workspace(g->ws);
+    agp::free_workspace(g->ws2);
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     cudaFree(g->rowptr);
     cudaFree(g->colidx);
     cudaFree(g->deg);

@@ -1,8 +1,9 @@
 // lanes.cuh -- lane state of the level pipeline, shared by batched queries and the server.
 //
 // A lane is one propagation problem with a non-negative, L1-normalised signal (one sign part of a
-// query or of a feature column, Section 3). Lanes own two dense FP32 residue vectors (level parity)
-// and a coefficient row; their reserves accumulate at out[u * su].
+// query or of a feature column, Section 3). Lanes own one dense FP32 residue vector (r^(i) until the
+// level's compaction empties it, then r^(i+1)) and a coefficient row; their reserves accumulate at
+// out[u * su].
 #pragma once
 
 #include <vector>
@@ -33,7 +34,31 @@ struct LaneParam {
     uint32_t key0, key1;
     float *out;       // pi(u) of this lane accumulates at out[u * su]
     int64_t su;
+    // derived by lane_param_derive (FP32 forms of the FP64 decision; the GPU's FP64 rate is low)
+    float eps_up;          // smallest float f with (double)f >= eps_d: for a = 0, c >= eps_up is
+                           // exactly (double)c >= eps_d
+    float eps_lo, eps_hi;  // FP32 bracket of eps wider than the FP32 error of c / d^a
+    float inv_eps;         // 1 / eps in FP32, for the sampling probabilities c / (eps d^a)
+    int32_t screen;        // 1: decide in FP32 outside [eps_lo, eps_hi), FP64 only inside
 };
+
+// Fill the derived fields of a lane whose eps_d, a_d and a_mode are set. For a in {1, 1/2} the FP32
+// quotient c / d^a (correctly rounded division and square root) is within 2 ulp (2.4e-7 relative) of
+// the exact value, for general 0 < a <= 1 (powf) well within 2^-16; the bracket is 2^-20 (resp.
+// 2^-16) wide on each side, so a decision made outside it equals the FP64 one.
+inline void lane_param_derive(LaneParam &P)
+{
+    const double e = P.eps_d;
+    float f = (float)e;
+    if ((double)f < e) f = nextafterf(f, INFINITY);
+    P.eps_up = f;
+    const double m = (P.a_mode == 3) ? 0x1p-16 : 0x1p-20;
+    P.eps_lo = (float)(e * (1.0 - m));
+    P.eps_hi = (float)(e * (1.0 + m));
+    P.inv_eps = e > 0.0 ? (float)(1.0 / e) : 0.f;
+    const bool a_ok = P.a_mode == 1 || P.a_mode == 2 || (P.a_mode == 3 && P.a_d > 0.0 && P.a_d <= 1.0);
+    P.screen = (a_ok && e >= 1e-30 && e <= 1e30) ? 1 : 0;
+}
 
 struct LaneStats {
     unsigned long long frontier[kMaxLevels];
@@ -55,8 +80,7 @@ struct KArgs {
     DevGraph g;
     int ubits;
     uint32_t umask;
-    float *R;                 // [2][G][ldR]
-    size_t par_stride;        // G * ldR
+    float *R;                 // [G][ldR]
     uint32_t *items;          // current frontier, ascending (lane << ubits | u)
     float *rval;              // r^(i)(u) of each frontier item
     int64_t ldR;              // lane stride of R (n rounded up to kScanUnit floats)
@@ -97,9 +121,14 @@ struct Workspace {
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;            // pinned
     LaneParam *h_lanes = nullptr;      // pinned
-    // per-call staging (grown on demand)
+    // per-wave staging (grown on demand): device block for coefficient specs, weights and seed maps,
+    // and a pinned host block it is filled from (so uploads need no stream synchronisation)
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    int prof_levels = 0;           // AGP_PROFILE: levels whose events are not read yet
+    bool pending = false;          // a wave was launched and not checked yet
     float *out_stage = nullptr;
     size_t out_stage_bytes = 0;
     // captured wave graph

@@ -2,26 +2,29 @@
 //
 // Unit of work: a "lane" = one propagation problem with a non-negative, L1-normalised signal (one
 // sign part of one query or of one feature column, Section 3 "Assumption on graph signal"). A
-// wave runs up to G lanes at once; every lane keeps two dense FP32 residue vectors (r^(i) and
-// r^(i+1), swapped by level parity) and accumulates its reserve straight into the caller's output.
+// wave runs up to G lanes at once; every lane keeps one dense FP32 residue vector and accumulates
+// its reserve straight into the caller's output. The compaction at the start of a level moves
+// r^(i) out of the vector (into the frontier list) and leaves it zero, so the pushes of the level
+// build r^(i+1) in the same vector: one n-vector per lane is all that must stay in L2.
 //
-// One level of one lane, for every u with r^(i)(u) != 0 (Algorithm 2, inner loop):
-//   k_expand   reads and clears r^(i)(u); reserve pi(u) += (w_i/Y_i) r^(i)(u);
-//              c = (Y_{i+1}/Y_i) r^(i)(u) / d_u^b; deterministic prefix length k(u) = number of
-//              neighbours with c / d_v^a >= eps (binary search over the degree-sorted row, or all
-//              or nothing when a = 0); short prefixes and light tails are done by the same thread,
-//              long prefixes become 1024-edge chunk records, heavy tails become segment records.
-//   k_push     one warp per chunk record: r^(i+1)(v) += c / d_v^a for the prefix neighbours.
-//   k_sample   one thread per segment record: subset sampling of the tail, Section 4: neighbours
-//              are grouped by degree in [2^g, 2^{g+1}); in a group every position is a Bernoulli
-//              trial with the group's largest probability p* (geometric skips, so the cost is the
-//              number of trials reached, not the group size) and a reached neighbour is kept with
-//              probability p_v/p*; a kept neighbour gets r^(i+1)(v) += eps.
-//   k_level_end   swaps the frontier buffers and advances every lane's level.
-// The frontier of the next level is built during the pushes: the thread whose atomic add finds the
-// residue at zero appends (lane, v). Increments below FLT_MIN are dropped so that this first-touch
-// test is exact. Sizes stay on the device; kernels are grid-stride loops over device-side counts,
-// so a whole wave can be captured in one CUDA graph.
+// One level of all lanes of a wave (Algorithm 2, inner loop over u with r^(i)(u) != 0):
+//   k_compact_count / _scan / _emit   dense scan of the lanes' residue vectors: the frontier
+//              F_i = {(lane, u) : r^(i)(u) != 0} as an ascending item list with the values
+//              r^(i)(u); the vectors are cleared as they are read.
+//   k_expand   one thread per item: reserve pi(u) += (w_i/Y_i) r^(i)(u); c = (Y_{i+1}/Y_i) r / d_u^b;
+//              deterministic prefix length k(u) = number of neighbours with c / d_v^a >= eps
+//              (binary search over the degree-sorted row, all or nothing when a = 0). Short
+//              prefixes and light tails (few expected trials) are done inline; long prefixes,
+//              dense tails (p >= 1/8) and heavy sparse tails become records.
+//   k_push     one warp per 512-position record: r^(i+1)(v) += c / d_v^a over a prefix chunk, or
+//              one Bernoulli trial per position of a dense-tail chunk (kept: += eps).
+//   k_sample   one thread per segment record of a sparse tail: subset sampling (Section 4) with
+//              neighbours grouped by degree in [2^g, 2^{g+1}); every position of a group is a trial
+//              with the group's largest probability p* (geometric skips, so the cost is the number
+//              of trials reached) and a reached neighbour is kept with probability p_v / p*.
+//   k_level_end   advances the lanes' levels and resets the record counters.
+// Pushes are fire-and-forget atomic adds. Sizes stay on the device; kernels are grid-stride loops
+// over device-side counts, so a wave's levels are captured in one CUDA graph.
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
@@ -30,6 +33,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "lanes.cuh"
@@ -61,15 +65,22 @@ __device__ __forceinline__ float apply_deg(float c, int32_t d, int mode, float p
     }
 }
 
-// push condition of Algorithm 2 in FP64 from the FP32 value c: c / d^a >= eps
-__device__ __forceinline__ bool push_test(float c, int32_t d, int mode, double a, double eps)
+// push condition of Algorithm 2, c / d^a >= eps, as evaluated in FP64 from the FP32 value c. The
+// FP32 screen decides every case outside the bracket [eps_lo, eps_hi); only the rare values inside
+// it take the FP64 path (see lane_param_derive).
+__device__ __forceinline__ bool push_test(float c, int32_t d, const LaneParam &P)
 {
+    if (P.a_mode == 0) return c >= P.eps_up;
+    if (P.screen) {
+        const float q = apply_deg(c, d, P.a_mode, P.a);
+        if (q >= P.eps_hi) return true;
+        if (q < P.eps_lo) return false;
+    }
     const double cd = (double)c;
-    switch (mode) {
-    case 0: return cd >= eps;
-    case 1: return cd / (double)d >= eps;
-    case 2: return cd / sqrt((double)d) >= eps;
-    default: return cd / pow((double)d, a) >= eps;
+    switch (P.a_mode) {
+    case 1: return cd / (double)d >= P.eps_d;
+    case 2: return cd / sqrt((double)d) >= P.eps_d;
+    default: return cd / pow((double)d, P.a_d) >= P.eps_d;
     }
 }
 
@@ -78,19 +89,31 @@ __device__ __forceinline__ int det_prefix(float c, const LaneParam &P, const int
                                           const int32_t *deg)
 {
     if (P.eps_d == 0.0) return d;
-    if (P.a_mode == 0) return ((double)c >= P.eps_d) ? d : 0;
-    if (!push_test(c, deg[row[0]], P.a_mode, P.a_d, P.eps_d)) return 0;
-    if (push_test(c, deg[row[d - 1]], P.a_mode, P.a_d, P.eps_d)) return d;
+    if (P.a_mode == 0) return (c >= P.eps_up) ? d : 0;
+    if (!push_test(c, __ldg(deg + __ldg(row)), P)) return 0;
+    if (push_test(c, __ldg(deg + __ldg(row + d - 1)), P)) return d;
     int lo = 1, hi = d - 1;  // first failing position is in [1, d-1]
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (push_test(c, deg[row[mid]], P.a_mode, P.a_d, P.eps_d)) lo = mid + 1;
+        if (push_test(c, __ldg(deg + __ldg(row + mid)), P)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
 // ---- pushes --------------------------------------------------------------------------------------
+// Neighbour lists are streamed: the CSR is several times larger than L2, while the residue vectors
+// that take the random atomic adds fit in it. Neighbour-list loads are therefore marked evict-first
+// in L2, so that they do not displace the residue vectors.
+__device__ __forceinline__ int32_t ld_col(const int32_t *p)
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Pushes are fire-and-forget atomic adds (no value returned, so no thread waits on them). The next
 // frontier is not tracked during the pushes: each level starts by scanning the residue vectors of
 // the active lanes (see k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
@@ -134,7 +157,7 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int 
                              unsigned long long &accepted, int kern)
 {
     Uniforms U((uint32_t)u, (uint32_t)lvl, seg, P.key0, P.key1);
-    const float ce = (float)((double)c / P.eps_d);  // c / eps
+    const float ce = c * P.inv_eps;  // c / eps
     int j = j0;
     while (j < j1) {
         int gend = j1;
@@ -156,13 +179,14 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int 
         }
         pstar = fminf(pstar, 1.f);
         if (!(pstar > 0.f)) { j = gend; continue; }
-        const float lq = (pstar < 1.f) ? log1pf(-pstar) : -INFINITY;
+        // geometric skip: floor(ln U / ln(1 - p*)) positions are passed over before the next trial
+        const float rlq = (pstar < 1.f) ? 1.f / log1pf(-pstar) : 0.f;
         while (true) {
-            const float skip = (pstar < 1.f) ? floorf(logf(U.next()) / lq) : 0.f;
+            const float skip = (pstar < 1.f) ? floorf(logf(U.next()) * rlq) : 0.f;
             if (!(skip < (float)(gend - j))) { j = gend; break; }
             j += (int)skip;
             ++drawn;
-            const int32_t v = row[j];
+            const int32_t v = ld_col(row + j);
             bool keep = true;
             if (P.a_mode != 0) {
                 const float pv = apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
@@ -197,7 +221,7 @@ __device__ __forceinline__ float4 *unit_ptr(const KArgs &A, int64_t unit, int &l
     const int lvl = A.level[lane];
     live = lvl >= 0;
     const int64_t off = (unit - (int64_t)lane * A.units) * kScanUnit;
-    return (float4 *)(A.R + (size_t)(lvl & 1) * A.par_stride + (size_t)lane * A.ldR + off);
+    return (float4 *)(A.R + (size_t)lane * A.ldR + off);
 }
 
 __device__ __forceinline__ int nz4(float4 v)
@@ -256,89 +280,114 @@ __global__ void k_compact_scan(KArgs A)
     }
 }
 
+// Pass 3: units are taken four at a time. The four float4 loads of a thread are issued together,
+// and one block scan of the four per-thread counts (packed in 16-bit fields of a 64-bit word: a
+// unit holds at most 1024 non-zeros, so no field carries into the next) places every non-zero.
+// The warp totals are double-buffered, so a batch needs a single __syncthreads.
+constexpr int kEmitBatch = 4;
 __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
 {
-    __shared__ unsigned int wsum[kBlock / 32];
-    __shared__ unsigned long long run_s;
+    __shared__ unsigned long long wsum[2][kBlock / 32];
     int64_t begin, end;
     compact_range(A, begin, end);
     const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) run_s = (unsigned long long)A.part[blockIdx.x];
-    __syncthreads();
-    for (int64_t unit = begin; unit < end; ++unit) {
-        int lane;
-        bool live;
-        float4 *p = unit_ptr(A, unit, lane, live);
-        if (!live) continue;  // uniform across the block
-        const float4 v = p[threadIdx.x];
-        const unsigned int c = nz4(v);
-        unsigned int x = c;  // inclusive warp scan
+    unsigned long long run = (unsigned long long)A.part[blockIdx.x];
+    int parity = 0;
+    for (int64_t u0 = begin; u0 < end; u0 += kEmitBatch, parity ^= 1) {
+        float4 v[kEmitBatch];
+        float4 *ptr[kEmitBatch];
+        int lanes[kEmitBatch];
+        unsigned long long packed = 0;
+#pragma unroll
+        for (int j = 0; j < kEmitBatch; ++j) {
+            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ptr[j] = nullptr;
+            lanes[j] = 0;
+            if (u0 + j < end) {
+                bool live;
+                float4 *p = unit_ptr(A, u0 + j, lanes[j], live);
+                if (live) {
+                    ptr[j] = p;
+                    v[j] = p[threadIdx.x];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kEmitBatch; ++j) packed |= (unsigned long long)nz4(v[j]) << (16 * j);
+        unsigned long long x = packed;  // inclusive warp scan of the packed counts
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane_id >= o) x += y;
         }
-        if (lane_id == 31) wsum[warp] = x;
+        if (lane_id == 31) wsum[parity][warp] = x;
         __syncthreads();
-        unsigned long long off = run_s;
-        for (int k = 0; k < warp; ++k) off += wsum[k];
-        off += x - c;
-        if (c) {
-            const uint32_t u0 = (uint32_t)((unit - (int64_t)lane * A.units) * kScanUnit + 4 * threadIdx.x);
+        unsigned long long before = 0, total = 0;
+        for (int k = 0; k < kBlock / 32; ++k) {
+            const unsigned long long w = wsum[parity][k];
+            if (k < warp) before += w;
+            total += w;
+        }
+        const unsigned long long excl = before + x - packed;
+        unsigned long long unit_base = run;
+#pragma unroll
+        for (int j = 0; j < kEmitBatch; ++j) {
+            const unsigned int c = (unsigned int)(packed >> (16 * j)) & 0xFFFFu;
+            unsigned long long off = unit_base + ((excl >> (16 * j)) & 0xFFFFull);
+            unit_base += (total >> (16 * j)) & 0xFFFFull;
+            if (c == 0) continue;
+            const int lane = lanes[j];
+            const uint32_t ub = (uint32_t)((u0 + j - (int64_t)lane * A.units) * kScanUnit + 4 * threadIdx.x);
             const uint32_t hi = (uint32_t)lane << A.ubits;
-            const float e[4] = {v.x, v.y, v.z, v.w};
+            const float e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (e[k] == 0.f) continue;
                 if (off < A.cap_items) {
-                    A.items[off] = hi | (u0 + (uint32_t)k);
+                    A.items[off] = hi | (ub + (uint32_t)k);
                     A.rval[off] = e[k];
                 } else {
                     atomicOr(&A.ctrl->error, 1u);
                 }
                 ++off;
             }
-            p[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ptr[j][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (A.collect) atomicAdd(&A.stats[lane].frontier[A.level[lane]], (unsigned long long)c);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0;
-            for (int k = 0; k < kBlock / 32; ++k) t += wsum[k];
-            run_s += t;
-        }
-        __syncthreads();
+        run = unit_base;
     }
 }
 
 __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long idx)
 {
     Ctrl *ctrl = A.ctrl;
-    const uint32_t item = A.items[idx];
+    // every array read here is written only by earlier kernels: read-only path
+    const uint32_t item = __ldg(A.items + idx);
     const int lane = (int)(item >> A.ubits);
     const int32_t u = (int32_t)(item & A.umask);
-    const int lvl = A.level[lane];
+    const int32_t d = __ldg(A.g.deg + u);
+    const int64_t e0 = __ldg(A.g.rowptr + u);
+    const float r = __ldg(A.rval + idx);  // the compaction read r^(i)(u) and cleared it
+    const int lvl = __ldg(A.level + lane);
     if (lvl < 0 || lvl >= kMaxLevels) {
         atomicOr(&ctrl->error, 16u);
         return;
     }
     const LaneParam &P = A.lanes[lane];
-    float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
-    const float r = A.rval[idx];  // the compaction read r^(i)(u) and cleared it
-    const float2 cf = A.coef[lane * kMaxLevels + lvl];
+    float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
+    const float2 cf = __ldg(A.coef + lane * kMaxLevels + lvl);
     // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
     atomicAdd(P.out + (int64_t)u * P.su, cf.x * r);
     if (lvl >= P.L) return;
-    const int32_t d = A.g.deg[u];
     if (d == 0) return;
     const float c = apply_deg(cf.y * r, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
     if (!(c > 0.f)) return;
-    const int32_t *row = A.g.colidx + A.g.rowptr[u];
+    const int32_t *row = A.g.colidx + e0;
     const int k = det_prefix(c, P, row, d, A.g.deg);
     unsigned long long drawn = 0, accepted = 0;
     if (k > 0) {
         if (k <= kInlineDet) {
             for (int j = 0; j < k; ++j) {
-                const int32_t v = row[j];
+                const int32_t v = ld_col(row + j);
                 const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
                 push_to(Rn, v, inc);
             }
@@ -356,7 +405,7 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
     int seglen = 0;
     bool dense = false;
     if (tail > 0) {
-        const float ce = (float)((double)c / P.eps_d);
+        const float ce = c * P.inv_eps;
         const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
         const float expect = p0 * (float)tail;  // upper bound on the trials reached
         if (expect <= kLightSamples) {
@@ -408,7 +457,7 @@ __device__ __forceinline__ void dense_tail_chunk(const KArgs &A, const LaneParam
                                                  const int32_t *row, int k, int d, int chunk, float c, int lane_id,
                                                  unsigned long long &drawn, unsigned long long &accepted)
 {
-    const float ce = (float)((double)c / P.eps_d);
+    const float ce = c * P.inv_eps;
     const int r0 = chunk * kChunk, r1 = min(d - k, r0 + kChunk);
     for (int rel = r0 + 4 * lane_id; rel < r1; rel += 128) {
         const Philox4 q = philox4x32_10((uint32_t)u, (uint32_t)lvl, (uint32_t)(rel >> 2), kDenseTag, P.key0, P.key1);
@@ -416,7 +465,7 @@ __device__ __forceinline__ void dense_tail_chunk(const KArgs &A, const LaneParam
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (rel + t >= r1) break;
-            const int32_t v = row[k + rel + t];
+            const int32_t v = ld_col(row + k + rel + t);
             const float p = (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
             ++drawn;
             if (u01_open(w[t]) < p) {
@@ -443,14 +492,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         const int32_t u = (int32_t)(item & A.umask);
         const int lvl = A.level[lane];
         const LaneParam &P = A.lanes[lane];
-        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
+        float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
         const float c = A.c_item[R.x];
         const int k = A.k_item[R.x].x;
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         if (det) {
             const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
             for (int j = j0 + lane_id; j < j1; j += 32) {
-                const int32_t v = row[j];
+                const int32_t v = ld_col(row + j);
                 const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
                 push_to(Rn, v, inc);
             }
@@ -477,7 +526,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         const int32_t u = (int32_t)(item & A.umask);
         const int lvl = A.level[lane];
         const LaneParam &P = A.lanes[lane];
-        float *Rn = A.R + (size_t)((lvl + 1) & 1) * A.par_stride + (size_t)lane * A.ldR;
+        float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
         const float c = A.c_item[R.x];
         const int2 ks = A.k_item[R.x];
         const int d = A.g.deg[u];
@@ -609,7 +658,7 @@ __global__ void k_seed_sparse(KArgs A, const int64_t *off, const int32_t *idx, c
         const int lane = lane_of[2 * q + part];
         const int32_t u = idx[t];
         if (lane < 0 || u < 0 || u >= A.g.n) continue;
-        float *R0 = A.R + (size_t)lane * A.ldR;  // level 0 lives in parity 0
+        float *R0 = A.R + (size_t)lane * A.ldR;
         const float r0 = (float)((double)fabsf(x) / norms[2 * q + part]);
         push_to(R0, u, r0);
     }
@@ -660,17 +709,9 @@ __global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const
     }
 }
 
-__global__ void k_threshold(DevGraph g, double a, int a_mode, double eps, int64_t count, const int32_t *nodes,
-                            const float *c, int32_t *k_out)
+__global__ void k_threshold(DevGraph g, LaneParam P, int64_t count, const int32_t *nodes, const float *c,
+                            int32_t *k_out)
 {
-    LaneParam P;
-    P.eps_d = eps;
-    P.eps = (float)eps;
-    P.a = (float)a;
-    P.b = 0.f;
-    P.a_d = a;
-    P.a_mode = a_mode;
-    P.b_mode = 0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = nodes[t];
         int k = 0;
@@ -758,11 +799,9 @@ size_t bytes_per_lane(const agp_graph_s *g)
 {
     const size_t n = (size_t)g->n;
     const double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
-    // R (2 x 4) + items (2 x 4) + c (4) + k (8) + chunk and segment records (8 + 8, with the
-    // extra records of long rows) per (lane, node)
-    // R (2 x 4) + items (4) + r values (4) + c (4) + k (8) + prefix-chunk, dense-tail-chunk and
+    // R (4) + items (4) + r values (4) + c (4) + k (8) + prefix-chunk, dense-tail-chunk and
     // segment records (8 each, with the extra records of long rows) per (lane, node)
-    return n * (8 + 4 + 4 + 4 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
+    return n * (4 + 4 + 4 + 4 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
 int lane_capacity(const agp_graph_s *g)
@@ -795,6 +834,7 @@ void free_workspace(Workspace *ws)
     cudaFree(ws->stats);
     cudaFree(ws->ctrl);
     cudaFree(ws->stage);
+    cudaFreeHost(ws->h_stage);
     cudaFree(ws->out_stage);
     cudaFreeHost(ws->h_ctrl);
     cudaFreeHost(ws->h_lanes);
@@ -844,7 +884,7 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     ws->ldR = ((int64_t)n + kScanUnit - 1) / kScanUnit * kScanUnit;
     const int64_t units = (int64_t)G * (ws->ldR / kScanUnit);
     ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kNumSMs * 8, units));
-    A(dev_alloc(&ws->R, (size_t)2 * G * ws->ldR, acc));
+    A(dev_alloc(&ws->R, (size_t)G * ws->ldR, acc));
     A(dev_alloc(&ws->items, ws->cap_items, acc));
     A(dev_alloc(&ws->rval, ws->cap_items, acc));
     A(dev_alloc(&ws->part, (size_t)ws->part_blocks + 1, acc));
@@ -861,7 +901,7 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     if (rc == AGP_OK && cudaMallocHost((void **)&ws->h_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = fail(AGP_ENOMEM, "cudaMallocHost");
     if (rc == AGP_OK && cudaMallocHost((void **)&ws->h_lanes, sizeof(LaneParam) * G) != cudaSuccess) rc = fail(AGP_ENOMEM, "cudaMallocHost");
     if (rc == AGP_OK) {
-        cudaError_t e = cudaMemset(ws->R, 0, sizeof(float) * (size_t)2 * G * ws->ldR);
+        cudaError_t e = cudaMemset(ws->R, 0, sizeof(float) * (size_t)G * ws->ldR);
         if (e == cudaSuccess) e = cudaMemset(ws->level, 0xff, sizeof(int32_t) * G);
         if (e == cudaSuccess) e = cudaMemset(ws->ctrl, 0, sizeof(Ctrl));
         if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(LaneStats) * G);
@@ -884,7 +924,9 @@ void drop_workspace(agp_graph_s *g)
     cudaDeviceSynchronize();
     cudaGetLastError();
     free_workspace(g->ws);
+    free_workspace(g->ws2);
     g->ws = nullptr;
+    g->ws2 = nullptr;
 }
 
 int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
@@ -900,6 +942,8 @@ int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
         AGP_CUDA_TRY(cudaDeviceSynchronize());
         free_workspace(g->ws);
         g->ws = nullptr;
+        free_workspace(g->ws2);
+        g->ws2 = nullptr;
     }
     AGP_TRY(create_workspace(g, G, &g->ws));
     *out = g->ws;
@@ -923,6 +967,22 @@ int grow(void **p, size_t *have, size_t need)
     return AGP_OK;
 }
 
+int grow_pinned(void **p, size_t *have, size_t need)
+{
+    if (*have >= need) return AGP_OK;
+    cudaFreeHost(*p);
+    *p = nullptr;
+    *have = 0;
+    need = std::max<size_t>(need, 4096);
+    if (cudaMallocHost(p, need) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(AGP_ENOMEM, "pinned staging buffer");
+    }
+    *have = need;
+    return AGP_OK;
+}
+
 KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
 {
     KArgs A;
@@ -930,7 +990,6 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.ubits = g->ubits;
     A.umask = (g->ubits >= 32) ? 0xffffffffu : ((1u << g->ubits) - 1u);
     A.R = ws->R;
-    A.par_stride = (size_t)ws->G * (size_t)ws->ldR;
     A.items = ws->items;
     A.rval = ws->rval;
     A.ldR = ws->ldR;
@@ -1070,6 +1129,7 @@ void launch_seed_dense_bf16(const KArgs &A, const uint16_t *X, int64_t ldx, cons
 // Run the levels of the current wave (lanes already seeded, level 0 frontier in items[cur]).
 int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool plain, bool profile, cudaStream_t s)
 {
+    ws->prof_levels = 0;
     if (profile) AGP_TRY(ensure_events(ws));
     if (plain) {
         bool ran[kMaxLevels * kProfKernels] = {};
@@ -1121,10 +1181,7 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
     __atomic_fetch_add(&g->kernel_launches, (int64_t)(7 * (max_L + 1)), __ATOMIC_RELAXED);
-    if (profile) {
-        AGP_CUDA_TRY(cudaStreamSynchronize(s));
-        read_profile(g, ws, max_L + 1, nullptr);
-    }
+    ws->prof_levels = profile ? max_L + 1 : 0;  // read when the wave is checked
     return AGP_OK;
 }
 
@@ -1144,17 +1201,36 @@ struct LaneSpec {
     int params;      // index into params
 };
 
+// Lane parameters, coefficients and levels of a wave, plus `aux` (int32 seed map of the caller),
+// uploaded from the workspace's pinned staging on stream s. The workspace must be idle (its
+// previous wave checked), which is what makes reusing the pinned staging safe without a sync.
 int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lanes, size_t first, int count,
                  const agp_params_t *params, uint64_t stream_base_is_query, float *out, int64_t su, int64_t sr,
-                 cudaStream_t s, std::vector<CoefSpec> &cs, std::vector<double> &wts, int *max_L)
+                 const std::vector<int32_t> &aux, int32_t **d_aux, cudaStream_t s, int *max_L)
 {
-    cs.assign(count, CoefSpec{});
-    wts.clear();
     *max_L = 0;
+    size_t nw = 0;
+    for (int l = 0; l < count; ++l) {
+        const agp_params_t &p = params[lanes[first + l].params];
+        if (p.kind == AGP_W_FINITE) nw += (size_t)p.L + 1;
+    }
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t lp_b = sizeof(LaneParam) * count, cs_b = sizeof(CoefSpec) * count, w_b = sizeof(double) * std::max<size_t>(nw, 1),
+                 lv_b = sizeof(int32_t) * ws->G, aux_b = sizeof(int32_t) * std::max<size_t>(aux.size(), 1);
+    const size_t total = al(lp_b) + al(cs_b) + al(w_b) + al(lv_b) + al(aux_b);
+    AGP_TRY(grow(&ws->stage, &ws->stage_bytes, total));
+    AGP_TRY(grow_pinned(&ws->h_stage, &ws->h_stage_bytes, total));
+    char *h = (char *)ws->h_stage;
+    LaneParam *h_lp = (LaneParam *)h;
+    CoefSpec *h_cs = (CoefSpec *)(h + al(lp_b));
+    double *h_w = (double *)(h + al(lp_b) + al(cs_b));
+    int32_t *h_lv = (int32_t *)(h + al(lp_b) + al(cs_b) + al(w_b));
+    int32_t *h_aux = (int32_t *)(h + al(lp_b) + al(cs_b) + al(w_b) + al(lv_b));
+    size_t w_used = 0;
     for (int l = 0; l < count; ++l) {
         const LaneSpec &ls = lanes[first + l];
         const agp_params_t &p = params[ls.params];
-        LaneParam &P = ws->h_lanes[l];
+        LaneParam &P = h_lp[l];
         P.eps_d = p.eps;
         P.eps = (float)p.eps;
         P.a = (float)p.a;
@@ -1166,8 +1242,10 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
         P.out_row = ls.query;
         P.out = out + (int64_t)ls.query * sr;
         P.su = su;
+        lane_param_derive(P);
         lane_key(p.seed, stream_base_is_query ? (uint64_t)ls.query : 0ull, ls.part, P.key0, P.key1);
-        CoefSpec &c = cs[l];
+        CoefSpec &c = h_cs[l];
+        c = CoefSpec{};
         c.lane = l;
         c.kind = p.kind;
         c.L = p.L;
@@ -1175,38 +1253,29 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
         c.scale = (ls.part ? -1.0 : 1.0) * ls.norm;
         c.w_off = 0;
         if (p.kind == AGP_W_FINITE) {
-            c.w_off = (int32_t)wts.size();
-            for (int i = 0; i <= p.L; ++i) wts.push_back(p.w[i]);
+            c.w_off = (int32_t)w_used;
+            for (int i = 0; i <= p.L; ++i) h_w[w_used++] = p.w[i];
         }
         *max_L = std::max(*max_L, p.L);
     }
-    // device copies: lane params, coefficient specs, weights (staging area)
-    const size_t cs_bytes = sizeof(CoefSpec) * count, w_bytes = sizeof(double) * std::max<size_t>(wts.size(), 1);
-    AGP_TRY(grow(&ws->stage, &ws->stage_bytes, cs_bytes + w_bytes + 256));
-    char *st = (char *)ws->stage;
-    CoefSpec *d_cs = (CoefSpec *)st;
-    double *d_w = (double *)(st + ((cs_bytes + 15) / 16) * 16);
-    AGP_CUDA_TRY(cudaMemcpyAsync(ws->lanes, ws->h_lanes, sizeof(LaneParam) * count, cudaMemcpyHostToDevice, s));
-    AGP_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), cs_bytes, cudaMemcpyHostToDevice, s));
-    if (!wts.empty()) AGP_CUDA_TRY(cudaMemcpyAsync(d_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, s));
-    launch_coef(d_cs, d_w, ws->coef, count, s);
-    // all wave lanes start at level 0, the other lanes idle
-    std::vector<int32_t> lv(ws->G, -1);
-    for (int l = 0; l < count; ++l) lv[l] = 0;
-    AGP_CUDA_TRY(cudaMemcpyAsync(ws->level, lv.data(), sizeof(int32_t) * ws->G, cudaMemcpyHostToDevice, s));
+    for (int l = 0; l < ws->G; ++l) h_lv[l] = l < count ? 0 : -1;  // wave lanes start at level 0
+    std::copy(aux.begin(), aux.end(), h_aux);
+    char *d = (char *)ws->stage;
+    AGP_CUDA_TRY(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, s));
+    AGP_CUDA_TRY(cudaMemcpyAsync(ws->lanes, d, lp_b, cudaMemcpyDeviceToDevice, s));
+    launch_coef((const CoefSpec *)(d + al(lp_b)), (const double *)(d + al(lp_b) + al(cs_b)), ws->coef, count, s);
+    AGP_CUDA_TRY(cudaMemcpyAsync(ws->level, d + al(lp_b) + al(cs_b) + al(w_b), lv_b, cudaMemcpyDeviceToDevice, s));
     AGP_CUDA_TRY(cudaMemsetAsync(ws->stats, 0, sizeof(LaneStats) * ws->G, s));
-    // the copies above read host memory that lives until the next synchronisation point
-    AGP_CUDA_TRY(cudaStreamSynchronize(s));
+    *d_aux = (int32_t *)(d + al(lp_b) + al(cs_b) + al(w_b) + al(lv_b));
     return AGP_OK;
 }
 
 int reset_ctrl(Workspace *ws, int lanes_used, cudaStream_t s)
 {
-    Ctrl *h = ws->h_ctrl;
+    Ctrl *h = ws->h_ctrl;  // pinned; the workspace's previous wave has been checked
     std::memset(h, 0, sizeof(Ctrl));
     h->lanes_used = (unsigned int)lanes_used;
     AGP_CUDA_TRY(cudaMemcpyAsync(ws->ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
-    AGP_CUDA_TRY(cudaStreamSynchronize(s));
     return AGP_OK;
 }
 
@@ -1227,6 +1296,99 @@ int collect_stats(Workspace *ws, const std::vector<LaneSpec> &lanes, size_t firs
         }
     }
     return AGP_OK;
+}
+
+// ------------------------------------------------------------------------------------ wave pipeline
+// What a call does per wave besides the common steps: its seed map (uploaded with the wave's
+// parameters) and its seed kernel.
+struct WaveJob {
+    float *out;
+    int64_t su, sr;
+    uint64_t stream_base_is_query;
+    std::function<void(size_t first, int count, std::vector<int32_t> &aux)> make_aux;
+    std::function<int(const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st)> seed;
+};
+
+// Runs the waves (G lanes each) of a call. Unless the call is on the plain path or on a fixed
+// workspace, two waves are in flight: wave w uses workspace w % 2 on stream w % 2 (the caller's
+// stream and a side stream forked from it), so the latency-bound expansion of one wave overlaps
+// the L2-bound pushes of the other. A workspace's wave is checked (errors, profile, statistics)
+// only when the workspace is needed again or at the end.
+int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<LaneSpec> &lanes,
+              const agp_params_t *params, int G, bool plain, bool profile, int collect, agp_stats_t *stats,
+              cudaStream_t s, const WaveJob &job)
+{
+    const bool two = !plain && !ctx->ws && lanes.size() > (size_t)G;
+    Workspace *wss[2] = {ws0, nullptr};
+    cudaStream_t ss[2] = {s, nullptr};
+    if (two) {
+        if (g->ws2 && g->ws2->G < ws0->G) {
+            AGP_CUDA_TRY(cudaDeviceSynchronize());
+            free_workspace(g->ws2);
+            g->ws2 = nullptr;
+        }
+        if (!g->ws2) AGP_TRY(create_workspace(g, ws0->G, &g->ws2));
+        if (!g->side) {
+            AGP_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+            AGP_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+            AGP_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+        }
+        wss[1] = g->ws2;
+        ss[1] = g->side;
+        AGP_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
+        AGP_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+    }
+    size_t wfirst[2] = {0, 0};
+    int wcount[2] = {0, 0};
+    auto finish = [&](int k) -> int {
+        Workspace *W = wss[k];
+        if (!W || !W->pending) return AGP_OK;
+        W->pending = false;
+        int rc = check_ctrl(W, ss[k]);
+        if (rc == AGP_OK && W->prof_levels > 0) {
+            read_profile(g, W, W->prof_levels, nullptr);
+            W->prof_levels = 0;
+        }
+        if (rc == AGP_OK && collect) rc = collect_stats(W, lanes, wfirst[k], wcount[k], stats, ss[k]);
+        return rc;
+    };
+    int rc = AGP_OK;
+    size_t first = 0;
+    for (int w = 0; first < lanes.size(); first += G, ++w) {
+        const int k = two ? (w & 1) : 0;
+        Workspace *W = wss[k];
+        const cudaStream_t st = ss[k];
+        if ((rc = finish(k)) != AGP_OK) break;
+        const int count = (int)std::min<size_t>(G, lanes.size() - first);
+        std::vector<int32_t> aux;
+        job.make_aux(first, count, aux);
+        int32_t *d_aux = nullptr;
+        int max_L = 0;
+        if ((rc = prepare_wave(g, W, lanes, first, count, params, job.stream_base_is_query, job.out, job.su, job.sr, aux,
+                               &d_aux, st, &max_L)) != AGP_OK)
+            break;
+        if ((rc = reset_ctrl(W, count, st)) != AGP_OK) break;
+        const KArgs A = make_args(g, W, collect);
+        if ((rc = job.seed(A, count, d_aux, st)) != AGP_OK) break;
+        __atomic_fetch_add(&g->kernel_launches, (int64_t)2, __ATOMIC_RELAXED);  // coefficients + seed
+        if ((rc = run_levels(g, W, A, max_L, plain, profile, st)) != AGP_OK) break;
+        W->pending = true;
+        wfirst[k] = first;
+        wcount[k] = count;
+    }
+    for (int k = 0; k < 2; ++k) {
+        const int r2 = finish(k);
+        if (rc == AGP_OK) rc = r2;
+    }
+    if (two) {
+        cudaEventRecord(g->ev_join, g->side);
+        cudaStreamWaitEvent(s, g->ev_join, 0);
+    }
+    if (rc != AGP_OK) {
+        if (!ctx->ws) drop_workspace(g);
+        else wss[0]->pending = false;
+    }
+    return rc;
 }
 
 // ------------------------------------------------------------------------------------ queries
@@ -1284,7 +1446,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     int32_t *d_idx = (int32_t *)p; p += al(idx_b);
     float *d_val = x_val ? (float *)p : nullptr; p += al(val_b);
     double *d_norm = (double *)p; p += al(norm_b);
-    int32_t *d_map = (int32_t *)p; p += al(map_b);
+    p += al(map_b);
     unsigned int *d_bad = (unsigned int *)p;
     const int64_t *off_src = x_off;
     const int32_t *idx_src = x_idx;
@@ -1332,29 +1494,24 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     if (n > 0) AGP_CUDA_TRY(cudaMemset2DAsync(out, sizeof(float) * ld, 0, sizeof(float) * n, Q, s));
 
     if (stats) std::memset(stats, 0, sizeof(agp_stats_t) * Q);
-    const KArgs A = make_args(g, ws, collect);
     const int G = plain ? 1 : std::min(ws->G, ctx->ws ? ws->G : wave_lanes(g));
-    std::vector<CoefSpec> cs;
-    std::vector<double> wts;
-    for (size_t first = 0; first < lanes.size(); first += G) {
-        const int count = (int)std::min<size_t>(G, lanes.size() - first);
-        int max_L = 0;
-        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 0, out, 1, ld, s, cs, wts, &max_L));
-        std::vector<int32_t> map(2 * Q, -1);
-        for (int l = 0; l < count; ++l) map[2 * lanes[first + l].query + lanes[first + l].part] = l;
-        AGP_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), map_b, cudaMemcpyHostToDevice, s));
-        AGP_TRY(reset_ctrl(ws, count, s));
-        k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, s>>>(A, off_src, idx_src, val_src, Q, d_map, d_norm);
-        __atomic_fetch_add(&g->kernel_launches, (int64_t)(2), __ATOMIC_RELAXED);  // coefficients + seed
+    WaveJob job;
+    job.out = out;
+    job.su = 1;
+    job.sr = ld;
+    job.stream_base_is_query = 0;  // a query's random stream depends on its seed, not its position
+    job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
+        aux.assign(2 * (size_t)Q, -1);
+        for (int l = 0; l < count; ++l) aux[2 * lanes[first + l].query + lanes[first + l].part] = l;
+    };
+    job.seed = [&](const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st) -> int {
+        (void)count;
+        k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, st>>>(A, off_src, idx_src, val_src, Q,
+                                                                                       d_aux, d_norm);
         AGP_CUDA_TRY(cudaGetLastError());
-        int rc = run_levels(g, ws, A, max_L, plain, profile, s);
-        if (rc == AGP_OK) rc = check_ctrl(ws, s);
-        if (rc != AGP_OK) {
-            if (!ctx->ws) drop_workspace(g);
-            return rc;
-        }
-        if (collect) AGP_TRY(collect_stats(ws, lanes, first, count, stats, s));
-    }
+        return AGP_OK;
+    };
+    AGP_TRY(run_waves(g, ctx, ws, lanes, params, G, plain, profile, collect, stats, s, job));
     if (collect)
         for (int q = 0; q < Q; ++q) stats[q].levels = params[n_params == 1 ? 0 : q].L + 1;
     if (host_out) {
@@ -1388,11 +1545,9 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     Workspace *ws = ctx->ws;
     if (!ws) AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), &ws));
     // column norms of the sign parts
-    const size_t norm_b = sizeof(double) * 2 * d, map_b = sizeof(int32_t) * 2 * 4096;
-    AGP_TRY(grow(ctx->stage, ctx->stage_bytes, norm_b + 2 * map_b + 512));
+    const size_t norm_b = sizeof(double) * 2 * d;
+    AGP_TRY(grow(ctx->stage, ctx->stage_bytes, norm_b + 256));
     double *d_norm = (double *)*ctx->stage;
-    int32_t *d_col = (int32_t *)((char *)*ctx->stage + (norm_b + 255) / 256 * 256);
-    int32_t *d_part = d_col + 4096;
     AGP_CUDA_TRY(cudaMemsetAsync(d_norm, 0, norm_b, s));
     launch_colnorms_bf16(X, n, d, ldx, d_norm, s);
     __atomic_fetch_add(&g->kernel_launches, (int64_t)(1), __ATOMIC_RELAXED);
@@ -1405,29 +1560,25 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     for (int64_t c = 0; c < d; ++c)
         for (int part = 0; part < 2; ++part)
             if (norms[2 * c + part] > 0.0) lanes.push_back(LaneSpec{(int)c, part, norms[2 * c + part], 0});
-    const KArgs A = make_args(g, ws, 0);
     const int G = plain ? 1 : std::min({ws->G, 4096, ctx->ws ? ws->G : wave_lanes(g)});
-    std::vector<CoefSpec> cs;
-    std::vector<double> wts;
-    for (size_t first = 0; first < lanes.size(); first += G) {
-        const int count = (int)std::min<size_t>(G, lanes.size() - first);
-        int max_L = 0;
-        AGP_TRY(prepare_wave(g, ws, lanes, first, count, params, 1, Z, ldz, 1, s, cs, wts, &max_L));
-        std::vector<int32_t> col(count), part(count);
-        for (int l = 0; l < count; ++l) { col[l] = lanes[first + l].query; part[l] = lanes[first + l].part; }
-        AGP_CUDA_TRY(cudaMemcpyAsync(d_col, col.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
-        AGP_CUDA_TRY(cudaMemcpyAsync(d_part, part.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
-        AGP_TRY(reset_ctrl(ws, count, s));
-        launch_seed_dense_bf16(A, X, ldx, nullptr, d_col, d_part, d_norm, count, s);
-        __atomic_fetch_add(&g->kernel_launches, (int64_t)(2), __ATOMIC_RELAXED);  // coefficients + seed
-        AGP_CUDA_TRY(cudaGetLastError());
-        int rc = run_levels(g, ws, A, max_L, plain, profile, s);
-        if (rc == AGP_OK) rc = check_ctrl(ws, s);
-        if (rc != AGP_OK) {
-            if (!ctx->ws) drop_workspace(g);
-            return rc;
+    WaveJob job;
+    job.out = Z;
+    job.su = ldz;
+    job.sr = 1;
+    job.stream_base_is_query = 1;  // column c of part s draws from the stream (seed, c, s)
+    job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
+        aux.resize(2 * (size_t)count);
+        for (int l = 0; l < count; ++l) {
+            aux[l] = lanes[first + l].query;          // column
+            aux[count + l] = lanes[first + l].part;   // sign part
         }
-    }
+    };
+    job.seed = [&](const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st) -> int {
+        launch_seed_dense_bf16(A, X, ldx, nullptr, d_aux, d_aux + count, d_norm, count, st);
+        AGP_CUDA_TRY(cudaGetLastError());
+        return AGP_OK;
+    };
+    AGP_TRY(run_waves(g, ctx, ws, lanes, params, G, plain, profile, 0, nullptr, s, job));
     return AGP_OK;
 }
 
@@ -1439,7 +1590,14 @@ int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t
     if (count < 0 || (count > 0 && (!nodes || !c || !k_out))) return fail(AGP_EINVAL, "bad arrays");
     if (count == 0) return AGP_OK;
     AGP_CUDA_TRY(cudaSetDevice(g->device));
-    k_threshold<<<blocks_for((unsigned long long)count, kBlock), kBlock, 0, s>>>(g->dev(), a, exponent_mode(a), eps, count, nodes, c, k_out);
+    LaneParam P{};
+    P.eps_d = eps;
+    P.eps = (float)eps;
+    P.a = (float)a;
+    P.a_d = a;
+    P.a_mode = exponent_mode(a);
+    lane_param_derive(P);
+    k_threshold<<<blocks_for((unsigned long long)count, kBlock), kBlock, 0, s>>>(g->dev(), P, count, nodes, c, k_out);
     AGP_CUDA_TRY(cudaGetLastError());
     return AGP_OK;
 }

@@ -41,6 +41,8 @@ struct Request {
     int status = AGP_OK;
     bool done = false, cancelled = false, released = false, cut = false, counted = false;
     int lanes_left = 0;
+    double cost = 0.0;              // estimated operations (admission priority)
+    bool heavy = false;
     std::vector<int> slots;
     float *d_out = nullptr;         // device result (n or n * cols floats)
     float *h_out = nullptr;         // pinned host copy when results live on the host
@@ -70,6 +72,7 @@ struct agp_server_s {
     int64_t result_bytes = 0;
     int64_t completed = 0, sweeps = 0;
     int active_lanes = 0;
+    int heavy_lanes = 0;
     // device staging for seeds
     int32_t *d_seed_lane = nullptr, *d_seed_src = nullptr;
     agp::CoefSpec *d_spec = nullptr;
@@ -88,6 +91,30 @@ namespace agp {
 namespace {
 
 constexpr int kMaxCols = 1024;
+constexpr double kHeavyCost = 1e8;     // estimated operations above which a request is "heavy"
+constexpr double kAgingUs = 1e6;       // a request's priority doubles every second it waits
+constexpr double kStarveUs = 30e6;     // a request waiting longer than this reserves the lanes it needs
+
+// Upper bound on the expected operations of a request, from the proof of Theorem 4.3:
+// E[cost] <= (1/eps) sum_{i=1..L} (Y_i / Y_0) ||P^i x||_1. The mass ||P^i x||_1 is 1 for the
+// column-stochastic presets (a = 0, b = 1 and one-hot x) and is bounded by the number of levels
+// otherwise; eps = 0 (exact) counts as the full graph per level.
+double estimate_cost(const agp_request_t &r, int64_t nnz)
+{
+    const agp_params_t &p = r.params;
+    const int L = p.L;
+    double mass;
+    const bool stochastic = p.a == 0.0 && p.b == 1.0;
+    switch (p.kind) {
+    case AGP_W_PPR: mass = stochastic ? std::min((double)L, (1.0 - p.param) / p.param) : L; break;
+    case AGP_W_HKPR: mass = stochastic ? std::min((double)L, p.param) : L; break;
+    case AGP_W_KATZ: mass = (double)L * 10.0; break;  // mass grows like (beta lambda_1)^i times the source's reach
+    default: mass = L; break;
+    }
+    const double parts = r.source >= 0 ? 1.0 : 2.0 * r.cols;
+    const double per_lane = p.eps > 0.0 ? mass / p.eps : (double)L * (double)nnz;
+    return parts * std::min(per_lane, (double)(L + 1) * (double)nnz) + 1e5;
+}
 
 void finish(agp_server_s *S, Request *q, int status)
 {
@@ -149,6 +176,7 @@ CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, do
         P.su = q->r.cols;
     }
     lane_key(p.seed, q->r.source >= 0 ? 0ull : (uint64_t)col, part, P.key0, P.key1);
+    lane_param_derive(P);
     S->ws->h_lanes[slot] = P;
     CoefSpec c{};
     c.lane = slot;
@@ -175,25 +203,64 @@ int admit(agp_server_s *S)
         }
         for (int sl : cut) S->slot_owner[sl]->cut = true;
         const double t = now_us();
-        while (!S->queue.empty()) {
-            Request *q = S->queue.front();
-            if (q->cancelled) { S->queue.pop_front(); finish(S, q, AGP_ECANCELED); continue; }
+        // cancelled and expired requests leave the queue first
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+            Request *q = *it;
+            if (q->cancelled) { finish(S, q, AGP_ECANCELED); it = S->queue.erase(it); continue; }
             if (q->r.deadline_us > 0 && t - q->t_submit > (double)q->r.deadline_us) {
-                S->queue.pop_front();
                 finish(S, q, AGP_ETIMEDOUT);
+                it = S->queue.erase(it);
                 continue;
             }
+            ++it;
+        }
+        const bool fifo = S->cfg.admission == AGP_ADMIT_FIFO;
+        // The heavy cap keeps lanes for light requests, but it only binds while another heavy
+        // request holds lanes: a request wider than the cap is still admitted once it is alone.
+        auto fits = [&](const Request *q, int need) {
+            if ((int)S->free_slots.size() < need) return false;
+            return !q->heavy || S->heavy_lanes == 0 || S->heavy_lanes + need <= (3 * S->cfg.max_lanes) / 4;
+        };
+        while (!S->queue.empty()) {
+            // FIFO: the head; cost-aware: the best priority among the requests that fit now, unless
+            // the oldest request has waited past kStarveUs, in which case nothing else is admitted
+            // until its lanes have drained free (no starvation of wide requests)
+            auto pick = S->queue.end();
+            double best = 0.0;
+            Request *oldest = S->queue.front();
+            const bool forced = !fifo && t - oldest->t_submit > kStarveUs;
+            if (forced) {
+                const int need = oldest->r.source >= 0 ? 1 : 2 * oldest->r.cols;
+                if (!fits(oldest, need)) break;
+                pick = S->queue.begin();
+            }
+            for (auto it = S->queue.begin(); !forced && it != S->queue.end(); ++it) {
+                Request *q = *it;
+                const int need = q->r.source >= 0 ? 1 : 2 * q->r.cols;
+                if (fifo) {
+                    if (fits(q, need)) pick = it;
+                    break;
+                }
+                if (!fits(q, need)) continue;
+                const double prio = q->cost / (1.0 + (t - q->t_submit) / kAgingUs);
+                if (pick == S->queue.end() || prio < best) {
+                    pick = it;
+                    best = prio;
+                }
+            }
+            if (pick == S->queue.end()) break;
+            Request *q = *pick;
             const int need = q->r.source >= 0 ? 1 : 2 * q->r.cols;
             const int64_t bytes = (int64_t)S->g->n * (q->r.source >= 0 ? 1 : q->r.cols) * (int64_t)sizeof(float);
-            if ((int)S->free_slots.size() < need) break;
             if (S->result_bytes + bytes > S->cfg.result_budget && S->result_bytes > 0) break;
-            S->queue.pop_front();
+            S->queue.erase(pick);
             q->t_admit = t;
             q->slots.clear();
             for (int k = 0; k < need; ++k) {
                 q->slots.push_back(S->free_slots.back());
                 S->free_slots.pop_back();
             }
+            if (q->heavy) S->heavy_lanes += need;
             S->result_bytes += bytes;
             q->counted = true;
             take.push_back(q);
@@ -279,6 +346,7 @@ int admit(agp_server_s *S)
         {
             std::lock_guard<std::mutex> lk(S->m);
             for (size_t k = used; k < q->slots.size(); ++k) give_back.push_back(q->slots[k]);
+            if (q->heavy) S->heavy_lanes -= (int)(q->slots.size() - used);
             q->slots.resize(used);
         }
         q->lanes_left = (int)used;
@@ -350,6 +418,7 @@ int retire(agp_server_s *S)
         {
             std::lock_guard<std::mutex> lk(S->m);
             S->free_slots.push_back(sl);
+            if (q->heavy) --S->heavy_lanes;
         }
         if (--q->lanes_left == 0) ready.push_back(q);
     }
@@ -457,11 +526,13 @@ int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **o
     if (cfg) c = *cfg;
     if (c.mode != AGP_SERVE_BATCHED && c.mode != AGP_SERVE_FIFO_PLAIN) return fail(AGP_EINVAL, "unknown serve mode");
     if (c.max_lanes < 0 || c.result_budget < 0) return fail(AGP_EINVAL, "negative limit");
+    if (c.admission != AGP_ADMIT_COST && c.admission != AGP_ADMIT_FIFO) return fail(AGP_EINVAL, "unknown admission policy");
     if (c.result_budget == 0) c.result_budget = 4ll << 30;
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     agp_server_s *S = new agp_server_s();
     S->g = g;
-    int lanes = c.max_lanes > 0 ? c.max_lanes : std::min(lane_capacity(g), 8 * wave_lanes(g));
+    // default: room for the widest feature block (2 x 64 columns) next to 8 waves of queries
+    int lanes = c.max_lanes > 0 ? c.max_lanes : std::min(lane_capacity(g), std::max(8 * wave_lanes(g), 128));
     lanes = std::max(lanes, 2);
     if (c.mode == AGP_SERVE_FIFO_PLAIN) lanes = 1;
     c.max_lanes = lanes;
@@ -533,6 +604,8 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
         q->r.X = nullptr;
     }
     q->t_submit = now_us();
+    q->cost = estimate_cost(q->r, S->g->nnz);
+    q->heavy = q->cost > kHeavyCost;
     {
         std::lock_guard<std::mutex> lk(S->m);
         if (S->fatal != AGP_OK) {

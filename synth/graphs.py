@@ -166,3 +166,85 @@ def cached(tag: str, fn, *args, **kwargs):
     np.savez(tmp, **{f"a{i}": x for i, x in enumerate(out)})
     os.replace(tmp, path)
     return out
+
+
+def chung_lu_edges_cuda(n: int, m: int, gamma: float, seed: int, device: str = "cuda", chunk: int = 1 << 27,
+                        log=None, bucket_keys: int = 1 << 30):
+    """Chung-Lu graph drawn on a CUDA device (for graphs too large to draw quickly on the host).
+
+    Same model and weights as ``chung_lu_edges``: endpoints are drawn independently by inverse
+    CDF of the capped power-law weights (torch RNG seeded with ``seed``), non-loop pairs are
+    canonicalised and deduplicated on the device, draws repeat until at least ``m`` distinct edges
+    exist and a uniformly random surplus is dropped; node ids are then randomly relabelled.
+    Pairs are spread over hash buckets of about ``bucket_keys`` (2^30) keys, so that no tensor
+    operation sees 2^31 elements or more. Returns CUDA int32 tensors ``(u, v)`` of length m. Deterministic for a
+    given seed on a given GPU model.
+    """
+    import torch
+
+    say = log or (lambda *_: None)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    w = chung_lu_weights(n, m, gamma)
+    cdf = torch.from_numpy(np.cumsum(w) / w.sum()).to(device)
+    del w
+    P = max(1, -(-int(m * 1.1) // bucket_keys))
+    parts = [torch.empty(0, dtype=torch.int64, device=device) for _ in range(P)]
+    want = int(m * 1.05) + 1024
+    while True:
+        new = [[] for _ in range(P)]
+        left = want
+        while left > 0:
+            k = min(chunk, left)
+            left -= k
+            u = torch.searchsorted(cdf, torch.rand(k, dtype=torch.float64, generator=gen, device=device), right=True)
+            v = torch.searchsorted(cdf, torch.rand(k, dtype=torch.float64, generator=gen, device=device), right=True)
+            u.clamp_(max=n - 1)
+            v.clamp_(max=n - 1)
+            lo, hi = torch.minimum(u, v), torch.maximum(u, v)
+            del u, v
+            keep = lo != hi
+            lo, hi = lo[keep], hi[keep]
+            key = lo * n + hi
+            if P == 1:
+                new[0].append(key)
+            else:
+                b = torch.remainder(lo + hi, P)
+                for p in range(P):
+                    new[p].append(key[b == p])
+                del b
+            del lo, hi, keep, key
+        count = 0
+        for p in range(P):
+            parts[p] = torch.unique(torch.cat([parts[p]] + new[p]))
+            new[p] = None
+            count += parts[p].numel()
+        say(f"[synth] {count} distinct edges after drawing {want} pairs ({P} buckets)")
+        if count >= m:
+            break
+        want = int((m - count) * 1.5) + 1024
+    surplus = count - m
+    if surplus:
+        sizes = np.array([t.numel() for t in parts], dtype=np.int64)
+        drops = np.random.default_rng(seed).multivariate_hypergeometric(sizes, surplus)
+        for p in range(P):
+            if drops[p]:
+                idx = torch.randperm(int(sizes[p]), generator=gen, device=device)[: int(drops[p])]
+                mask = torch.ones(int(sizes[p]), dtype=torch.bool, device=device)
+                mask[idx] = False
+                parts[p] = parts[p][mask]
+                del idx, mask
+    perm = torch.randperm(n, generator=gen, device=device).to(torch.int32)
+    lo = torch.empty(m, dtype=torch.int32, device=device)
+    hi = torch.empty(m, dtype=torch.int32, device=device)
+    off = 0
+    for p in range(P):
+        keys = parts[p]
+        parts[p] = None
+        c = keys.numel()
+        lo[off:off + c] = perm[keys // n]
+        hi[off:off + c] = perm[keys % n]
+        off += c
+        del keys
+    del perm
+    return lo, hi
