@@ -149,6 +149,10 @@ typedef struct {
 #define AGP_PROFILE 0x10u         /* record CUDA events around every kernel of the level loop
                                      (inside the captured graph as well); read the per-kernel
                                      device time with agp_profile_read                          */
+#define AGP_EPS_ABSOLUTE 0x20u    /* eps is in the raw units of the signal: a sign part x+- runs
+                                     with eps / ||x+-||_1 on its normalised residues. Default
+                                     (flag clear): eps applies to the normalised residues, the
+                                     convention of Section 3 and Algorithm 2                     */
 
 /*
  * Batched queries (Algorithm 2 per query). Query q has the sparse signal
@@ -180,7 +184,8 @@ AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, 
 /*
  * Feature propagation for GNNs (Section 5.2; SGC, APPNP and GDC rows of Table 1): every column
  * c of X is a graph signal, Z[:, c] = estimate of sum_i w_i (D^-a A D^-b)^i X[:, c]. Columns are
- * split into sign parts and normalised as in agp_query_batch; eps applies per normalised part.
+ * split into sign parts and normalised as in agp_query_batch; eps applies per normalised part
+ * (flags AGP_PLAIN, AGP_PROFILE and AGP_EPS_ABSOLUTE; with the last, eps is in X's raw units).
  *   X       device, n rows x d columns of bfloat16 (raw 16-bit patterns), row stride ldx >= d
  *   Z       device, n rows x d columns of FP32, row stride ldz >= d; fully written
  *   seed    of params: column c part s uses the stream (seed, c, s)
@@ -230,7 +235,8 @@ typedef struct {
                                  admitted next, nothing else starting until its slots are free      */
 } agp_serve_config_t;
 
-#define AGP_REQ_X_ON_DEVICE 0x1u /* X is a device pointer that stays valid until the request is done */
+#define AGP_REQ_X_ON_DEVICE 0x1u   /* X is a device pointer that stays valid until the request is done */
+#define AGP_REQ_EPS_ABSOLUTE 0x2u  /* eps in the raw units of the signal, as AGP_EPS_ABSOLUTE          */
 
 typedef struct {
     agp_params_t params;      /* a, b, L, weights, eps, seed                                         */

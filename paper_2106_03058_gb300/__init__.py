@@ -22,12 +22,12 @@ __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
     "feature_propagate", "katz_beta", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
-    "PLAIN", "COLLECT_STATS", "PROFILE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
-    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
+    "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
+    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
 ]
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
-INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE = 0x1, 0x2, 0x4, 0x8, 0x10
+INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
 ADD_SELF_LOOPS, EDGES_ON_DEVICE = 0x1, 0x2
 MAX_LEVELS = 64
@@ -77,7 +77,7 @@ class Result(C.Structure):
                 ("cols", C.c_int64), ("queue_us", C.c_double), ("latency_us", C.c_double)]
 
 
-SERVE_BATCHED, SERVE_FIFO_PLAIN, REQ_X_ON_DEVICE = 0, 1, 0x1
+SERVE_BATCHED, SERVE_FIFO_PLAIN, REQ_X_ON_DEVICE, REQ_EPS_ABSOLUTE = 0, 1, 0x1, 0x2
 ADMIT_COST, ADMIT_FIFO = 0, 1
 
 _lib = None
@@ -318,13 +318,14 @@ class Server:
         self.handle = h
         self._keep = {}
 
-    def submit(self, params, source=None, X=None, deadline_us=0):
+    def submit(self, params, source=None, X=None, deadline_us=0, eps_absolute=False):
         """Queue a query from `source` or a feature block X (CUDA bf16 [n, cols], read in place)."""
+        fl = REQ_EPS_ABSOLUTE if eps_absolute else 0
         if source is not None:
-            req = Request(params, int(source), 0, None, 0, int(deadline_us), 0, 0)
+            req = Request(params, int(source), 0, None, 0, int(deadline_us), fl, 0)
         else:
             req = Request(params, -1, int(X.shape[1]), X.data_ptr(), int(X.stride(0)), int(deadline_us),
-                          REQ_X_ON_DEVICE, 0)
+                          REQ_X_ON_DEVICE | fl, 0)
         t = C.c_uint64()
         _check("agp_serve_submit", lib().agp_serve_submit(self.handle, C.byref(req), C.byref(t)))
         if X is not None:
@@ -416,7 +417,7 @@ def query_sources(g, params, sources, out=None, plain=False, collect_stats=False
     return out, st
 
 
-def feature_propagate(g, params, X, Z=None, plain=False, stream=None):
+def feature_propagate(g, params, X, Z=None, plain=False, stream=None, eps_absolute=False):
     """``agp_feature_propagate``: X CUDA bfloat16 [n, d] (row stride X.stride(0)), Z CUDA float32 [n, d]."""
     import torch
     if X.dtype != torch.bfloat16 or not X.is_cuda:
@@ -425,7 +426,9 @@ def feature_propagate(g, params, X, Z=None, plain=False, stream=None):
     if Z is None:
         Z = torch.empty((n, d), dtype=torch.float32, device=X.device)
     _check("agp_feature_propagate", lib().agp_feature_propagate(g.handle, C.byref(params), X.data_ptr(), d, X.stride(0),
-                                                                 Z.data_ptr(), Z.stride(0), PLAIN if plain else 0, _stream(stream)))
+                                                                 Z.data_ptr(), Z.stride(0),
+                                                                 (PLAIN if plain else 0) | (EPS_ABSOLUTE if eps_absolute else 0),
+                                                                 _stream(stream)))
     return Z
 
 

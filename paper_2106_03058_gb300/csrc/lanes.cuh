@@ -42,6 +42,11 @@ struct LaneParam {
     int32_t screen;        // 1: decide in FP32 outside [eps_lo, eps_hi), FP64 only inside
 };
 
+// eps of a lane from an eps in raw signal units (AGP_EPS_ABSOLUTE): the lane runs on the sign part
+// x+-/||x+-||_1, whose residues are those of the raw problem divided by ||x+-||_1 (the ratios
+// Y_{i+1}/Y_i do not depend on the scale of w).
+inline double lane_eps_absolute(double eps, double norm) { return norm > 0.0 ? eps / norm : eps; }
+
 // Fill the derived fields of a lane whose eps_d, a_d and a_mode are set. For a in {1, 1/2} the FP32
 // quotient c / d^a (correctly rounded division and square root) is within 2 ulp (2.4e-7 relative) of
 // the exact value, for general 0 < a <= 1 (powf) well within 2^-16; the bracket is 2^-20 (resp.

@@ -1205,8 +1205,8 @@ struct LaneSpec {
 // uploaded from the workspace's pinned staging on stream s. The workspace must be idle (its
 // previous wave checked), which is what makes reusing the pinned staging safe without a sync.
 int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lanes, size_t first, int count,
-                 const agp_params_t *params, uint64_t stream_base_is_query, float *out, int64_t su, int64_t sr,
-                 const std::vector<int32_t> &aux, int32_t **d_aux, cudaStream_t s, int *max_L)
+                 const agp_params_t *params, uint64_t stream_base_is_query, bool eps_absolute, float *out, int64_t su,
+                 int64_t sr, const std::vector<int32_t> &aux, int32_t **d_aux, cudaStream_t s, int *max_L)
 {
     *max_L = 0;
     size_t nw = 0;
@@ -1231,8 +1231,8 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
         const LaneSpec &ls = lanes[first + l];
         const agp_params_t &p = params[ls.params];
         LaneParam &P = h_lp[l];
-        P.eps_d = p.eps;
-        P.eps = (float)p.eps;
+        P.eps_d = eps_absolute ? lane_eps_absolute(p.eps, ls.norm) : p.eps;
+        P.eps = (float)P.eps_d;
         P.a = (float)p.a;
         P.b = (float)p.b;
         P.a_d = p.a;
@@ -1305,6 +1305,7 @@ struct WaveJob {
     float *out;
     int64_t su, sr;
     uint64_t stream_base_is_query;
+    bool eps_absolute = false;  // eps in raw signal units: a lane uses eps / ||x+-||_1
     std::function<void(size_t first, int count, std::vector<int32_t> &aux)> make_aux;
     std::function<int(const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st)> seed;
 };
@@ -1364,8 +1365,8 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
         job.make_aux(first, count, aux);
         int32_t *d_aux = nullptr;
         int max_L = 0;
-        if ((rc = prepare_wave(g, W, lanes, first, count, params, job.stream_base_is_query, job.out, job.su, job.sr, aux,
-                               &d_aux, st, &max_L)) != AGP_OK)
+        if ((rc = prepare_wave(g, W, lanes, first, count, params, job.stream_base_is_query, job.eps_absolute, job.out,
+                               job.su, job.sr, aux, &d_aux, st, &max_L)) != AGP_OK)
             break;
         if ((rc = reset_ctrl(W, count, st)) != AGP_OK) break;
         const KArgs A = make_args(g, W, collect);
@@ -1411,7 +1412,8 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     if (!params || !(n_params == 1 || n_params == Q)) return fail(AGP_EINVAL, "n_params must be 1 or Q");
     if (!x_off || !pi_out) return fail(AGP_EINVAL, "x_off / pi_out NULL");
     if (ld_out < g->n) return fail(AGP_EINVAL, "ld_out < n");
-    if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE))
+    if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
+                  AGP_EPS_ABSOLUTE))
         return fail(AGP_EINVAL, "unknown flag");
     if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
     for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params(params[i]));
@@ -1500,6 +1502,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     job.su = 1;
     job.sr = ld;
     job.stream_base_is_query = 0;  // a query's random stream depends on its seed, not its position
+    job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.assign(2 * (size_t)Q, -1);
         for (int l = 0; l < count; ++l) aux[2 * lanes[first + l].query + lanes[first + l].part] = l;
@@ -1535,7 +1538,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
 {
     if (!g || !params || !X || !Z) return fail(AGP_EINVAL, "NULL argument");
     if (d < 0 || ldx < d || ldz < d) return fail(AGP_EINVAL, "need d >= 0, ldx >= d, ldz >= d");
-    if (flags & ~(AGP_PLAIN | AGP_PROFILE)) return fail(AGP_EINVAL, "unknown flag");
+    if (flags & ~(AGP_PLAIN | AGP_PROFILE | AGP_EPS_ABSOLUTE)) return fail(AGP_EINVAL, "unknown flag");
     AGP_TRY(validate_params(*params));
     const bool profile = flags & AGP_PROFILE;
     if (d == 0 || g->n == 0) return AGP_OK;
@@ -1566,6 +1569,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     job.su = ldz;
     job.sr = 1;
     job.stream_base_is_query = 1;  // column c of part s draws from the stream (seed, c, s)
+    job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.resize(2 * (size_t)count);
         for (int l = 0; l < count; ++l) {

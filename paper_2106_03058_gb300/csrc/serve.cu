@@ -159,8 +159,8 @@ CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, do
 {
     const agp_params_t &p = q->r.params;
     LaneParam P{};
-    P.eps_d = p.eps;
-    P.eps = (float)p.eps;
+    P.eps_d = (q->r.flags & AGP_REQ_EPS_ABSOLUTE) ? lane_eps_absolute(p.eps, norm) : p.eps;
+    P.eps = (float)P.eps_d;
     P.a = (float)p.a;
     P.b = (float)p.b;
     P.a_d = p.a;
@@ -593,7 +593,7 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
         q->w.assign(req->params.w, req->params.w + req->params.L + 1);
         q->r.params.w = nullptr;
     }
-    if (req->flags & ~AGP_REQ_X_ON_DEVICE) {
+    if (req->flags & ~(AGP_REQ_X_ON_DEVICE | AGP_REQ_EPS_ABSOLUTE)) {
         delete q;
         return fail(AGP_EINVAL, "unknown request flag");
     }

@@ -175,8 +175,8 @@ def chung_lu_edges_cuda(n: int, m: int, gamma: float, seed: int, device: str = "
     Same model and weights as ``chung_lu_edges``: endpoints are drawn independently by inverse
     CDF of the capped power-law weights (torch RNG seeded with ``seed``), non-loop pairs are
     canonicalised and deduplicated on the device, draws repeat until at least ``m`` distinct edges
-    exist and a uniformly random surplus is dropped; node ids are then randomly relabelled.
-    Pairs are spread over hash buckets of about ``bucket_keys`` (2^30) keys, so that no tensor
+    exist and a random surplus is dropped (uniformly within hash buckets, in proportion to their
+    sizes); node ids are then randomly relabelled. Pairs are spread over hash buckets of about ``bucket_keys`` (2^30) keys, so that no tensor
     operation sees 2^31 elements or more. Returns CUDA int32 tensors ``(u, v)`` of length m. Deterministic for a
     given seed on a given GPU model.
     """
@@ -225,8 +225,11 @@ def chung_lu_edges_cuda(n: int, m: int, gamma: float, seed: int, device: str = "
         want = int((m - count) * 1.5) + 1024
     surplus = count - m
     if surplus:
+        # the surplus is split over the buckets in proportion to their sizes (the buckets are a
+        # hash partition, so this is a uniform drop up to rounding of the split)
         sizes = np.array([t.numel() for t in parts], dtype=np.int64)
-        drops = np.random.default_rng(seed).multivariate_hypergeometric(sizes, surplus)
+        drops = (sizes * surplus) // count
+        drops[: surplus - int(drops.sum())] += 1
         for p in range(P):
             if drops[p]:
                 idx = torch.randperm(int(sizes[p]), generator=gen, device=device)[: int(drops[p])]

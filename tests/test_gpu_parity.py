@@ -357,6 +357,51 @@ def test_feature_propagation_unbiased(agp, rmat14):
     assert np.mean(np.abs(z) > 2.576) <= 0.02
 
 
+# ---------------------------------------------------------------- eps in raw signal units
+def test_eps_absolute(agp, rmat14):
+    """AGP_EPS_ABSOLUTE: a part x+- runs with eps / ||x+-||_1 on its normalised residues. Scaling the
+    signal by 4 and eps by 4 (both exact in binary) gives the same lanes and the same draws, so the
+    result is 4 times the unscaled one; without the flag, eps stays on the normalised residues."""
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    live = np.flatnonzero(np.bincount(u, minlength=n) + np.bincount(v, minlength=n))
+    srcs = live[:: max(1, len(live) // 6)][:6].astype(np.int32)
+    Q = len(srcs)
+    eps = 1e-6
+    off = torch.arange(Q + 1, dtype=torch.int64, device="cuda")
+    idx = torch.as_tensor(srcs, device="cuda")
+    F = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
+    outs = {}
+    for name, val, e, flags in (("unit", 1.0, eps, F), ("abs", 4.0, 4 * eps, F | agp.EPS_ABSOLUTE),
+                                ("rel", 4.0, eps, F)):
+        params = [agp.ppr(0.2, 12, e, seed=31 + q) for q in range(Q)]
+        out = torch.empty((Q, n), dtype=torch.float32, device="cuda")
+        x_val = torch.full((Q,), val, dtype=torch.float32, device="cuda")
+        agp.query_batch(g, params, off, idx, x_val, out, n, flags)
+        outs[name] = out.cpu().numpy()
+    for q in range(Q):
+        want = 4.0 * outs["unit"][q]
+        assert close(outs["abs"][q], want) or same_draws(outs["abs"][q], want)
+        assert close(outs["rel"][q], want) or same_draws(outs["rel"][q], want)
+    # features: doubling a BF16 column (exact) and eps doubles the result
+    X = torch.randn(n, 3, generator=torch.Generator().manual_seed(6)).to(torch.bfloat16).cuda()
+    g2 = agp.build_graph(n, u, v, add_self_loops=True)
+    Z1 = agp.feature_propagate(g2, agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=1e-4, seed=3), X,
+                               eps_absolute=True).cpu().numpy()
+    Z2 = agp.feature_propagate(g2, agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=2e-4, seed=3), X * 2,
+                               eps_absolute=True).cpu().numpy()
+    # the column norms are FP64 atomic sums, so a last-bit difference can flip a sampling decision:
+    # then the two must be equally accurate against the exact propagation
+    Z0 = agp.feature_propagate(g2, agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=0.0), X).cpu().numpy()
+    for c in range(3):
+        assert close(Z2[:, c], 2.0 * Z1[:, c]) or equally_accurate(Z2[:, c] / 2.0, Z1[:, c], Z0[:, c])
+    # and the flag does change the lane's eps: a column of norm ~ n/1.25 is far from eps = 1e-4
+    Zr = agp.feature_propagate(g2, agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=1e-4, seed=3), X).cpu().numpy()
+    assert not np.allclose(Zr, Z1)
+    g2.destroy()
+    g.destroy()
+
+
 # ---------------------------------------------------------------- error paths
 def test_errors(agp, rmat14):
     n, u, v = rmat14
