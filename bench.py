@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -388,31 +389,55 @@ def run_large(args):
     off = torch.arange(Q + 1, dtype=torch.int64, device="cuda")
     out = torch.empty((Q, n), dtype=torch.float32, device="cuda")
     w_ppr = 1.0 - 0.8 ** 31
-    w_hk = float(sum(np.exp(-5.0) * 5.0 ** i / np.prod(np.arange(1, i + 1)) for i in range(31)))
+    w_hk = float(sum(math.exp(-5.0 + i * math.log(5.0) - math.lgamma(i + 1.0)) for i in range(31)))
     flags = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
+    # wave width by timing on the first 32 PPR queries
+    qs = min(Q, 32)
+    lanes, tuned_ms = agp.autotune(g, [agp.ppr(0.2, 30, 1e-8, seed=S + q) for q in range(qs)], off[:qs + 1],
+                                   d_srcs[:qs], None, out, n, candidates=[1, 2, 4, 8, 16])
+    log(f"[large] autotuned wave width {lanes} lanes")
     res = {}
     for name, mk, mass in (("ppr", lambda sd: agp.ppr(0.2, 30, 1e-8, seed=sd), w_ppr),
                            ("hkpr", lambda sd: agp.hkpr(5.0, 30, 1e-8, seed=sd), w_hk)):
         times, masses = [], []
+        agp.profile_read(g, reset=True)
         for k in range(args.warmup + args.steps):
             params = [mk(S + 10000 * k + q) for q in range(Q)]
+            if k == args.warmup:
+                agp.profile_read(g, reset=True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            agp.query_batch(g, params, off, d_srcs[k * Q:(k + 1) * Q], None, out, n, flags)
+            agp.query_batch(g, params, off, d_srcs[k * Q:(k + 1) * Q], None, out, n,
+                            flags | (agp.PROFILE if k >= args.warmup else 0))
             e1.record()
             e1.synchronize()
             if k >= args.warmup:
                 times.append(e0.elapsed_time(e1))
                 masses.append(np.array([float(out[q].sum(dtype=torch.float64)) for q in range(Q)]))
+        kern_ms, kern_launches, _ = agp.profile_read(g, reset=True)
+        # work of one launch (same sources and seeds, counted in a separate pass)
+        k = args.warmup
+        st = agp.query_batch(g, [mk(S + 10000 * k + q) for q in range(Q)], off, d_srcs[k * Q:(k + 1) * Q], None,
+                             out, n, flags | agp.COLLECT_STATS)
+        work = np.zeros((3, 4))
+        items = 0
+        for s_ in st:
+            work += np.array([list(r) for r in s_.by_kernel], dtype=np.float64)
+            items += sum(s_.frontier[: s_.levels])
         ms = float(np.mean(times))
         mm = np.concatenate(masses)
-        log(f"[large] {name}: {ms:.1f} ms per launch of {Q} queries")
+        log(f"[large] {name}: {ms:.1f} ms per launch of {Q} queries; kernel ms {kern_ms}")
         res[name] = {"ms_per_launch": ms, "queries_per_s": Q / (ms / 1e3),
-                     "mass_expected": mass, "mass_mean": float(mm.mean()), "mass_std": float(mm.std())}
+                     "mass_expected": mass, "mass_mean": float(mm.mean()), "mass_std": float(mm.std()),
+                     "kernel_ms_per_launch": {k_: v_ / args.steps for k_, v_ in kern_ms.items()},
+                     "work_per_launch": {"frontier_items": float(items),
+                                         "deterministic_pushes": float(work[:, 0].sum()),
+                                         "sampler_trials": float(work[:, 1].sum()),
+                                         "samples_accepted": float(work[:, 2].sum())}}
     line = {"metric": "queries/s", "value": 2 * Q / ((res["ppr"]["ms_per_launch"] + res["hkpr"]["ms_per_launch"]) / 1e3),
             "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"chung-lu-2.0 n={n} m={m} ppr(0.2)+hkpr(5), L=30, eps=1e-8, {Q} uniform sources per launch",
-                       "generate_s": t_gen, "build_s": t_build},
+                       "generate_s": t_gen, "build_s": t_build, "wave_lanes": lanes, "autotune_ms": tuned_ms},
             "checks": checks, "models": res,
             "note": "a = 0, b = 1 keeps mass: E[sum pi] = sum_{i<=L} w_i for every source with degree >= 1"}
     print(json.dumps(line), flush=True)

@@ -296,10 +296,10 @@ AGP_API int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_pa
  * Kernel accounting of a graph handle since the last reset.
  *   ms[5], launches[5]  (host, may be NULL): device time in milliseconds and number of launches of
  *                       the level-loop steps measured under AGP_PROFILE, in the order
- *                       0 = compact (next-frontier bitmaps -> ascending item list, 3 kernels),
+ *                       0 = compact (residue vectors -> ascending frontier item list, 3 kernels),
  *                       1 = expand (reserve, threshold, short pushes, light sampling),
- *                       2 = push (long deterministic prefixes), 3 = sample (heavy tails),
- *                       4 = level end
+ *                       2 = push (long deterministic prefixes, per-position dense tails),
+ *                       3 = sample (sparse heavy tails), 4 = level end
  *   kernel_launches     (host, may be NULL): every kernel the library launched for this graph
  *                       (graph nodes included), with or without AGP_PROFILE
  *   reset               non-zero: clear the counters after reading

@@ -104,6 +104,7 @@ struct agp_graph_s {
     agp::Workspace *ws2 = nullptr; // second workspace: two waves in flight on two streams
     cudaStream_t side = nullptr;   // stream of the second wave slot
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_wave[2] = {nullptr, nullptr};  // end of the last wave on stream k (result copies)
     void *in_stage = nullptr;      // device staging of per-call inputs (grown on demand)
     size_t in_bytes = 0;
     double prof_ms[5] = {0, 0, 0, 0, 0};   // AGP_PROFILE: device time per level-loop step

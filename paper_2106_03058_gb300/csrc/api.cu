@@ -239,6 +239,8 @@ int agp_graph_destroy(agp_graph_t g)
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
+    for (int k = 0; k < 2; ++k)
+        if (g->ev_wave[k]) cudaEventDestroy(g->ev_wave[k]);
     cudaFree(g->rowptr);
     cudaFree(g->colidx);
     cudaFree(g->deg);

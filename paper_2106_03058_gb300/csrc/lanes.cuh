@@ -79,6 +79,8 @@ struct Ctrl {
 };
 
 constexpr int kProfKernels = 5;  // compact, expand, push, sample, level end
+constexpr int kKernelsPerLevel = 9;  // compaction 3, expansion 3 (expand, record scan, record emit),
+                                     // push, sample, level end
 constexpr int kScanUnit = 1024;  // floats of a lane's residue vector scanned by one CTA step (256 x float4)
 
 struct KArgs {
@@ -94,6 +96,8 @@ struct KArgs {
     int part_blocks;          // compaction ranges (blocks)
     float *c_item;
     int2 *k_item;             // (prefix length, tail segment length)
+    uint2 *nrec;              // per item: (prefix chunks, tail records | dense bit)
+    unsigned long long *rpart;  // [3][kGridStrideBlocks] per-block record counts / offsets
     uint2 *det_rec, *smp_rec, *dns_rec;
     unsigned long long cap_items, cap_det, cap_smp, cap_dns;
     const LaneParam *lanes;
@@ -118,6 +122,8 @@ struct Workspace {
     int part_blocks = 1;
     float *c_item = nullptr;
     int2 *k_item = nullptr;
+    uint2 *nrec = nullptr;
+    unsigned long long *rpart = nullptr;
     uint2 *det_rec = nullptr, *smp_rec = nullptr, *dns_rec = nullptr;
     LaneParam *lanes = nullptr;
     float2 *coef = nullptr;

@@ -117,20 +117,17 @@ __device__ __forceinline__ int32_t ld_col(const int32_t *p)
 // Pushes are fire-and-forget atomic adds (no value returned, so no thread waits on them). The next
 // frontier is not tracked during the pushes: each level starts by scanning the residue vectors of
 // the active lanes (see k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
-__device__ __forceinline__ void push_to(float *Rn, int32_t v, float inc)
+// Fire-and-forget FP32 add into global memory. Written as red.global explicitly: for a pointer
+// loaded from memory (an output row of the lane parameters) the compiler cannot prove the global
+// space and would issue a returning generic atomic, which the warp waits for.
+__device__ __forceinline__ void red_add(float *p, float v)
 {
-    if (inc != 0.f) atomicAdd(Rn + v, inc);
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
 }
 
-// Reserve `count` consecutive slots of a record list with one atomic per coalesced group.
-__device__ __forceinline__ unsigned long long reserve_records(unsigned long long *counter, unsigned int count)
+__device__ __forceinline__ void push_to(float *Rn, int32_t v, float inc)
 {
-    cg::coalesced_group grp = cg::coalesced_threads();
-    const unsigned int before = cg::exclusive_scan(grp, count);
-    unsigned long long base = 0;
-    if (grp.thread_rank() == grp.size() - 1) base = atomicAdd(counter, (unsigned long long)(before + count));
-    base = grp.shfl(base, grp.size() - 1);
-    return base + before;
+    if (inc != 0.f) red_add(Rn + v, inc);
 }
 
 struct Uniforms {
@@ -152,6 +149,7 @@ struct Uniforms {
 };
 
 // Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane.
+template <int kSampleBatch>
 __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int lane, int32_t u, int lvl, uint32_t seg,
                              const int32_t *row, int j0, int j1, float c, unsigned long long &drawn,
                              unsigned long long &accepted, int kern)
@@ -179,24 +177,46 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int 
         }
         pstar = fminf(pstar, 1.f);
         if (!(pstar > 0.f)) { j = gend; continue; }
-        // geometric skip: floor(ln U / ln(1 - p*)) positions are passed over before the next trial
+        // geometric skip: floor(ln U / ln(1 - p*)) positions are passed over before the next trial.
+        // Trials are taken kSampleBatch at a time: their uniforms are drawn first, in the order of
+        // one trial after the other (skip, then the acceptance uniform when a > 0), so that the
+        // neighbour loads of a batch are in flight together.
         const float rlq = (pstar < 1.f) ? 1.f / log1pf(-pstar) : 0.f;
-        while (true) {
-            const float skip = (pstar < 1.f) ? floorf(logf(U.next()) * rlq) : 0.f;
-            if (!(skip < (float)(gend - j))) { j = gend; break; }
-            j += (int)skip;
-            ++drawn;
-            const int32_t v = ld_col(row + j);
-            bool keep = true;
-            if (P.a_mode != 0) {
-                const float pv = apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
-                keep = U.next() * pstar < pv;
+        bool more = true;
+        while (more) {
+            int pos[kSampleBatch];
+            float acc[kSampleBatch];
+            int cnt = 0;
+#pragma unroll
+            for (int t = 0; t < kSampleBatch; ++t) {
+                if (!more) continue;
+                const float skip = (pstar < 1.f) ? floorf(logf(U.next()) * rlq) : 0.f;
+                if (!(skip < (float)(gend - j))) {
+                    j = gend;
+                    more = false;
+                    continue;
+                }
+                j += (int)skip;
+                pos[t] = j;
+                acc[t] = (P.a_mode != 0) ? U.next() : 0.f;
+                cnt = t + 1;
+                if (++j >= gend) more = false;
             }
-            if (keep) {
-                ++accepted;
-                push_to(Rn, v, P.eps);
+            int32_t v[kSampleBatch];
+#pragma unroll
+            for (int t = 0; t < kSampleBatch; ++t)
+                if (t < cnt) v[t] = ld_col(row + pos[t]);
+#pragma unroll
+            for (int t = 0; t < kSampleBatch; ++t) {
+                if (t >= cnt) continue;
+                ++drawn;
+                bool keep = true;
+                if (P.a_mode != 0) keep = acc[t] * pstar < apply_deg(ce, A.g.deg[v[t]], P.a_mode, P.a);
+                if (keep) {
+                    ++accepted;
+                    push_to(Rn, v[t], P.eps);
+                }
             }
-            if (++j >= gend) break;
         }
     }
 }
@@ -357,7 +377,12 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
     }
 }
 
-__device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long idx)
+// Record counts of one frontier item: x = long-prefix chunks, y = tail records (bit 31 set: dense
+// per-position chunks; clear: sparse segments). Written for every item; k_rec_* turn them into
+// record lists without a shared counter.
+constexpr uint32_t kDenseBit = 0x80000000u;
+
+__device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long idx)
 {
     Ctrl *ctrl = A.ctrl;
     // every array read here is written only by earlier kernels: read-only path
@@ -370,22 +395,23 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
     const int lvl = __ldg(A.level + lane);
     if (lvl < 0 || lvl >= kMaxLevels) {
         atomicOr(&ctrl->error, 16u);
-        return;
+        return make_uint2(0u, 0u);
     }
     const LaneParam &P = A.lanes[lane];
     float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
     const float2 cf = __ldg(A.coef + lane * kMaxLevels + lvl);
     // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
-    atomicAdd(P.out + (int64_t)u * P.su, cf.x * r);
-    if (lvl >= P.L) return;
-    if (d == 0) return;
+    red_add(P.out + (int64_t)u * P.su, cf.x * r);
+    if (lvl >= P.L || d == 0) return make_uint2(0u, 0u);
     const float c = apply_deg(cf.y * r, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
-    if (!(c > 0.f)) return;
+    if (!(c > 0.f)) return make_uint2(0u, 0u);
     const int32_t *row = A.g.colidx + e0;
     const int k = det_prefix(c, P, row, d, A.g.deg);
     unsigned long long drawn = 0, accepted = 0;
+    uint2 nrec = make_uint2(0u, 0u);
     if (k > 0) {
         if (k <= kInlineDet) {
+#pragma unroll 4
             for (int j = 0; j < k; ++j) {
                 const int32_t v = ld_col(row + j);
                 const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
@@ -393,45 +419,28 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
             }
             if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
         } else {
-            const unsigned int nrec = (unsigned int)((k + kChunk - 1) / kChunk);
-            const unsigned long long base = reserve_records(&ctrl->n_det, nrec);
-            for (unsigned int t = 0; t < nrec; ++t) {
-                if (base + t < A.cap_det) A.det_rec[base + t] = make_uint2((uint32_t)idx, t);
-                else atomicOr(&ctrl->error, 2u);
-            }
+            nrec.x = (unsigned int)((k + kChunk - 1) / kChunk);
         }
     }
     const int tail = d - k;
     int seglen = 0;
-    bool dense = false;
     if (tail > 0) {
         const float ce = c * P.inv_eps;
         const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
         const float expect = p0 * (float)tail;  // upper bound on the trials reached
         if (expect <= kLightSamples) {
-            sample_range(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, drawn, accepted, 0);
+            sample_range<2>(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, drawn, accepted, 0);
         } else if (p0 >= kDenseP) {
             // most positions are kept: one Bernoulli per position, by warps, coalesced colidx reads
-            dense = true;
-            const unsigned int nrec = (unsigned int)((tail + kChunk - 1) / kChunk);
-            const unsigned long long base = reserve_records(&ctrl->n_dns, nrec);
-            for (unsigned int t = 0; t < nrec; ++t) {
-                if (base + t < A.cap_dns) A.dns_rec[base + t] = make_uint2((uint32_t)idx, t);
-                else atomicOr(&ctrl->error, 8u);
-            }
+            nrec.y = kDenseBit | (unsigned int)((tail + kChunk - 1) / kChunk);
         } else {
             int nseg = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
             nseg = max(nseg, 1);
             seglen = (tail + nseg - 1) / nseg;
-            nseg = (tail + seglen - 1) / seglen;
-            const unsigned long long base = reserve_records(&ctrl->n_smp, (unsigned int)nseg);
-            for (int t = 0; t < nseg; ++t) {
-                if (base + t < A.cap_smp) A.smp_rec[base + t] = make_uint2((uint32_t)idx, (uint32_t)t);
-                else atomicOr(&ctrl->error, 4u);
-            }
+            nrec.y = (unsigned int)((tail + seglen - 1) / seglen);
         }
     }
-    if (k > kInlineDet || seglen > 0 || dense) {
+    if (nrec.x | nrec.y) {
         A.c_item[idx] = c;
         A.k_item[idx] = make_int2(k, seglen);
     }
@@ -439,14 +448,151 @@ __device__ __forceinline__ void expand_item(const KArgs &A, unsigned long long i
         atomicAdd(&A.stats[lane].by_kernel[0][1], drawn);
         atomicAdd(&A.stats[lane].by_kernel[0][2], accepted);
     }
+    return nrec;
+}
+
+// Items are split into contiguous block ranges, a multiple of kBlock long (k_rec_emit walks the
+// same ranges). Returns [begin, end) of this block.
+__device__ __forceinline__ void item_range(const KArgs &A, unsigned long long &begin, unsigned long long &end)
+{
+    const unsigned long long n = min(A.ctrl->n_items, A.cap_items);
+    const unsigned long long per = ((n + gridDim.x - 1) / gridDim.x + kBlock - 1) / kBlock * kBlock;
+    begin = (unsigned long long)blockIdx.x * per;
+    end = min(n, begin + per);
+}
+
+__device__ __forceinline__ void rec_split(uint2 nr, unsigned int &det, unsigned int &dns, unsigned int &smp)
+{
+    det = nr.x;
+    dns = (nr.y & kDenseBit) ? (nr.y & ~kDenseBit) : 0u;
+    smp = (nr.y & kDenseBit) ? 0u : nr.y;
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
 {
-    const unsigned long long n_items = min(A.ctrl->n_items, A.cap_items);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < n_items; idx += stride)
-        expand_item(A, idx);
+    __shared__ unsigned long long tot_s[3][kBlock / 32];
+    unsigned long long begin, end;
+    item_range(A, begin, end);
+    // per-thread record totals (32-bit: a thread's items have far fewer than 2^32 records; the
+    // block sums are 64-bit)
+    unsigned int tot[3] = {0u, 0u, 0u};
+    for (unsigned long long idx = begin + threadIdx.x; idx < end; idx += kBlock) {
+        const uint2 nr = expand_item(A, idx);
+        A.nrec[idx] = nr;
+        unsigned int det, dns, smp;
+        rec_split(nr, det, dns, smp);
+        tot[0] += det;
+        tot[1] += dns;
+        tot[2] += smp;
+    }
+    // block totals of the three record kinds, for k_rec_scan
+    unsigned long long wt[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        wt[t] = tot[t];
+        for (int o = 16; o > 0; o >>= 1) wt[t] += __shfl_down_sync(0xffffffffu, wt[t], o);
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int t = 0; t < 3; ++t) tot_s[t][threadIdx.x >> 5] = wt[t];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        unsigned long long s = 0;
+        for (int w = 0; w < kBlock / 32; ++w) s += tot_s[threadIdx.x][w];
+        A.rpart[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// One block: exclusive scan of the per-block record counts of k_expand (three kinds, each a row of
+// nb entries); the totals become the record list sizes.
+__global__ void k_rec_scan(KArgs A, int nb)
+{
+    __shared__ unsigned long long sums[1024];
+    const int t = threadIdx.x;
+    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
+    for (int kind = 0; kind < 3; ++kind) {
+        unsigned long long *row = A.rpart + (size_t)kind * nb;
+        unsigned long long s = 0;
+        for (int b = b0; b < b1; ++b) s += row[b];
+        sums[t] = s;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long run = 0;
+            for (int k = 0; k < (int)blockDim.x; ++k) {
+                const unsigned long long v = sums[k];
+                sums[k] = run;
+                run += v;
+            }
+            if (kind == 0) A.ctrl->n_det = run;
+            else if (kind == 1) A.ctrl->n_dns = run;
+            else A.ctrl->n_smp = run;
+        }
+        __syncthreads();
+        unsigned long long run = sums[t];
+        for (int b = b0; b < b1; ++b) {
+            const unsigned long long v = row[b];
+            row[b] = run;
+            run += v;
+        }
+        __syncthreads();
+    }
+}
+
+// Writes the records of every item at its block's offset plus its place in the block: prefix
+// chunks (item, chunk), dense-tail chunks (item, chunk) and sparse segments (item, segment), in
+// item order. Same grid and ranges as k_expand.
+__global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
+{
+    __shared__ unsigned int wsum[2][3][kBlock / 32];
+    unsigned long long begin, end;
+    item_range(A, begin, end);
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long base[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) base[t] = A.rpart[(size_t)t * gridDim.x + blockIdx.x];
+    int parity = 0;
+    for (unsigned long long tile = begin; tile < end; tile += kBlock, parity ^= 1) {
+        const unsigned long long idx = tile + threadIdx.x;
+        unsigned int cnt[3] = {0u, 0u, 0u};
+        if (idx < end) rec_split(A.nrec[idx], cnt[0], cnt[1], cnt[2]);
+        unsigned int x[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            x[t] = cnt[t];  // inclusive warp scan
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xffffffffu, x[t], o);
+                if (lane_id >= o) x[t] += y;
+            }
+            if (lane_id == 31) wsum[parity][t][warp] = x[t];
+        }
+        __syncthreads();
+        unsigned long long off[3], total[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            unsigned long long before = 0, all = 0;
+            for (int w = 0; w < kBlock / 32; ++w) {
+                const unsigned int v = wsum[parity][t][w];
+                if (w < warp) before += v;
+                all += v;
+            }
+            off[t] = base[t] + before + x[t] - cnt[t];
+            total[t] = all;
+        }
+        for (unsigned int r = 0; r < cnt[0]; ++r) {
+            if (off[0] + r < A.cap_det) A.det_rec[off[0] + r] = make_uint2((uint32_t)idx, r);
+            else atomicOr(&A.ctrl->error, 2u);
+        }
+        for (unsigned int r = 0; r < cnt[1]; ++r) {
+            if (off[1] + r < A.cap_dns) A.dns_rec[off[1] + r] = make_uint2((uint32_t)idx, r);
+            else atomicOr(&A.ctrl->error, 8u);
+        }
+        for (unsigned int r = 0; r < cnt[2]; ++r) {
+            if (off[2] + r < A.cap_smp) A.smp_rec[off[2] + r] = make_uint2((uint32_t)idx, r);
+            else atomicOr(&A.ctrl->error, 4u);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) base[t] += total[t];
+    }
 }
 
 // Per-position subset sampling of tail positions [k + chunk * kChunk, ...) of a dense tail: every
@@ -498,6 +644,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         if (det) {
             const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
+#pragma unroll 4
             for (int j = j0 + lane_id; j < j1; j += 32) {
                 const int32_t v = ld_col(row + j);
                 const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
@@ -533,7 +680,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         const int j0 = ks.x + (int)R.y * ks.y, j1 = min(d, j0 + ks.y);
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         unsigned long long drawn = 0, accepted = 0;
-        sample_range(A, P, Rn, lane, u, lvl, R.y, row, j0, j1, c, drawn, accepted, 2);
+        sample_range<4>(A, P, Rn, lane, u, lvl, R.y, row, j0, j1, c, drawn, accepted, 2);
         if (A.collect && (drawn | accepted)) {
             atomicAdd(&A.stats[lane].by_kernel[2][1], drawn);
             atomicAdd(&A.stats[lane].by_kernel[2][2], accepted);
@@ -799,9 +946,9 @@ size_t bytes_per_lane(const agp_graph_s *g)
 {
     const size_t n = (size_t)g->n;
     const double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
-    // R (4) + items (4) + r values (4) + c (4) + k (8) + prefix-chunk, dense-tail-chunk and
-    // segment records (8 each, with the extra records of long rows) per (lane, node)
-    return n * (4 + 4 + 4 + 4 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
+    // R (4) + items (4) + r values (4) + c (4) + k (8) + record counts (8) + prefix-chunk,
+    // dense-tail-chunk and segment records (8 each, with the extra records of long rows) per (lane, node)
+    return n * (4 + 4 + 4 + 4 + 8 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
 int lane_capacity(const agp_graph_s *g)
@@ -825,6 +972,8 @@ void free_workspace(Workspace *ws)
     cudaFree(ws->part);
     cudaFree(ws->c_item);
     cudaFree(ws->k_item);
+    cudaFree(ws->nrec);
+    cudaFree(ws->rpart);
     cudaFree(ws->det_rec);
     cudaFree(ws->smp_rec);
     cudaFree(ws->dns_rec);
@@ -890,6 +1039,8 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     A(dev_alloc(&ws->part, (size_t)ws->part_blocks + 1, acc));
     A(dev_alloc(&ws->c_item, ws->cap_items, acc));
     A(dev_alloc(&ws->k_item, ws->cap_items, acc));
+    A(dev_alloc(&ws->nrec, ws->cap_items, acc));
+    A(dev_alloc(&ws->rpart, (size_t)3 * kGridStrideBlocks, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
     A(dev_alloc(&ws->dns_rec, ws->cap_dns, acc));
@@ -998,6 +1149,8 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.part_blocks = ws->part_blocks;
     A.c_item = ws->c_item;
     A.k_item = ws->k_item;
+    A.nrec = ws->nrec;
+    A.rpart = ws->rpart;
     A.det_rec = ws->det_rec;
     A.smp_rec = ws->smp_rec;
     A.dns_rec = ws->dns_rec;
@@ -1025,12 +1178,21 @@ int ensure_events(Workspace *ws)
     return AGP_OK;
 }
 
-// Frontier compaction: bitmaps of the lanes -> ascending item list, size in ctrl->n_items.
+// Frontier compaction: residue vectors of the lanes -> ascending item list, size in ctrl->n_items.
 void launch_compact(const KArgs &A, cudaStream_t s)
 {
     k_compact_count<<<A.part_blocks, kBlock, 0, s>>>(A);
     k_compact_scan<<<1, 1024, 0, s>>>(A);
     k_compact_emit<<<A.part_blocks, kBlock, 0, s>>>(A);
+}
+
+// Expansion and its record lists (sizes in ctrl->n_det, n_dns, n_smp). k_expand and k_rec_emit
+// must run on the same grid: they walk the same item ranges.
+void launch_expand(const KArgs &A, cudaStream_t s)
+{
+    k_expand<<<kGridStrideBlocks, kBlock, 0, s>>>(A);
+    k_rec_scan<<<1, 1024, 0, s>>>(A, kGridStrideBlocks);
+    k_rec_emit<<<kGridStrideBlocks, kBlock, 0, s>>>(A);
 }
 
 // One level: compact, expand, push, sample, level end. With `ev` (profiling) every step is
@@ -1044,7 +1206,7 @@ void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_bl
     if (ev) rec(ev[0][0]);
     launch_compact(A, s);
     if (ev) { rec(ev[0][1]); rec(ev[1][0]); }
-    k_expand<<<expand_blocks, kBlock, 0, s>>>(A);
+    launch_expand(A, s);
     if (ev) { rec(ev[1][1]); rec(ev[2][0]); }
     k_push<<<push_blocks, kBlock, 0, s>>>(A);
     if (ev) { rec(ev[2][1]); rec(ev[3][0]); }
@@ -1147,14 +1309,14 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             const unsigned long long items = std::min(ws->h_ctrl->n_items, ws->cap_items);
             if (items == 0) break;
             rec(1, 0);
-            k_expand<<<blocks_for(items, kBlock), kBlock, 0, s>>>(A);
+            launch_expand(A, s);
             rec(1, 1);
             ran[lvl * kProfKernels + 1] = true;
             AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
             AGP_CUDA_TRY(cudaStreamSynchronize(s));
             const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det) + std::min(ws->h_ctrl->n_dns, ws->cap_dns),
                                      ns = std::min(ws->h_ctrl->n_smp, ws->cap_smp);
-            __atomic_fetch_add(&g->kernel_launches, (int64_t)(2 + (nd ? 1 : 0) + (ns ? 1 : 0)), __ATOMIC_RELAXED);
+            __atomic_fetch_add(&g->kernel_launches, (int64_t)(4 + (nd ? 1 : 0) + (ns ? 1 : 0)), __ATOMIC_RELAXED);
             if (nd) { rec(2, 0); k_push<<<blocks_for(nd, kBlock / 32), kBlock, 0, s>>>(A); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
             if (ns) { rec(3, 0); k_sample<<<blocks_for(ns, kBlock), kBlock, 0, s>>>(A); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
             rec(4, 0);
@@ -1180,7 +1342,7 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         ws->graph_profile = (int)profile;
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
-    __atomic_fetch_add(&g->kernel_launches, (int64_t)(7 * (max_L + 1)), __ATOMIC_RELAXED);
+    __atomic_fetch_add(&g->kernel_launches, (int64_t)(kKernelsPerLevel * (max_L + 1)), __ATOMIC_RELAXED);
     ws->prof_levels = profile ? max_L + 1 : 0;  // read when the wave is checked
     return AGP_OK;
 }
@@ -1308,6 +1470,9 @@ struct WaveJob {
     bool eps_absolute = false;  // eps in raw signal units: a lane uses eps / ||x+-||_1
     std::function<void(size_t first, int count, std::vector<int32_t> &aux)> make_aux;
     std::function<int(const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st)> seed;
+    // optional: called on the wave's stream after its levels, once every earlier wave is complete
+    // on that stream too (result rows that are final can be copied out while later waves compute)
+    std::function<int(size_t first, int count, cudaStream_t st)> after_wave;
 };
 
 // Runs the waves (G lanes each) of a call. Unless the call is on the plain path or on a fixed
@@ -1373,6 +1538,12 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
         if ((rc = job.seed(A, count, d_aux, st)) != AGP_OK) break;
         __atomic_fetch_add(&g->kernel_launches, (int64_t)2, __ATOMIC_RELAXED);  // coefficients + seed
         if ((rc = run_levels(g, W, A, max_L, plain, profile, st)) != AGP_OK) break;
+        if (job.after_wave) {
+            if (!g->ev_wave[k]) AGP_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_wave[k], cudaEventDisableTiming));
+            if (two && w > 0) AGP_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_wave[k ^ 1], 0));
+            if ((rc = job.after_wave(first, count, st)) != AGP_OK) break;
+            AGP_CUDA_TRY(cudaEventRecord(g->ev_wave[k], st));
+        }
         W->pending = true;
         wfirst[k] = first;
         wcount[k] = count;
@@ -1514,11 +1685,27 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
         AGP_CUDA_TRY(cudaGetLastError());
         return AGP_OK;
     };
+    // host output: the rows of the queries whose lanes have all run are copied after each wave, on
+    // that wave's stream, so the copies overlap the next waves (lanes are sorted by query)
+    int64_t next_q = 0;
+    auto copy_rows = [&](int64_t q_end, cudaStream_t st) -> int {
+        if (n > 0 && q_end > next_q)
+            AGP_CUDA_TRY(cudaMemcpy2DAsync(pi_out + next_q * ld_out, sizeof(float) * ld_out, out + next_q * n,
+                                           sizeof(float) * n, sizeof(float) * n, (size_t)(q_end - next_q),
+                                           cudaMemcpyDeviceToHost, st));
+        next_q = std::max(next_q, q_end);
+        return AGP_OK;
+    };
+    if (host_out)
+        job.after_wave = [&](size_t first, int count, cudaStream_t st) -> int {
+            const size_t end = first + (size_t)count;
+            return copy_rows(end < lanes.size() ? (int64_t)lanes[end].query : (int64_t)Q, st);
+        };
     AGP_TRY(run_waves(g, ctx, ws, lanes, params, G, plain, profile, collect, stats, s, job));
     if (collect)
         for (int q = 0; q < Q; ++q) stats[q].levels = params[n_params == 1 ? 0 : q].L + 1;
     if (host_out) {
-        if (n > 0) AGP_CUDA_TRY(cudaMemcpy2DAsync(pi_out, sizeof(float) * ld_out, out, sizeof(float) * n, sizeof(float) * n, Q, cudaMemcpyDeviceToHost, s));
+        AGP_TRY(copy_rows(Q, s));  // queries without lanes (zero signals) after the last wave
         AGP_CUDA_TRY(cudaStreamSynchronize(s));
     }
     AGP_CUDA_TRY(cudaGetLastError());

@@ -156,6 +156,16 @@ def test_eps0_signed_sparse_signal_and_finite_weights(agp, rmat14):
         pp = oracle.basic(og, 0.5, 0.5, 4, wl, Y, xp) if xp.any() else np.zeros(n)
         pm = oracle.basic(og, 0.5, 0.5, 4, wl, Y, xm) if xm.any() else np.zeros(n)
         _assert_rel(out[q], pp - pm, scale=np.abs(pp) + np.abs(pm))
+    # waves of one and two lanes: sign parts of a query straddle waves, the empty query has none,
+    # and host rows are copied after each wave (pinned and pageable host buffers)
+    for lanes in (1, 2):
+        g.set_wave_lanes(lanes)
+        for pinned in (False, True):
+            o2 = torch.zeros((Q, n), dtype=torch.float32, pin_memory=True).numpy() if pinned else np.zeros((Q, n), np.float32)
+            agp.query_batch(g, p, off, idx, val, o2)
+            for q in range(Q):
+                assert close(o2[q], out[q]) and (sizes[q] > 0 or not o2[q].any())
+    g.set_wave_lanes(0)
 
 
 def test_frontier_sets_bit_exact(agp, rmat14):
