@@ -45,6 +45,12 @@ HBM_FALLBACK_GBS = 6800.0
 #   accepted sample:        residue atomic RMW 8
 B_ITEM, B_DET, B_TRIAL, B_ACC, B_DEG, B_COMPACT_ITEM, B_SCAN = 28, 12, 4, 8, 4, 12, 8
 
+# DRAM traffic of k_push per L2 reduction, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over lts__t_sectors_srcunit_tex_op_red.sum, all 52 k_push launches of a step
+# of 8 Katz + 8 transition sources at four lanes per wave, warm L2). It scales a launch of the bench
+# step by its reductions; it holds for this kernel version and a four-lane wave only.
+PUSH_DRAM_BYTES_PER_RED, PUSH_TRAFFIC_LANES = 11.005, 4
+
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
@@ -694,6 +700,9 @@ def main():
     else:
         peak, peak_src = HBM_FALLBACK_GBS, "fallback"
     edge_ops = work[:, 0].sum() + work[:, 2].sum()
+    traffic = None
+    if dom == "push" and lanes == PUSH_TRAFFIC_LANES:
+        traffic = PUSH_DRAM_BYTES_PER_RED * (work[1, 0] + work[1, 2]) / launches
     # k_push is bound by random FP32 atomic adds into residue vectors that stay in L2, not by HBM:
     # its adds per second against a library scatter-add of the same shape on this GPU
     atomics = None
@@ -766,7 +775,7 @@ def main():
                                                                 for i_, k_ in enumerate(("expand", "push", "sample"))}},
             "plain_path": plain_qps,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": bytes_k[dom] / launches, "avg_launch_ms": avg_ms},
             "l2_atomics": atomics,
             "kernel_ms": kern_ms, "kernel_launches_profiled": kern_launches,

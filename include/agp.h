@@ -189,6 +189,7 @@ AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, 
  *   X       device, n rows x d columns of bfloat16 (raw 16-bit patterns), row stride ldx >= d
  *   Z       device, n rows x d columns of FP32, row stride ldz >= d; fully written
  *   seed    of params: column c part s uses the stream (seed, c, s)
+ * d = 0 (or n = 0) returns AGP_OK without touching X or Z, which may then be NULL.
  * Errors as agp_query_batch.
  */
 AGP_API int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, const uint16_t *X,

@@ -249,6 +249,33 @@ __device__ __forceinline__ int nz4(float4 v)
     return (v.x != 0.f) + (v.y != 0.f) + (v.z != 0.f) + (v.w != 0.f);
 }
 
+// Exclusive scan across a block of 1024 threads (32 warps): warp shuffles, then one warp scans the
+// warp totals. `sm` holds 32 entries; *total receives the block sum. Contains two barriers; the
+// caller must not reuse `sm` before a further barrier.
+__device__ __forceinline__ unsigned long long block_scan_1024(unsigned long long v, unsigned long long *sm,
+                                                               unsigned long long *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = sm[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sm[lane] = w;  // inclusive prefix of the warp totals
+    }
+    __syncthreads();
+    *total = sm[31];
+    return (warp > 0 ? sm[warp - 1] : 0ull) + x - v;
+}
+
 __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
 {
     __shared__ unsigned long long red[kBlock / 32];
@@ -271,33 +298,24 @@ __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
     }
 }
 
-// Pass 2 (one block): exclusive scan of the range counts; the total is the frontier size.
-__global__ void k_compact_scan(KArgs A)
+// Pass 2 (one block of 1024 threads): exclusive scan of the range counts; the total is the
+// frontier size.
+__global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
 {
-    __shared__ int64_t sums[1024];
+    __shared__ unsigned long long sm[32];
     const int t = threadIdx.x, nb = A.part_blocks;
     const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
-    int64_t s = 0;
-    for (int b = b0; b < b1; ++b) s += A.part[b];
-    sums[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        int64_t run = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            const int64_t v = sums[k];
-            sums[k] = run;
-            run += v;
-        }
-        A.ctrl->n_items = (unsigned long long)run;
-    }
-    __syncthreads();
-    int64_t run = sums[t];
+    const int b0 = min(nb, t * chunk), b1 = min(nb, b0 + chunk);
+    unsigned long long s = 0;
+    for (int b = b0; b < b1; ++b) s += (unsigned long long)A.part[b];
+    unsigned long long total;
+    unsigned long long run = block_scan_1024(s, sm, &total);
     for (int b = b0; b < b1; ++b) {
         const int64_t v = A.part[b];
-        A.part[b] = run;
-        run += v;
+        A.part[b] = (int64_t)run;
+        run += (unsigned long long)v;
     }
+    if (t == 0) A.ctrl->n_items = total;
 }
 
 // Pass 3: units are taken four at a time. The four float4 loads of a thread are issued together,
@@ -502,39 +520,31 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
     }
 }
 
-// One block: exclusive scan of the per-block record counts of k_expand (three kinds, each a row of
-// nb entries); the totals become the record list sizes.
-__global__ void k_rec_scan(KArgs A, int nb)
+// One block of 1024 threads: exclusive scan of the per-block record counts of k_expand (three kinds,
+// each a row of nb entries); the totals become the record list sizes.
+__global__ void __launch_bounds__(1024) k_rec_scan(KArgs A, int nb)
 {
-    __shared__ unsigned long long sums[1024];
+    __shared__ unsigned long long sm[32];
     const int t = threadIdx.x;
     const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
+    const int b0 = min(nb, t * chunk), b1 = min(nb, b0 + chunk);
     for (int kind = 0; kind < 3; ++kind) {
         unsigned long long *row = A.rpart + (size_t)kind * nb;
         unsigned long long s = 0;
         for (int b = b0; b < b1; ++b) s += row[b];
-        sums[t] = s;
-        __syncthreads();
-        if (t == 0) {
-            unsigned long long run = 0;
-            for (int k = 0; k < (int)blockDim.x; ++k) {
-                const unsigned long long v = sums[k];
-                sums[k] = run;
-                run += v;
-            }
-            if (kind == 0) A.ctrl->n_det = run;
-            else if (kind == 1) A.ctrl->n_dns = run;
-            else A.ctrl->n_smp = run;
-        }
-        __syncthreads();
-        unsigned long long run = sums[t];
+        unsigned long long total;
+        unsigned long long run = block_scan_1024(s, sm, &total);
         for (int b = b0; b < b1; ++b) {
             const unsigned long long v = row[b];
             row[b] = run;
             run += v;
         }
-        __syncthreads();
+        if (t == 0) {
+            if (kind == 0) A.ctrl->n_det = total;
+            else if (kind == 1) A.ctrl->n_dns = total;
+            else A.ctrl->n_smp = total;
+        }
+        __syncthreads();  // sm is reused by the next kind
     }
 }
 
@@ -1723,12 +1733,13 @@ int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t
 int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, const uint16_t *X, int64_t d,
                           int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t s)
 {
-    if (!g || !params || !X || !Z) return fail(AGP_EINVAL, "NULL argument");
+    if (!g || !params) return fail(AGP_EINVAL, "NULL argument");
     if (d < 0 || ldx < d || ldz < d) return fail(AGP_EINVAL, "need d >= 0, ldx >= d, ldz >= d");
     if (flags & ~(AGP_PLAIN | AGP_PROFILE | AGP_EPS_ABSOLUTE)) return fail(AGP_EINVAL, "unknown flag");
     AGP_TRY(validate_params(*params));
     const bool profile = flags & AGP_PROFILE;
-    if (d == 0 || g->n == 0) return AGP_OK;
+    if (d == 0 || g->n == 0) return AGP_OK;  // nothing to read or write: X and Z may be NULL
+    if (!X || !Z) return fail(AGP_EINVAL, "NULL argument");
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     const bool plain = flags & AGP_PLAIN;
     const int64_t n = g->n;

@@ -412,6 +412,56 @@ def test_eps_absolute(agp, rmat14):
     g.destroy()
 
 
+# ---------------------------------------------------------------- degenerate cases
+def test_degenerate_cases(agp, rmat14):
+    """Empty batch, L = 0, the largest L, isolated sources, a one-node graph, zero feature columns and
+    an eps so large that nothing is pushed deterministically, each against what Algorithm 2 gives."""
+    n, u, v = rmat14
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    # an extra isolated node n (no edges), so d_s = 0 for s = n
+    g = agp.build_graph(n + 1, u, v)
+    og = oracle.build_csr(n + 1, u, v)
+    s_live = int(np.argmax(deg))
+    # Q = 0: nothing to do
+    out0 = torch.empty((0, n + 1), dtype=torch.float32, device="cuda")
+    agp.query_sources(g, [], [], out=out0)
+    # L = 0: pi = w_0 x (PPR: alpha e_s)
+    out, _ = agp.query_sources(g, agp.ppr(0.2, 0, 1e-6), [s_live])
+    want = np.zeros(n + 1); want[s_live] = 0.2
+    _assert_rel(out[0].cpu().numpy(), want)
+    # isolated source: its residue is reserved and never pushed (D^-1 := 0), pi = w_0 e_s
+    out, _ = agp.query_sources(g, agp.ppr(0.2, 20, 0.0), [n])
+    want = np.zeros(n + 1); want[n] = 0.2
+    _assert_rel(out[0].cpu().numpy(), want)
+    # the largest L (63) at eps = 0 against the oracle; L = 64 is rejected
+    w, Y = oracle.tail_sums(oracle.PPR, 63, 0.2)
+    x = np.zeros(n + 1); x[s_live] = 1.0
+    out, _ = agp.query_sources(g, agp.ppr(0.2, 63, 0.0), [s_live])
+    _assert_rel(out[0].cpu().numpy(), oracle.basic(og, 0.0, 1.0, 63, w, Y, x))
+    with pytest.raises(agp.AgpError):
+        agp.query_sources(g, agp.ppr(0.2, 64, 0.0), [s_live])
+    # eps = 1: every increment c / d_v^a < 1 is sampled; the estimate is still unbiased in total mass
+    outs, _ = agp.query_sources(g, [agp.ppr(0.2, 6, 1.0, seed=k) for k in range(400)], [s_live] * 400)
+    mass = outs.sum(1, dtype=torch.float64).cpu().numpy()
+    expect = 1.0 - 0.8 ** 7
+    assert abs(mass.mean() - expect) < 4 * mass.std(ddof=1) / np.sqrt(400) + 1e-6
+    g.destroy()
+    # one node, no edges
+    g1 = agp.build_graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    out, _ = agp.query_sources(g1, agp.katz(0.5, 5, 0.0), [0])
+    assert abs(float(out[0, 0]) - 1.0) < 1e-6  # w_0 / Y_0 * Y_0 = w_0 = 1 (Katz w_i = beta^i)
+    g1.destroy()
+    # feature columns that are zero (no lanes) or of one sign only
+    g2 = agp.build_graph(n, u, v, add_self_loops=True)
+    X = torch.zeros(n, 3, dtype=torch.bfloat16, device="cuda")
+    X[:, 1] = 1.0
+    Z = agp.feature_propagate(g2, agp._params(0.5, 0.5, 3, agp.W_TRANSITION, eps=0.0), X).cpu().numpy()
+    assert not Z[:, 0].any() and not Z[:, 2].any() and Z[:, 1].min() > 0
+    Z0 = agp.feature_propagate(g2, agp._params(0.5, 0.5, 3, agp.W_TRANSITION, eps=0.0), X[:, :0])
+    assert Z0.shape == (n, 0)
+    g2.destroy()
+
+
 # ---------------------------------------------------------------- error paths
 def test_errors(agp, rmat14):
     n, u, v = rmat14
