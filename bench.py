@@ -454,24 +454,30 @@ def run_large(args):
 def serve_trace(n, u, v, rate, duration, seed, beta):
     """Seeded Poisson trace of the serving mix: PPR / Katz / HKPR / transition (22.5% each) and
     BF16 feature blocks of 1-64 columns (10%, log-uniform); eps in {1e-6, 1e-7, 1e-8, 1e-9};
-    L uniform in 5..40; sources uniform (50%) or degree-weighted (50%)."""
+    L uniform in 5..40; sources uniform over nodes with edges (50%) or degree-weighted (50%)."""
     rng = np.random.default_rng(seed)
     deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
     live = np.flatnonzero(deg > 0)
-    p_deg = deg / deg.sum()
-    t, trace = 0.0, []
-    while True:
-        t += rng.exponential(1.0 / rate)
-        if t >= duration:
-            break
-        r = rng.random()
-        kind = "features" if r < 0.10 else ("ppr", "katz", "hkpr", "transition")[min(3, int((r - 0.10) / 0.225))]
-        eps = float(rng.choice([1e-6, 1e-7, 1e-8, 1e-9]))
-        L = int(rng.integers(5, 41))
-        src = int(rng.choice(live)) if rng.random() < 0.5 else int(rng.choice(n, p=p_deg))
-        cols = int(np.clip(np.round(np.exp(rng.uniform(0, np.log(64)))), 1, 64))
-        trace.append((t, kind, eps, L, src, cols, int(rng.integers(0, 2**62))))
-    return trace
+    cdf = np.cumsum(deg, dtype=np.float64)
+    cdf /= cdf[-1]
+    gaps = rng.exponential(1.0 / rate, size=int(rate * duration * 1.2) + 64)
+    t = np.cumsum(gaps)
+    while t[-1] < duration:  # extend in the rare case the draw fell short
+        t = np.concatenate([t, t[-1] + np.cumsum(rng.exponential(1.0 / rate, size=1024))])
+    t = t[t < duration]
+    k = len(t)
+    r = rng.random(k)
+    kinds = np.where(r < 0.10, 4, np.minimum(3, ((r - 0.10) / 0.225).astype(np.int64)))
+    names = ("ppr", "katz", "hkpr", "transition", "features")
+    eps = rng.choice([1e-6, 1e-7, 1e-8, 1e-9], size=k)
+    L = rng.integers(5, 41, size=k)
+    uniform_src = live[rng.integers(0, len(live), size=k)]
+    weighted_src = np.minimum(np.searchsorted(cdf, rng.random(k), side="right"), n - 1)
+    src = np.where(rng.random(k) < 0.5, uniform_src, weighted_src)
+    cols = np.clip(np.round(np.exp(rng.uniform(0, np.log(64), size=k))), 1, 64).astype(np.int64)
+    seeds = rng.integers(0, 2**62, size=k)
+    return [(float(t[i]), names[kinds[i]], float(eps[i]), int(L[i]), int(src[i]), int(cols[i]), int(seeds[i]))
+            for i in range(k)]
 
 
 def run_serve(args, wl):
@@ -481,7 +487,8 @@ def run_serve(args, wl):
     n = wl["n"]
     g = agp.build_graph(n, u, v)
     beta, lam = agp.katz_beta(g, 0.85, iters=1000, tol=1e-12)
-    trace = serve_trace(n, u, v, args.rate, args.duration, S + 500, beta)
+    # the trace spans the warm-up and the measured window; only requests arriving in the window count
+    trace = serve_trace(n, u, v, args.rate, args.serve_warmup + args.duration, S + 500, beta)
     X = torch.randn(n, 64, generator=torch.Generator().manual_seed(S + 200)).to(torch.bfloat16).cuda()
 
     def params_of(kind, eps, L, seed):
@@ -498,7 +505,7 @@ def run_serve(args, wl):
     def replay(mode, admission=agp.ADMIT_COST):
         srv = agp.Server(g, mode=mode, max_lanes=args.lanes if args.lanes > 0 else 0, admission=admission)
         tickets = []
-        log(f"[serve] mode {mode}: replaying {len(trace)} requests over {args.duration}s")
+        log(f"[serve] mode {mode}: replaying {len(trace)} requests over {args.serve_warmup + args.duration}s")
         t0 = time.perf_counter()
         for (ta, kind, eps, L, src, cols, seed) in trace:
             dt = ta - (time.perf_counter() - t0)
@@ -508,18 +515,18 @@ def run_serve(args, wl):
             tk = srv.submit(p, X=X[:, :cols]) if kind == "features" else srv.submit(p, source=src)
             tickets.append((tk, kind))
         submitted_by = time.perf_counter() - t0
-        deadline = t0 + args.duration + args.drain
+        deadline = t0 + args.serve_warmup + args.duration + args.drain
         lat, done = [], 0
-        for tk, kind in tickets:
+        for (tk, kind), tr in zip(tickets, trace):
             left = max(0.0, deadline - time.perf_counter())
             r = srv.wait(tk, timeout_us=int(left * 1e6))
             if r is None:
                 continue
-            if r.status == 0:
+            if r.status == 0 and tr[0] >= args.serve_warmup:
                 done += 1
                 lat.append(r.latency_us / 1e3)
             srv.release(tk)
-        elapsed = min(time.perf_counter(), deadline) - t0
+        elapsed = min(time.perf_counter(), deadline) - t0 - args.serve_warmup
         st = srv.stats()
         log(f"[serve] mode {mode}: {done} done in {elapsed:.1f}s, stats {st}; stopping the server")
         for tk, _ in tickets:  # requests still queued are dropped, the running ones end their sweep
@@ -530,7 +537,8 @@ def run_serve(args, wl):
         srv.destroy()
         log(f"[serve] mode {mode}: stopped after {time.perf_counter() - t0:.1f}s")
         lat = np.array(lat) if lat else np.array([np.nan])
-        return {"offered": len(trace), "completed": done, "incomplete": len(trace) - done, "queries_per_s": done / elapsed,
+        offered = sum(1 for tr in trace if tr[0] >= args.serve_warmup)
+        return {"offered": offered, "completed": done, "incomplete": offered - done, "queries_per_s": done / elapsed,
                 "p50_ms": float(np.nanpercentile(lat, 50)), "p99_ms": float(np.nanpercentile(lat, 99)),
                 "elapsed_s": elapsed, "submit_s": submitted_by, "sweeps": st["sweeps"]}
 
@@ -540,7 +548,7 @@ def run_serve(args, wl):
     line = {"metric": "served queries/s (continuous batching)", "value": batched["queries_per_s"], "unit": "queries/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"] + " | serving trace", "rate": args.rate, "duration_s": args.duration,
-                       "drain_s": args.drain, "lambda_1": lam},
+                       "warmup_s": args.serve_warmup, "drain_s": args.drain, "lambda_1": lam},
             "batched": batched, "batched_fifo_admission": batched_fifo, "fifo_plain": fifo,
             "note": "latency percentiles over the requests completed inside the window; 'incomplete' were still "
                     "queued or running when it closed"}
@@ -566,6 +574,8 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--drain", type=float, default=20.0)
     ap.add_argument("--no-fifo", action="store_true")
+    ap.add_argument("--serve-warmup", type=float, default=0.0,
+                    help="seconds of trace before the measured window (its requests are served, not counted)")
     ap.add_argument("--features", action="store_true", help="GNN feature propagation workload")
     ap.add_argument("--large", action="store_true", help="65M-node, 1.8B-edge PPR / HKPR workload")
     ap.add_argument("--eps", type=float, default=0.0)

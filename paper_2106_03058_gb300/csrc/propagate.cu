@@ -561,10 +561,15 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
 #pragma unroll
     for (int t = 0; t < 3; ++t) base[t] = A.rpart[(size_t)t * gridDim.x + blockIdx.x];
     int parity = 0;
+    // the counts of the next tile are loaded while the current one is scanned and written
+    uint2 nr_next = (begin + threadIdx.x < end) ? A.nrec[begin + threadIdx.x] : make_uint2(0u, 0u);
     for (unsigned long long tile = begin; tile < end; tile += kBlock, parity ^= 1) {
         const unsigned long long idx = tile + threadIdx.x;
+        const uint2 nr = nr_next;
+        const unsigned long long nidx = idx + kBlock;
+        nr_next = (nidx < end) ? A.nrec[nidx] : make_uint2(0u, 0u);
         unsigned int cnt[3] = {0u, 0u, 0u};
-        if (idx < end) rec_split(A.nrec[idx], cnt[0], cnt[1], cnt[2]);
+        rec_split(nr, cnt[0], cnt[1], cnt[2]);
         unsigned int x[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
