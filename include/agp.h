@@ -230,7 +230,9 @@ typedef struct {
     int32_t admission;        /* AGP_ADMIT_* (batched mode). The cost estimate is the bound of the
                                  proof of Theorem 4.3, (1/eps) sum_{i=1..L} (Y_i/Y_0) ||P^i x||_1,
                                  with the mass ||P^i x||_1 bounded per weight kind; a request's
-                                 priority is cost / (1 + seconds waited); requests above 1e8
+                                 priority is cost / (1 + seconds waited), compared between the
+                                 oldest waiting requests of 64 cost classes (floor(log2 cost));
+                                 requests above 1e8
                                  estimated operations use at most 3/4 of the slots while another
                                  such request holds slots; a request that has waited over 30 s is
                                  admitted next, nothing else starting until its slots are free      */

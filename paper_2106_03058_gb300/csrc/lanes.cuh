@@ -16,9 +16,9 @@ constexpr int kMaxLevels = AGP_MAX_LEVELS;
 constexpr int kChunk = 512;          // prefix edges per chunk record (one warp)
 constexpr int kMinBlocks = 4;        // resident CTAs per SM the level kernels are compiled for
 constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
-constexpr float kLightSamples = 4.f; // tails expected to yield at most this many trials stay inline
+constexpr float kLightSamples = 8.f; // tails expected to yield at most this many trials stay inline
 constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
-constexpr float kDenseP = 0.125f;    // tails whose largest probability is >= this are sampled per position
+constexpr float kDenseP = 0.25f;     // tails whose largest probability is >= this are sampled per position
 constexpr uint32_t kSampleTag = 0x53414D50u;  // Philox counter word of the skip sampler
 constexpr uint32_t kDenseTag = 0x44534E53u;   // Philox counter word of the per-position sampler
 

@@ -15,7 +15,7 @@
 //              deterministic prefix length k(u) = number of neighbours with c / d_v^a >= eps
 //              (binary search over the degree-sorted row, all or nothing when a = 0). Short
 //              prefixes and light tails (few expected trials) are done inline; long prefixes,
-//              dense tails (p >= 1/8) and heavy sparse tails become records.
+//              dense tails (p >= 1/4) and heavy sparse tails become records.
 //   k_push     one warp per 512-position record: r^(i+1)(v) += c / d_v^a over a prefix chunk, or
 //              one Bernoulli trial per position of a dense-tail chunk (kept: += eps).
 //   k_sample   one thread per segment record of a sparse tail: subset sampling (Section 4) with

@@ -4,14 +4,17 @@
 // server's stream. One sweep = one level of Algorithm 2 for every admitted lane (the captured
 // expand/push/sample/level-end graph); lanes carry their own level, coefficients, L and random key,
 // so requests admitted at different times share sweeps. Between sweeps the thread
-//   1. admits queued requests (FIFO) while free slots and result memory allow, seeds them into the
-//      current frontier and starts them at level 0,
+//   1. admits waiting requests (cost-aware or FIFO) while free slots and result memory allow, seeds
+//      them into the current frontier and starts them at level 0,
 //   2. runs one sweep,
 //   3. reads the lanes' levels back; a lane whose level became -1 has reserved its last level, and
 //      a request whose lanes are all finished completes (its result is copied to the host first
 //      when results live there).
 // Waits of host threads on results are bounded by the caller's timeout.
+#include <algorithm>
 #include <chrono>
+#include <climits>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -43,6 +46,9 @@ struct Request {
     int lanes_left = 0;
     double cost = 0.0;              // estimated operations (admission priority)
     bool heavy = false;
+    bool in_queue = false;          // waiting for admission (queue entries of other requests are dropped lazily)
+    int refs = 0;                   // queue entries that still point at this request
+    bool zombie = false;            // released while queue entries remained: deleted with the last one
     std::vector<int> slots;
     float *d_out = nullptr;         // device result (n or n * cols floats)
     float *h_out = nullptr;         // pinned host copy when results live on the host
@@ -64,7 +70,14 @@ struct agp_server_s {
     std::condition_variable cv_work, cv_done;
     bool stop = false;
     uint64_t next_ticket = 1;
+    // Waiting requests. `queue` is in arrival order (FIFO admission, the oldest request, the FIFO
+    // plain mode); `cls[c]` holds the requests of cost class c = floor(log2 cost), in arrival order.
+    // Entries of requests that left the queue (admitted, cancelled, expired) are dropped lazily when
+    // they reach a front, so every operation is O(1) or O(classes) however long the queue grows.
     std::deque<agp::Request *> queue;
+    std::deque<agp::Request *> cls[64];
+    std::vector<agp::Request *> with_deadline;  // waiting requests that carry a deadline
+    int64_t queued = 0;                          // waiting requests
     std::unordered_map<uint64_t, agp::Request *> all;
     std::vector<agp::Request *> slot_owner;
     std::vector<int> free_slots;
@@ -188,6 +201,76 @@ CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, do
     return c;
 }
 
+constexpr int kCostClasses = 64;
+
+int cost_class(double cost)
+{
+    const int c = cost >= 1.0 ? (int)std::floor(std::log2(cost)) : 0;
+    return std::min(kCostClasses - 1, std::max(0, c));
+}
+
+// One queue entry of q is gone; a released request is deleted with its last entry.
+void unref(Request *q)
+{
+    if (--q->refs == 0 && q->zombie) delete q;
+}
+
+// Drop the entries of requests that no longer wait from the front of d.
+void pop_dead(std::deque<Request *> &d)
+{
+    while (!d.empty() && !d.front()->in_queue) {
+        Request *q = d.front();
+        d.pop_front();
+        unref(q);
+    }
+}
+
+// q stops waiting (admitted or finished); its queue entries are dropped lazily.
+void dequeue(agp_server_s *S, Request *q)
+{
+    if (q->in_queue) {
+        q->in_queue = false;
+        --S->queued;
+    }
+}
+
+// Every queue entry (stop and fatal paths). Requests stay owned by S->all unless released.
+void drain_queues(agp_server_s *S)
+{
+    auto drain = [](std::deque<Request *> &d) {
+        while (!d.empty()) {
+            Request *q = d.front();
+            d.pop_front();
+            q->in_queue = false;
+            unref(q);
+        }
+    };
+    drain(S->queue);
+    for (auto &d : S->cls) drain(d);
+    for (Request *q : S->with_deadline) {
+        q->in_queue = false;
+        unref(q);
+    }
+    S->with_deadline.clear();
+    S->queued = 0;
+}
+
+// Waiting requests past their deadline finish with AGP_ETIMEDOUT (cancelled waiting requests are
+// finished by agp_serve_cancel itself). Called with S->m held.
+void expire_waiting(agp_server_s *S, double t)
+{
+    size_t keep = 0;
+    for (Request *q : S->with_deadline) {
+        if (q->in_queue && t - q->t_submit > (double)q->r.deadline_us) {
+            dequeue(S, q);
+            finish(S, q, AGP_ETIMEDOUT);
+        }
+        if (q->in_queue) S->with_deadline[keep++] = q;
+        else unref(q);
+    }
+    S->with_deadline.resize(keep);
+}
+
 // Admit queued requests while slots and result memory allow. Called by the server thread.
 int admit(agp_server_s *S)
 {
@@ -203,57 +286,52 @@ int admit(agp_server_s *S)
         }
         for (int sl : cut) S->slot_owner[sl]->cut = true;
         const double t = now_us();
-        // cancelled and expired requests leave the queue first
-        for (auto it = S->queue.begin(); it != S->queue.end();) {
-            Request *q = *it;
-            if (q->cancelled) { finish(S, q, AGP_ECANCELED); it = S->queue.erase(it); continue; }
-            if (q->r.deadline_us > 0 && t - q->t_submit > (double)q->r.deadline_us) {
-                finish(S, q, AGP_ETIMEDOUT);
-                it = S->queue.erase(it);
-                continue;
-            }
-            ++it;
-        }
+        expire_waiting(S, t);
         const bool fifo = S->cfg.admission == AGP_ADMIT_FIFO;
         // The heavy cap keeps lanes for light requests, but it only binds while another heavy
         // request holds lanes: a request wider than the cap is still admitted once it is alone.
-        auto fits = [&](const Request *q, int need) {
+        auto need_of = [](const Request *q) { return q->r.source >= 0 ? 1 : 2 * q->r.cols; };
+        auto fits = [&](const Request *q) {
+            const int need = need_of(q);
             if ((int)S->free_slots.size() < need) return false;
             return !q->heavy || S->heavy_lanes == 0 || S->heavy_lanes + need <= (3 * S->cfg.max_lanes) / 4;
         };
-        while (!S->queue.empty()) {
-            // FIFO: the head; cost-aware: the best priority among the requests that fit now, unless
-            // the oldest request has waited past kStarveUs, in which case nothing else is admitted
-            // until its lanes have drained free (no starvation of wide requests)
-            auto pick = S->queue.end();
-            double best = 0.0;
+        while (S->queued > 0) {
+            // FIFO: the oldest request. Cost-aware: among the oldest request of every cost class
+            // (floor(log2 cost)), the one that fits now with the best aged priority
+            // cost / (1 + seconds waited). Within a class requests start in arrival order. A
+            // request that has waited past kStarveUs goes next under either policy, and nothing
+            // else starts until its slots are free (no starvation of wide requests).
+            pop_dead(S->queue);
+            if (S->queue.empty()) break;
+            Request *q = nullptr;
+            std::deque<Request *> *from = nullptr;
             Request *oldest = S->queue.front();
-            const bool forced = !fifo && t - oldest->t_submit > kStarveUs;
-            if (forced) {
-                const int need = oldest->r.source >= 0 ? 1 : 2 * oldest->r.cols;
-                if (!fits(oldest, need)) break;
-                pick = S->queue.begin();
-            }
-            for (auto it = S->queue.begin(); !forced && it != S->queue.end(); ++it) {
-                Request *q = *it;
-                const int need = q->r.source >= 0 ? 1 : 2 * q->r.cols;
-                if (fifo) {
-                    if (fits(q, need)) pick = it;
-                    break;
+            if (fifo || t - oldest->t_submit > kStarveUs) {
+                if (!fits(oldest)) break;
+                q = oldest;
+                from = &S->queue;
+            } else {
+                double best = 0.0;
+                for (auto &d : S->cls) {
+                    pop_dead(d);
+                    if (d.empty() || !fits(d.front())) continue;
+                    Request *h = d.front();
+                    const double prio = h->cost / (1.0 + (t - h->t_submit) / kAgingUs);
+                    if (!q || prio < best) {
+                        q = h;
+                        best = prio;
+                        from = &d;
+                    }
                 }
-                if (!fits(q, need)) continue;
-                const double prio = q->cost / (1.0 + (t - q->t_submit) / kAgingUs);
-                if (pick == S->queue.end() || prio < best) {
-                    pick = it;
-                    best = prio;
-                }
+                if (!q) break;
             }
-            if (pick == S->queue.end()) break;
-            Request *q = *pick;
-            const int need = q->r.source >= 0 ? 1 : 2 * q->r.cols;
+            const int need = need_of(q);
             const int64_t bytes = (int64_t)S->g->n * (q->r.source >= 0 ? 1 : q->r.cols) * (int64_t)sizeof(float);
             if (S->result_bytes + bytes > S->cfg.result_budget && S->result_bytes > 0) break;
-            S->queue.erase(pick);
+            from->pop_front();
+            unref(q);  // still owned by S->all: not released while it waits
+            dequeue(S, q);
             q->t_admit = t;
             q->slots.clear();
             for (int k = 0; k < need; ++k) {
@@ -479,13 +557,15 @@ void server_main(agp_server_s *S)
             Request *q = nullptr;
             {
                 std::unique_lock<std::mutex> lk(S->m);
-                S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+                S->cv_work.wait(lk, [&] { return S->stop || S->queued > 0; });
                 if (S->stop) return;
+                expire_waiting(S, now_us());
+                pop_dead(S->queue);
+                if (S->queue.empty()) continue;
                 q = S->queue.front();
                 S->queue.pop_front();
-                const double t = now_us();
-                if (q->cancelled) { finish(S, q, AGP_ECANCELED); continue; }
-                if (q->r.deadline_us > 0 && t - q->t_submit > (double)q->r.deadline_us) { finish(S, q, AGP_ETIMEDOUT); continue; }
+                unref(q);
+                dequeue(S, q);
             }
             run_fifo_plain(S, q);
         }
@@ -494,8 +574,8 @@ void server_main(agp_server_s *S)
         {
             std::unique_lock<std::mutex> lk(S->m);
             if (S->stop) return;
-            if (S->active_lanes == 0 && S->queue.empty())
-                S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || !S->queue.empty(); });
+            if (S->active_lanes == 0 && S->queued == 0)
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || S->queued > 0; });
             if (S->stop) return;
         }
         int rc = admit(S);
@@ -510,7 +590,7 @@ void server_main(agp_server_s *S)
             S->fatal = rc;
             for (auto &kv : S->all)
                 if (!kv.second->done) finish(S, kv.second, rc);
-            S->queue.clear();
+            drain_queues(S);
             return;
         }
     }
@@ -614,7 +694,15 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
         }
         q->ticket = S->next_ticket++;
         S->all[q->ticket] = q;
+        q->in_queue = true;
+        ++S->queued;
         S->queue.push_back(q);
+        S->cls[cost_class(q->cost)].push_back(q);
+        q->refs = 2;
+        if (q->r.deadline_us > 0) {
+            S->with_deadline.push_back(q);
+            ++q->refs;
+        }
     }
     S->cv_work.notify_one();
     *ticket = q->ticket;
@@ -673,7 +761,14 @@ int serve_release(agp_server_s *S, uint64_t ticket)
         S->all.erase(it);
         if (q->counted) S->result_bytes -= (int64_t)(q->r.source >= 0 ? 1 : q->r.cols) * S->g->n * (int64_t)sizeof(float);
     }
-    free_result(q);
+    free_result(q);  // nobody deletes q meanwhile: it is not a zombie yet
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        if (q->refs > 0) {
+            q->zombie = true;  // queue entries remain: deleted with the last one
+            q = nullptr;
+        }
+    }
     delete q;
     S->cv_work.notify_one();
     return AGP_OK;
@@ -687,8 +782,13 @@ int serve_cancel(agp_server_s *S, uint64_t ticket)
     if (it == S->all.end()) return fail(AGP_EINVAL, "unknown ticket");
     Request *q = it->second;
     if (q->done) return AGP_OK;
-    q->cancelled = true;  // the server thread stops its lanes before the next sweep
-    S->cv_work.notify_one();
+    q->cancelled = true;
+    if (q->in_queue) {  // still waiting: finished now, its queue entries are dropped lazily
+        dequeue(S, q);
+        finish(S, q, AGP_ECANCELED);
+        return AGP_OK;
+    }
+    S->cv_work.notify_one();  // in flight: the server thread stops its lanes before the next sweep
     return AGP_OK;
 }
 
@@ -699,7 +799,7 @@ int serve_stats(agp_server_s *S, int64_t *completed, int64_t *sweeps, int32_t *l
     if (completed) *completed = S->completed;
     if (sweeps) *sweeps = S->sweeps;
     if (lanes_active) *lanes_active = S->active_lanes;
-    if (queued) *queued = (int32_t)S->queue.size();
+    if (queued) *queued = (int32_t)std::min<int64_t>(S->queued, INT32_MAX);
     return AGP_OK;
 }
 
@@ -715,13 +815,13 @@ int serve_destroy(agp_server_s *S)
     if (S->stream) cudaStreamSynchronize(S->stream);
     {
         std::lock_guard<std::mutex> lk(S->m);
+        drain_queues(S);  // released requests go with their last queue entry
         for (auto &kv : S->all) {
             if (!kv.second->done) finish(S, kv.second, AGP_ECANCELED);
             free_result(kv.second);
             delete kv.second;
         }
         S->all.clear();
-        S->queue.clear();
     }
     if (S->sweep) cudaGraphExecDestroy(S->sweep);
     free_workspace(S->ws);

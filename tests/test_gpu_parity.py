@@ -350,21 +350,33 @@ def test_feature_propagation_eps0(agp, rmat14):
 
 
 def test_feature_propagation_unbiased(agp, rmat14):
+    """Feature columns are unbiased (Lemma 4.1). 128 copies of one BF16 column draw from independent
+    streams. Per node, the mean of the 128 estimates is z-tested against the exact propagation.
+    The nodes share those 128 columns, so their z-values are correlated, and nodes with few sampled
+    increments are skewed. The fraction beyond 2.576 therefore varies more than a binomial would:
+    the FP64 oracle itself gave 0.7-2.1% over batches of 128 seeds on this graph. The bar is 3%,
+    plus a z-test of the sums over 64 random node groups (near-normal by aggregation), each
+    within 5 (the oracle's largest over its batches was 2.8)."""
     n, u, v = rmat14
     g = agp.build_graph(n, u, v, add_self_loops=True)
     og = oracle.build_csr(n, u, v, add_self_loops=True)
+    K = 128
     X = torch.randn(n, 1, generator=torch.Generator().manual_seed(1)).to(torch.bfloat16)
-    Xr = X.repeat(1, 64).contiguous()  # 64 copies of one column: independent streams per column
+    Xr = X.repeat(1, K).contiguous()  # K copies of one column: independent streams per column
     p = agp._params(0.5, 0.5, 4, agp.W_TRANSITION, eps=1e-6, seed=9)
     Z = agp.feature_propagate(g, p, Xr.cuda()).cpu().numpy().astype(np.float64)
     w, Y = oracle.tail_sums(oracle.TRANSITION, 4)
     xf = X.float().numpy()[:, 0].astype(np.float64)
     exact = oracle.basic(og, 0.5, 0.5, 4, w, Y, xf)
     assert not np.allclose(Z[:, 0], Z[:, 1])  # columns use different random streams
-    mean, sd = Z.mean(1), Z.std(1, ddof=1) / np.sqrt(64)
+    mean, sd = Z.mean(1), Z.std(1, ddof=1) / np.sqrt(K)
     live = sd > 0
     z = (mean[live] - exact[live]) / sd[live]
-    assert np.mean(np.abs(z) > 2.576) <= 0.02
+    assert np.mean(np.abs(z) > 2.576) <= 0.03
+    grp = np.random.default_rng(0).integers(0, 64, n)
+    G = np.stack([np.bincount(grp, weights=Z[:, k], minlength=64) for k in range(K)], 1)
+    gz = (G.mean(1) - np.bincount(grp, weights=exact, minlength=64)) / (G.std(1, ddof=1) / np.sqrt(K))
+    assert np.abs(gz).max() <= 5.0
 
 
 # ---------------------------------------------------------------- eps in raw signal units

@@ -114,8 +114,10 @@ def test_feature_request_in_mix(agp, graph, eps):
     eps = 0: identical up to FP32 summation order (1e-5 of the column's largest entry). eps > 0:
     the random streams are the same, but a different FP32 atomic order can move a residue across
     a sampling threshold by one ulp and flip that decision; the change then propagates through the
-    decisions downstream. Every column must either agree with the block run alone (same_draws) or be
-    as accurate as it against the exact propagation, and half of its entries must still agree."""
+    decisions downstream (with geometric skips, a changed probability moves every later trial of that
+    node), so the two blocks can drift apart within the estimator's own error. Every column must
+    either agree with the block run alone (same_draws) or be as accurate as it against the exact
+    propagation."""
     n, g, og, u, v = graph
     X = torch.randn(n, 6, generator=torch.Generator().manual_seed(4)).to(torch.bfloat16).cuda()
     pf = agp._params(0.5, 0.5, 6, agp.W_PPR, 0.1, eps=eps, seed=77)
@@ -141,7 +143,6 @@ def test_feature_request_in_mix(agp, graph, eps):
     for c in range(6):
         if not same_draws(Zs[:, c], Za[:, c]):
             assert equally_accurate(Zs[:, c], Za[:, c], Z0[:, c])
-        assert np.mean(np.abs(Zs[:, c] - Za[:, c]) <= 1e-5 * np.abs(Za[:, c]).max()) >= 0.5  # coupled
 
 
 def test_cancel_deadline_and_release(agp, graph):
