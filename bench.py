@@ -48,8 +48,10 @@ B_ITEM, B_DET, B_TRIAL, B_ACC, B_DEG, B_COMPACT_ITEM, B_SCAN = 28, 12, 4, 8, 4, 
 # DRAM traffic of k_push per L2 reduction, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over lts__t_sectors_srcunit_tex_op_red.sum, all 52 k_push launches of a step
 # of 8 Katz + 8 transition sources at four lanes per wave, warm L2). It scales a launch of the bench
-# step by its reductions; it holds for this kernel version and a four-lane wave only.
-PUSH_DRAM_BYTES_PER_RED, PUSH_TRAFFIC_LANES = 11.005, 4
+# step by its reductions, for a four-lane wave only. None while it is not measured for the current
+# split of tails between the samplers: it was 11.0 B with dense per-position sampling from p >= 1/8,
+# and per-position sampling now starts at p >= 1/4, which changes the kernel's mix of work.
+PUSH_DRAM_BYTES_PER_RED, PUSH_TRAFFIC_LANES = None, 4
 
 
 def log(*a):
@@ -715,7 +717,7 @@ def main():
         peak, peak_src = HBM_FALLBACK_GBS, "fallback"
     edge_ops = work[:, 0].sum() + work[:, 2].sum()
     traffic = None
-    if dom == "push" and lanes == PUSH_TRAFFIC_LANES:
+    if dom == "push" and lanes == PUSH_TRAFFIC_LANES and PUSH_DRAM_BYTES_PER_RED is not None:
         traffic = PUSH_DRAM_BYTES_PER_RED * (work[1, 0] + work[1, 2]) / launches
     # k_push is bound by random FP32 atomic adds into residue vectors that stay in L2, not by HBM:
     # its adds per second against a library scatter-add of the same shape on this GPU
