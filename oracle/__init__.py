@@ -59,6 +59,8 @@ def lib():
         L.ora_philox4x32_10.restype = None
         L.ora_build_csr.argtypes = [C.c_int64, C.c_int64, _i32p, _i32p, C.c_int, _i64p, _i32p, _i32p]
         L.ora_build_csr.restype = C.c_int64
+        L.ora_build_csr_directed.argtypes = [C.c_int64, C.c_int64, _i32p, _i32p, C.c_int, _i64p, _i32p, _i32p]
+        L.ora_build_csr_directed.restype = C.c_int64
         L.ora_tail_sums.argtypes = [C.c_int, C.c_int, C.c_double, _f64p, _f64p, _f64p]
         L.ora_tail_sums.restype = C.c_int
         L.ora_basic.argtypes = [C.c_int64, _i64p, _i32p, _i32p, C.c_double, C.c_double, C.c_int,
@@ -95,15 +97,17 @@ class CSR:
         return int(self.rowptr[-1])
 
 
-def build_csr(n, src, dst, add_self_loops=False) -> CSR:
-    """Section 4 pre-sorting: see ``ora_build_csr``."""
+def build_csr(n, src, dst, add_self_loops=False, directed=False) -> CSR:
+    """Section 4 pre-sorting: see ``ora_build_csr`` (``ora_build_csr_directed`` when directed:
+    rows are out-neighbours and degrees out-degrees, for the transposed adjacency)."""
     src = np.ascontiguousarray(src, np.int32)
     dst = np.ascontiguousarray(dst, np.int32)
     m = src.size
     rowptr = np.zeros(n + 1, np.int64)
     colidx = np.zeros(max(2 * m + (n if add_self_loops else 0), 1), np.int32)
     deg = np.zeros(max(n, 1), np.int32)
-    nnz = lib().ora_build_csr(n, m, src, dst, int(bool(add_self_loops)), rowptr, colidx, deg)
+    fn = lib().ora_build_csr_directed if directed else lib().ora_build_csr
+    nnz = fn(n, m, src, dst, int(bool(add_self_loops)), rowptr, colidx, deg)
     if nnz < 0:
         raise ValueError("ora_build_csr: bad argument")
     return CSR(n, rowptr, colidx[:nnz].copy(), deg[:n].copy())

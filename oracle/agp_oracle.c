@@ -13,6 +13,8 @@
  *   ora_philox4x32_10  Philox4x32-10 counter-based generator (Salmon et al., SC'11, Section 4).
  *   ora_build_csr      Section 4 "Pre-sorting adjacency list by degrees": undirected CSR whose
  *                      rows are sorted by neighbour degree (ties by neighbour id).
+ *   ora_build_csr_directed  the same for a directed graph (Section 4, "Propagation on directed
+ *                      graph", transposed adjacency): rows are out-neighbours, degrees out-degrees.
  *   ora_tail_sums      Def. 3.1: Y_i = sum_{k>=i} w_k, for the weight sequences of Table 1.
  *   ora_basic          Algorithm 1 (Basic Propagation), exact truncated sum.
  *   ora_randomized     Algorithm 2 (Randomized Propagation), subset sampling done neighbour by
@@ -95,20 +97,24 @@ static int cmp_by_degree_then_id(const void *pa, const void *pb)
 }
 
 /* Returns nnz, or -1 on a bad argument. rowptr has n+1 entries; colidx must hold
- * 2*m (+ n with add_self_loops) entries; deg has n entries. */
-int64_t ora_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
-                      int add_self_loops, int64_t *rowptr, int32_t *colidx, int32_t *deg)
+ * 2*m (+ n with add_self_loops) entries (m (+ n) when directed); deg has n entries.
+ * directed = 0: undirected graph as above. directed = 1: "Propagation on directed graph"
+ * (end of Section 4) with the transposed adjacency of PageRank, PPR, HKPR and Katz: r^(i+1)(v)
+ * sums over the in-neighbours u of v, so the push list of u is its out-neighbours, each edge
+ * (u, v) gives v in N_u only, and d_u is the out-degree. Rows are sorted by (d_out(v), v). */
+static int64_t build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, int add_self_loops,
+                         int directed, int64_t *rowptr, int32_t *colidx, int32_t *deg)
 {
     if (n < 0 || m < 0) return -1;
     for (int64_t e = 0; e < m; ++e)
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return -1;
 
-    /* 1. count both directions of every non-loop edge */
+    /* 1. count the kept directions of every non-loop edge */
     int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t e = 0; e < m; ++e) {
         if (src[e] == dst[e]) continue;
         cnt[src[e]]++;
-        cnt[dst[e]]++;
+        if (!directed) cnt[dst[e]]++;
     }
     int64_t *start = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     start[0] = 0;
@@ -119,7 +125,7 @@ int64_t ora_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *d
     for (int64_t e = 0; e < m; ++e) {
         if (src[e] == dst[e]) continue;
         tmp[fill[src[e]]++] = dst[e];
-        tmp[fill[dst[e]]++] = src[e];
+        if (!directed) tmp[fill[dst[e]]++] = src[e];
     }
     if (add_self_loops)
         for (int64_t u = 0; u < n; ++u) tmp[fill[u]++] = (int32_t)u;
@@ -147,6 +153,18 @@ int64_t ora_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *d
     int64_t nnz = rowptr[n];
     free(cnt); free(start); free(tmp); free(fill);
     return nnz;
+}
+
+int64_t ora_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                      int add_self_loops, int64_t *rowptr, int32_t *colidx, int32_t *deg)
+{
+    return build_csr(n, m, src, dst, add_self_loops, 0, rowptr, colidx, deg);
+}
+
+int64_t ora_build_csr_directed(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                               int add_self_loops, int64_t *rowptr, int32_t *colidx, int32_t *deg)
+{
+    return build_csr(n, m, src, dst, add_self_loops, 1, rowptr, colidx, deg);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -207,11 +225,14 @@ int ora_tail_sums(int kind, int L, double param, const double *w_in, double *w, 
     }
 }
 
-/* d^{-p} with the reading D^{-1} := 0 on isolated nodes (d = 0). */
+/* d^{-p} with the reading D^{-p} := 0 at degree 0 for p > 0; D^0 = I, so p = 0 gives 1 at any
+ * degree. (Undirected: a neighbour has degree >= 1, and a node of degree 0 pushes nothing, so
+ * only the directed case meets degree 0 here: a node without out-edges still receives pushes
+ * when a = 0.) */
 static double deg_pow_neg(int32_t d, double p)
 {
-    if (d == 0) return 0.0;
     if (p == 0.0) return 1.0;
+    if (d == 0) return 0.0;
     return pow((double)d, -p);
 }
 

@@ -150,9 +150,9 @@ struct Uniforms {
 
 // Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane.
 template <int kSampleBatch>
-__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int lane, int32_t u, int lvl, uint32_t seg,
+__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int32_t u, int lvl, uint32_t seg,
                              const int32_t *row, int j0, int j1, float c, unsigned long long &drawn,
-                             unsigned long long &accepted, int kern)
+                             unsigned long long &accepted)
 {
     Uniforms U((uint32_t)u, (uint32_t)lvl, seg, P.key0, P.key1);
     const float ce = c * P.inv_eps;  // c / eps
@@ -447,7 +447,7 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
         const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
         const float expect = p0 * (float)tail;  // upper bound on the trials reached
         if (expect <= kLightSamples) {
-            sample_range<2>(A, P, Rn, lane, u, lvl, 0u, row, k, d, c, drawn, accepted, 0);
+            sample_range<2>(A, P, Rn, u, lvl, 0u, row, k, d, c, drawn, accepted);
         } else if (p0 >= kDenseP) {
             // most positions are kept: one Bernoulli per position, by warps, coalesced colidx reads
             nrec.y = kDenseBit | (unsigned int)((tail + kChunk - 1) / kChunk);
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         const int j0 = ks.x + (int)R.y * ks.y, j1 = min(d, j0 + ks.y);
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         unsigned long long drawn = 0, accepted = 0;
-        sample_range<4>(A, P, Rn, lane, u, lvl, R.y, row, j0, j1, c, drawn, accepted, 2);
+        sample_range<4>(A, P, Rn, u, lvl, R.y, row, j0, j1, c, drawn, accepted);
         if (A.collect && (drawn | accepted)) {
             atomicAdd(&A.stats[lane].by_kernel[2][1], drawn);
             atomicAdd(&A.stats[lane].by_kernel[2][2], accepted);

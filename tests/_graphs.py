@@ -81,3 +81,31 @@ def dense_propagation(A, a, b, w, x):
             v = M @ v
         out += wi * v
     return out
+
+
+def dense_directed_adjacency(n, src, dst, add_self_loops=False):
+    """A[u, v] = 1 for every directed edge u -> v (repeats merged, input loops dropped)."""
+    A = np.zeros((n, n))
+    for s, d in zip(src, dst):
+        if s != d:
+            A[s, d] = 1.0
+    if add_self_loops:
+        A += np.eye(n)
+    return A
+
+
+def dense_directed_propagation(A, a, b, w, x):
+    """sum_i w_i (D^-a A^T D^-b)^i x with D the out-degree matrix (directed graphs, transposed
+    adjacency), dense FP64 powers; D^0 = I, and D^-p := 0 at out-degree 0 for p > 0."""
+    d = A.sum(1)
+    with np.errstate(divide="ignore"):
+        da = np.ones_like(d) if a == 0 else np.where(d > 0, d ** (-a), 0.0)
+        db = np.ones_like(d) if b == 0 else np.where(d > 0, d ** (-b), 0.0)
+    M = da[:, None] * A.T * db[None, :]
+    out = np.zeros(A.shape[0])
+    v = np.asarray(x, np.float64).copy()
+    for i, wi in enumerate(w):
+        if i > 0:
+            v = M @ v
+        out += wi * v
+    return out

@@ -263,3 +263,112 @@ def test_signed_signal_is_linear():
     plus = oracle.basic(g, 0.5, 0.5, 8, w, Y, np.maximum(x, 0))
     minus = oracle.basic(g, 0.5, 0.5, 8, w, Y, np.maximum(-x, 0))
     np.testing.assert_allclose(whole, plus - minus, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- directed graphs
+# Section 4, "Propagation on directed graph": pi = sum_i w_i (D^-a A^T D^-b)^i x with D the
+# out-degree matrix, for PageRank, PPR, HKPR and Katz. A push goes from u to its out-neighbours.
+def _directed_by_sets(n, src, dst, loops):
+    out = [set() for _ in range(n)]
+    for s, d in zip(src.tolist(), dst.tolist()):
+        if s != d:
+            out[s].add(d)
+    if loops:
+        for u in range(n):
+            out[u].add(u)
+    deg = np.array([len(s) for s in out], np.int32)
+    rows = [sorted(s, key=lambda v: (deg[v], v)) for s in out]
+    return deg, rows
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("loops", [False, True])
+def test_directed_csr_matches_set_construction(seed, loops):
+    n, src, dst = G.random_multigraph(60, 150, seed)
+    g = oracle.build_csr(n, src, dst, add_self_loops=loops, directed=True)
+    deg, rows = _directed_by_sets(n, src, dst, loops)
+    np.testing.assert_array_equal(g.deg, deg)
+    assert g.rowptr[0] == 0 and np.all(np.diff(g.rowptr) == deg)
+    for u in range(n):
+        assert g.colidx[g.rowptr[u]:g.rowptr[u + 1]].tolist() == rows[u]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_directed_basic_matches_dense_matrix_powers(seed):
+    """Random directed multigraphs with sinks (out-degree 0): a = 0 (the presets) or a random a,
+    random b, weights and signed signal, against dense powers of D^-a A^T D^-b."""
+    rng = np.random.default_rng(300 + seed)
+    n, src, dst = G.random_multigraph(40, 70, seed)
+    loops = bool(seed % 2)
+    g = oracle.build_csr(n, src, dst, add_self_loops=loops, directed=True)
+    if not loops:
+        assert np.any(g.deg == 0)  # sinks present
+    A = G.dense_directed_adjacency(n, src, dst, loops)
+    a = 0.0 if seed < 3 else rng.random()
+    b = rng.random()
+    L = int(rng.integers(1, 9))
+    w = rng.random(L + 1)
+    x = rng.standard_normal(n)
+    x[rng.random(n) < 0.5] = 0.0
+    wl, Y = oracle.tail_sums(oracle.FINITE, L, w=w)
+    got = oracle.basic(g, a, b, L, wl, Y, x)
+    want = G.dense_directed_propagation(A, a, b, w, x)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+def _directed_cycle(n):
+    src = np.arange(n, dtype=np.int32)
+    return src, ((src + 1) % n).astype(np.int32)
+
+
+def test_directed_cycle_transition_is_a_shift():
+    """On the directed cycle 0 -> 1 -> ... -> n-1 -> 0 every node has out-degree 1, so
+    A^T D^-1 moves all mass one step forward: the L-step transition vector is e_{s+L mod n}."""
+    n, s = 7, 2
+    src, dst = _directed_cycle(n)
+    g = oracle.build_csr(n, src, dst, directed=True)
+    for L in (1, 5, 9):
+        w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+        x = np.zeros(n); x[s] = 1.0
+        pi = oracle.basic(g, 0, 1, L, w, Y, x)
+        want = np.zeros(n); want[(s + L) % n] = 1.0
+        np.testing.assert_allclose(pi, want, atol=1e-15)
+
+
+def test_directed_cycle_ppr_closed_form():
+    """PPR on the directed cycle: the walk sits at s+i mod n after i steps, so the truncated PPR
+    is pi(v) = sum over i <= L with s+i = v (mod n) of alpha (1-alpha)^i."""
+    n, s, alpha, L = 5, 1, 0.15, 23
+    src, dst = _directed_cycle(n)
+    g = oracle.build_csr(n, src, dst, directed=True)
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    x = np.zeros(n); x[s] = 1.0
+    pi = oracle.basic(g, 0, 1, L, w, Y, x)
+    want = np.zeros(n)
+    for i in range(L + 1):
+        want[(s + i) % n] += alpha * (1 - alpha) ** i
+    np.testing.assert_allclose(pi, want, rtol=1e-13)
+
+
+def test_directed_mass_invariant_and_sink_loss():
+    """a = 0, b = 1: A^T D^-1 is column stochastic on nodes with out-edges. On a strongly connected
+    graph (a cycle plus chords) sum pi = sum_{i<=L} w_i. A sink keeps what reaches it as reserve
+    and passes nothing on (D^-1 := 0), so the total falls short by exactly the dense prediction."""
+    n = 50
+    rng = np.random.default_rng(9)
+    cs, cd = _directed_cycle(n)
+    ch_s = rng.integers(0, n, 120).astype(np.int32)
+    ch_d = rng.integers(0, n, 120).astype(np.int32)
+    src, dst = np.concatenate([cs, ch_s]), np.concatenate([cd, ch_d])
+    g = oracle.build_csr(n, src, dst, directed=True)
+    w, Y = oracle.tail_sums(oracle.HKPR, 12, 3.0)
+    x = np.zeros(n); x[4] = 1.0
+    pi = oracle.basic(g, 0, 1, 12, w, Y, x)
+    assert abs(pi.sum() - w.sum()) < 1e-12
+    keep = src != 7  # node 7 loses its out-edges and becomes a sink
+    g2 = oracle.build_csr(n, src[keep], dst[keep], directed=True)
+    assert g2.deg[7] == 0
+    pi2 = oracle.basic(g2, 0, 1, 12, w, Y, x)
+    want = G.dense_directed_propagation(G.dense_directed_adjacency(n, src[keep], dst[keep]), 0, 1, w, x)
+    np.testing.assert_allclose(pi2, want, rtol=1e-12, atol=1e-16)
+    assert pi2.sum() < w.sum() - 1e-6
