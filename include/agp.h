@@ -66,6 +66,7 @@ typedef struct agp_graph_s *agp_graph_t;
 
 #define AGP_ADD_SELF_LOOPS 0x1u  /* add one self-loop per node, counted once in its degree        */
 #define AGP_EDGES_ON_DEVICE 0x2u /* src/dst are device pointers (else host pointers)               */
+#define AGP_DIRECTED 0x4u        /* directed graph: see below                                      */
 
 /*
  * Build the device CSR of an undirected graph: Section 4 "Pre-sorting adjacency list by degrees".
@@ -73,6 +74,13 @@ typedef struct agp_graph_s *agp_graph_t;
  * are merged and input self-loops dropped. With AGP_ADD_SELF_LOOPS every node then gets exactly
  * one self-loop (the self-looped graph of SGC/GCN, Section 1). Each adjacency list N_u is stored
  * in ascending (d_v, v) order, so the neighbours of small degree form a prefix.
+ * AGP_DIRECTED: Section 4, "Propagation on directed graph", with the transposed adjacency that the
+ * paper uses for PageRank, PPR, HKPR and Katz: pi = sum_i w_i (D^-a A^T D^-b)^i x, D the out-degree
+ * matrix. Each edge (src[e], dst[e]) is directed src -> dst; N_u is the out-neighbour list of u and
+ * d_u its out-degree (rowptr, colidx and deg of agp_graph_info are these), so the propagation
+ * pushes along out-edges. Queries on a directed graph need a = 0 (AGP_EINVAL otherwise): a node
+ * without out-edges would have d^-a undefined. A node without out-edges keeps what reaches it as
+ * reserve and passes nothing on (D^-1 := 0).
  *   n        number of nodes, 0 <= n < 2^31
  *   n_edges  number of input edges (>= 0)
  *   src,dst  n_edges int32 ids each, host or device memory (AGP_EDGES_ON_DEVICE); not retained

@@ -23,13 +23,13 @@ __all__ = [
     "feature_propagate", "katz_beta", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
-    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "MAX_LEVELS",
+    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "MAX_LEVELS",
 ]
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
-ADD_SELF_LOOPS, EDGES_ON_DEVICE = 0x1, 0x2
+ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED = 0x1, 0x2, 0x4
 MAX_LEVELS = 64
 
 
@@ -252,9 +252,10 @@ class _CudaArray:
         self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False), "version": 3}
 
 
-def build_graph(n, src, dst, add_self_loops=False, device=0, stream=None):
-    """``agp_build_graph``: src/dst are int32 numpy arrays (host) or CUDA tensors (device)."""
-    flags = ADD_SELF_LOOPS if add_self_loops else 0
+def build_graph(n, src, dst, add_self_loops=False, device=0, stream=None, directed=False):
+    """``agp_build_graph``: src/dst are int32 numpy arrays (host) or CUDA tensors (device).
+    directed: edges are src -> dst, rows are out-neighbour lists (AGP_DIRECTED; queries need a = 0)."""
+    flags = (ADD_SELF_LOOPS if add_self_loops else 0) | (DIRECTED if directed else 0)
     on_dev = not isinstance(src, np.ndarray)
     if on_dev:
         flags |= EDGES_ON_DEVICE

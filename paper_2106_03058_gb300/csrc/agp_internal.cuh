@@ -94,6 +94,7 @@ struct agp_graph_s {
     int device = 0;
     int64_t n = 0, nnz = 0;
     int32_t max_deg = 0;
+    bool directed = false;         // rows are out-neighbour lists and deg out-degrees (AGP_DIRECTED)
     int ubits = 1;                 // bits of a node id inside a packed (lane, node) item
     int64_t *rowptr = nullptr;
     int32_t *colidx = nullptr;

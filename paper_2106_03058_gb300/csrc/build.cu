@@ -6,7 +6,8 @@
 //   1. key (u, v): groups each row and exposes repeated edges as equal neighbours (merged);
 //   2. key (u, d_v) with value v: stable, so ties on degree keep ascending v.
 // Input self-loops are dropped; with AGP_ADD_SELF_LOOPS one loop per node is added before the
-// sorts and counts once in the degree.
+// sorts and counts once in the degree. With AGP_DIRECTED (Section 4, "Propagation on directed
+// graph") only u -> v is kept, so rows are out-neighbour lists and degrees out-degrees.
 #include <algorithm>
 #include <vector>
 
@@ -15,8 +16,10 @@
 namespace agp {
 namespace {
 
+// Two keys per input edge: (u, v) and, for an undirected graph, (v, u); a directed graph keeps
+// only u -> v (the reverse slot holds the sentinel and is dropped with the loops).
 __global__ void k_expand_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int ubits,
-                               uint64_t sentinel, uint64_t *keys, unsigned int *bad)
+                               uint64_t sentinel, int directed, uint64_t *keys, unsigned int *bad)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = src[e], v = dst[e];
@@ -24,7 +27,7 @@ __global__ void k_expand_edges(const int32_t *src, const int32_t *dst, int64_t m
         if (!ok) atomicOr(bad, 1u);
         const bool keep = ok && u != v;
         keys[2 * e] = keep ? (((uint64_t)u << ubits) | (uint64_t)v) : sentinel;
-        keys[2 * e + 1] = keep ? (((uint64_t)v << ubits) | (uint64_t)u) : sentinel;
+        keys[2 * e + 1] = (keep && !directed) ? (((uint64_t)v << ubits) | (uint64_t)u) : sentinel;
     }
 }
 
@@ -116,7 +119,9 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     if (n < 0 || n >= (1ll << 31)) return fail(AGP_EINVAL, "agp_build_graph: n must be in [0, 2^31)");
     if (m < 0) return fail(AGP_EINVAL, "agp_build_graph: n_edges < 0");
     if (m > 0 && (!src || !dst)) return fail(AGP_EINVAL, "agp_build_graph: src/dst NULL");
-    if (flags & ~(AGP_ADD_SELF_LOOPS | AGP_EDGES_ON_DEVICE)) return fail(AGP_EINVAL, "agp_build_graph: unknown flag");
+    if (flags & ~(AGP_ADD_SELF_LOOPS | AGP_EDGES_ON_DEVICE | AGP_DIRECTED))
+        return fail(AGP_EINVAL, "agp_build_graph: unknown flag");
+    const int directed = (flags & AGP_DIRECTED) ? 1 : 0;
     AGP_CUDA_TRY(cudaSetDevice(device));
 
     const bool loops = flags & AGP_ADD_SELF_LOOPS;
@@ -146,7 +151,7 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     AGP_TRY(maxd.alloc(sizeof(int32_t)));
     AGP_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(unsigned int), stream));
     AGP_CUDA_TRY(cudaMemsetAsync(maxd.p, 0, sizeof(int32_t), stream));
-    if (m > 0) k_expand_edges<<<grid, kBlock, 0, stream>>>(s, t, m, n, ubits, sentinel, keys_a.as<uint64_t>(), bad.as<unsigned int>());
+    if (m > 0) k_expand_edges<<<grid, kBlock, 0, stream>>>(s, t, m, n, ubits, sentinel, directed, keys_a.as<uint64_t>(), bad.as<unsigned int>());
     if (loops && n > 0) k_self_loops<<<grid, kBlock, 0, stream>>>(n, ubits, keys_a.as<uint64_t>() + 2 * m);
     AGP_CUDA_TRY(cudaGetLastError());
     unsigned int h_bad = 0;
@@ -206,6 +211,7 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     g->n = n;
     g->nnz = nnz;
     g->max_deg = max_deg;
+    g->directed = directed != 0;
     g->ubits = ubits;
     g->rowptr = (int64_t *)rowptr.release();
     g->deg = (int32_t *)degb.release();

@@ -177,6 +177,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
                           int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t s);
 int exponent_mode(double p);
 int validate_params(const agp_params_t &p);
+int validate_params_for(const agp_graph_s *g, const agp_params_t &p);
 void lane_key(uint64_t seed, uint64_t stream, int part, uint32_t &k0, uint32_t &k1);
 size_t bytes_per_lane(const agp_graph_s *g);
 int lane_capacity(const agp_graph_s *g);

@@ -894,6 +894,15 @@ int exponent_mode(double p)
     return 3;
 }
 
+// Parameters checked against the graph they run on: a directed graph (AGP_DIRECTED) needs a = 0,
+// because a node without out-edges would have d^-a undefined as a push target.
+int validate_params_for(const agp_graph_s *g, const agp_params_t &p)
+{
+    AGP_TRY(validate_params(p));
+    if (g->directed && p.a != 0.0) return fail(AGP_EINVAL, "params: a directed graph needs a = 0");
+    return AGP_OK;
+}
+
 int validate_params(const agp_params_t &p)
 {
     if (!(p.a >= 0.0 && p.a <= 1.0 && p.b >= 0.0 && p.b <= 1.0)) return fail(AGP_EINVAL, "params: a and b must be in [0, 1]");
@@ -1602,7 +1611,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
                   AGP_EPS_ABSOLUTE))
         return fail(AGP_EINVAL, "unknown flag");
     if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
-    for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params(params[i]));
+    for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     const bool plain = flags & AGP_PLAIN;
     const bool profile = flags & AGP_PROFILE;
@@ -1741,7 +1750,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     if (!g || !params) return fail(AGP_EINVAL, "NULL argument");
     if (d < 0 || ldx < d || ldz < d) return fail(AGP_EINVAL, "need d >= 0, ldx >= d, ldz >= d");
     if (flags & ~(AGP_PLAIN | AGP_PROFILE | AGP_EPS_ABSOLUTE)) return fail(AGP_EINVAL, "unknown flag");
-    AGP_TRY(validate_params(*params));
+    AGP_TRY(validate_params_for(g, *params));
     const bool profile = flags & AGP_PROFILE;
     if (d == 0 || g->n == 0) return AGP_OK;  // nothing to read or write: X and Z may be NULL
     if (!X || !Z) return fail(AGP_EINVAL, "NULL argument");
@@ -1794,6 +1803,7 @@ int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t
 {
     if (!g) return fail(AGP_EINVAL, "graph is NULL");
     if (!(a >= 0.0 && a <= 1.0) || !(eps >= 0.0)) return fail(AGP_EINVAL, "a in [0,1], eps >= 0");
+    if (g->directed && a != 0.0) return fail(AGP_EINVAL, "a directed graph needs a = 0");
     if (count < 0 || (count > 0 && (!nodes || !c || !k_out))) return fail(AGP_EINVAL, "bad arrays");
     if (count == 0) return AGP_OK;
     AGP_CUDA_TRY(cudaSetDevice(g->device));

@@ -657,7 +657,7 @@ int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **o
 int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
 {
     if (!S || !req || !ticket) return fail(AGP_EINVAL, "NULL argument");
-    AGP_TRY(validate_params(req->params));
+    AGP_TRY(validate_params_for(S->g, req->params));
     const int64_t n = S->g->n;
     if (req->source >= 0) {
         if (req->source >= n) return fail(AGP_EINVAL, "source outside [0, n)");

@@ -474,6 +474,44 @@ def test_degenerate_cases(agp, rmat14):
     g2.destroy()
 
 
+# ---------------------------------------------------------------- directed graphs
+def test_directed_graph(agp, rmat14):
+    """Section 4, "Propagation on directed graph" (transposed adjacency, out-degrees): the R-MAT
+    edges taken as directed. The CSR (out-neighbour rows in ascending (d_out, id)) is bit-exact
+    against the oracle; eps = 0 presets with a = 0 match it to 1e-5; eps > 0 keeps the expected
+    mass, sinks included; a != 0 is rejected."""
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v, directed=True)
+    og = oracle.build_csr(n, u, v, directed=True)
+    rp, ci, dg = (t.cpu().numpy() for t in g.csr())
+    np.testing.assert_array_equal(rp, og.rowptr)
+    np.testing.assert_array_equal(ci, og.colidx)
+    np.testing.assert_array_equal(dg, og.deg)
+    assert np.any(og.deg == 0)  # sinks
+    live = np.flatnonzero(og.deg > 0)
+    srcs = live[:: max(1, len(live) // 5)][:5]
+    for kind, L, param, a, b in ((oracle.PPR, 20, 0.2, 0.0, 1.0), (oracle.HKPR, 15, 3.0, 0.0, 1.0),
+                                 (oracle.TRANSITION, 4, 0.0, 0.0, 1.0), (oracle.KATZ, 10, 0.01, 0.0, 0.0)):
+        params = agp._params(a, b, L, kind, param, eps=0.0)
+        out, _ = agp.query_sources(g, params, srcs)
+        w, Y = oracle.tail_sums(kind, L, param)
+        for k, s_ in enumerate(srcs):
+            x = np.zeros(n); x[s_] = 1.0
+            _assert_rel(out[k].cpu().numpy(), oracle.basic(og, a, b, L, w, Y, x))
+    # eps > 0: the total mass is unbiased (200 seeds from one source)
+    s_ = int(srcs[0])
+    w, Y = oracle.tail_sums(oracle.PPR, 12, 0.2)
+    x = np.zeros(n); x[s_] = 1.0
+    want = oracle.basic(og, 0.0, 1.0, 12, w, Y, x).sum()
+    outs, _ = agp.query_sources(g, [agp.ppr(0.2, 12, 1e-5, seed=k) for k in range(200)], [s_] * 200)
+    mass = outs.sum(1, dtype=torch.float64).cpu().numpy()
+    assert abs(mass.mean() - want) <= 4.5 * mass.std(ddof=1) / np.sqrt(200) + 1e-6
+    with pytest.raises(agp.AgpError) as e:
+        agp.query_sources(g, agp._params(0.5, 0.5, 4, agp.W_PPR, 0.1, eps=0.0), srcs[:1])
+    assert e.value.code == 1
+    g.destroy()
+
+
 # ---------------------------------------------------------------- error paths
 def test_errors(agp, rmat14):
     n, u, v = rmat14
