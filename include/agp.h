@@ -209,6 +209,8 @@ AGP_API int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, con
  * of A by FP64 power iteration on the device (iterating A + I so that bipartite graphs converge),
  * stopping when the Rayleigh quotient changes by <= tol relatively or after `iters` steps.
  * beta = fraction / lambda_1. Synchronises `stream`. Outputs are host pointers (may be NULL).
+ * On a directed graph (AGP_DIRECTED) the iteration runs on the out-neighbour rows, i.e. on A,
+ * whose spectral radius is that of A^T; it may need more steps to converge than on a symmetric A.
  */
 AGP_API int agp_katz_beta(agp_graph_t g, double fraction, int32_t iters, double tol, double *beta,
                   double *lambda1, void *stream);
