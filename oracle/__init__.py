@@ -61,6 +61,8 @@ def lib():
         L.ora_build_csr.restype = C.c_int64
         L.ora_build_csr_directed.argtypes = [C.c_int64, C.c_int64, _i32p, _i32p, C.c_int, _i64p, _i32p, _i32p]
         L.ora_build_csr_directed.restype = C.c_int64
+        L.ora_sweep_conductance.argtypes = [C.c_int64, _i64p, _i32p, _i32p, _f64p, _i32p, C.POINTER(C.c_double)]
+        L.ora_sweep_conductance.restype = C.c_int64
         L.ora_tail_sums.argtypes = [C.c_int, C.c_int, C.c_double, _f64p, _f64p, _f64p]
         L.ora_tail_sums.restype = C.c_int
         L.ora_basic.argtypes = [C.c_int64, _i64p, _i32p, _i32p, C.c_double, C.c_double, C.c_int,
@@ -170,3 +172,14 @@ def randomized(g: CSR, a, b, L, w, Y, eps, x, seed, groups=False, stats=False):
 def power_lambda(g: CSR, iters=1000, tol=1e-13):
     """lambda_1(A) by FP64 power iteration (for Katz beta = fraction / lambda_1)."""
     return lib().ora_power_lambda(g.n, g.rowptr, g.colidx, int(iters), float(tol))
+
+
+def sweep_conductance(g: CSR, pi):
+    """Local-clustering sweep over pi(v)/d_v (see ``ora_sweep_conductance``):
+    returns (best prefix size, its conductance, the swept nodes in order)."""
+    pi = np.ascontiguousarray(pi, np.float64)
+    order = np.full(max(g.n, 1), -1, np.int32)
+    phi = C.c_double(0.0)
+    k = lib().ora_sweep_conductance(g.n, g.rowptr, g.colidx, g.deg, pi, order, C.byref(phi))
+    swept = order[: g.n]
+    return int(k), float(phi.value), swept[swept >= 0].copy()

@@ -483,3 +483,67 @@ double ora_power_lambda(int64_t n, const int64_t *rowptr, const int32_t *colidx,
     free(x); free(y);
     return lam;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Sweep for local clustering (Section 6, local clustering with HKPR): order the nodes by        */
+/* pi(v)/d_v, largest first, and return the prefix S_i with the smallest conductance            */
+/* Phi(S) = |cut(S)| / min(vol(S), 2m - vol(S)), vol(S) = sum of d_v over S, 2m = sum of all d.  */
+/* Readings: only nodes with pi(v) > 0 and d_v > 0 are swept (a zero score gives no order, and    */
+/* d_v = 0 gives no score); ties on the score go to the smaller id; prefixes run over i = 1 ..   */
+/* min(swept, n - 1); a prefix whose min(vol, 2m - vol) is 0 is skipped. The graph is the        */
+/* undirected CSR of ora_build_csr. Returns the best prefix size (0 when no prefix qualifies);    */
+/* order (n entries, may be NULL) receives the swept nodes in order, phi_out the conductance.     */
+/* ------------------------------------------------------------------------------------------ */
+static const double *g_sweep_score;
+
+static int cmp_sweep(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    double sa = g_sweep_score[a], sb = g_sweep_score[b];
+    if (sa != sb) return sa > sb ? -1 : 1;
+    return (a > b) - (a < b);
+}
+
+int64_t ora_sweep_conductance(int64_t n, const int64_t *rowptr, const int32_t *colidx, const int32_t *deg,
+                              const double *pi, int32_t *order, double *phi_out)
+{
+    if (n <= 0) return 0;
+    double *score = (double *)malloc((size_t)n * sizeof(double));
+    int32_t *nodes = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    char *in_s = (char *)calloc((size_t)n, 1);
+    double two_m = 0.0;
+    int64_t k = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        two_m += (double)deg[v];
+        score[v] = deg[v] > 0 ? pi[v] / (double)deg[v] : 0.0;
+        if (deg[v] > 0 && pi[v] > 0.0) nodes[k++] = (int32_t)v;
+    }
+    g_sweep_score = score;
+    qsort(nodes, (size_t)k, sizeof(int32_t), cmp_sweep);
+    g_sweep_score = NULL;
+    int64_t last = k < n - 1 ? k : n - 1;
+    double vol = 0.0, cut = 0.0, best = INFINITY;
+    int64_t best_i = 0;
+    for (int64_t i = 0; i < last; ++i) {
+        int32_t v = nodes[i];
+        /* adding v: its edges into S stop being cut, its other edges start being cut */
+        int64_t inside = 0;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
+            if (in_s[colidx[e]] && colidx[e] != v) ++inside;
+        int64_t loops = 0;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) loops += colidx[e] == v;
+        in_s[v] = 1;
+        vol += (double)deg[v];
+        cut += (double)(deg[v] - loops - 2 * inside);
+        double den = vol < two_m - vol ? vol : two_m - vol;
+        if (den > 0.0 && cut / den < best) {
+            best = cut / den;
+            best_i = i + 1;
+        }
+    }
+    if (order)
+        for (int64_t i = 0; i < n; ++i) order[i] = i < k ? nodes[i] : -1;
+    if (phi_out) *phi_out = best_i > 0 ? best : NAN;
+    free(score); free(nodes); free(in_s);
+    return best_i;
+}

@@ -372,3 +372,58 @@ def test_directed_mass_invariant_and_sink_loss():
     want = G.dense_directed_propagation(G.dense_directed_adjacency(n, src[keep], dst[keep]), 0, 1, w, x)
     np.testing.assert_allclose(pi2, want, rtol=1e-12, atol=1e-16)
     assert pi2.sum() < w.sum() - 1e-6
+
+
+# ---------------------------------------------------------------- local-clustering sweep
+def _conductance_by_sets(n, src, dst, S):
+    """Phi(S) from the definition on the undirected simple graph of the edge list."""
+    E = {(min(a, b), max(a, b)) for a, b in zip(src.tolist(), dst.tolist()) if a != b}
+    deg = np.zeros(n)
+    for a, b in E:
+        deg[a] += 1
+        deg[b] += 1
+    S = set(S)
+    vol = sum(deg[v] for v in S)
+    cut = sum(1 for a, b in E if (a in S) != (b in S))
+    den = min(vol, deg.sum() - vol)
+    return cut / den if den > 0 else np.inf
+
+
+def test_sweep_finds_the_clique_of_a_barbell():
+    """Two K_6 joined by one edge, HKPR from a node of the first clique: the sweep stops at that
+    clique, whose conductance is 1 / (6*5 + 1) (one cut edge, volume 31 on either side)."""
+    k = 6
+    src, dst = [], []
+    for off in (0, k):
+        for i in range(k):
+            for j in range(i + 1, k):
+                src.append(off + i); dst.append(off + j)
+    src.append(0); dst.append(k)
+    src, dst = np.array(src, np.int32), np.array(dst, np.int32)
+    g = oracle.build_csr(2 * k, src, dst)
+    w, Y = oracle.tail_sums(oracle.HKPR, 30, 3.0)
+    x = np.zeros(2 * k); x[2] = 1.0
+    pi = oracle.basic(g, 0, 1, 30, w, Y, x)
+    size, phi, order = oracle.sweep_conductance(g, pi)
+    assert size == k and sorted(order[:k].tolist()) == list(range(k))
+    assert abs(phi - 1.0 / (k * (k - 1) + 1)) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sweep_matches_set_conductance(seed):
+    """The sweep's order is by pi(v)/d_v (largest first, ties by id) over nodes with pi > 0, and its
+    answer is the first prefix of least conductance computed from the definition."""
+    n, src, dst = G.random_multigraph(50, 120, seed, loops=False)
+    g = oracle.build_csr(n, src, dst)
+    w, Y = oracle.tail_sums(oracle.PPR, 6, 0.15)
+    x = np.zeros(n); x[int(np.argmax(g.deg))] = 1.0
+    pi = oracle.basic(g, 0, 1, 6, w, Y, x)
+    size, phi, order = oracle.sweep_conductance(g, pi)
+    live = [v for v in range(n) if g.deg[v] > 0 and pi[v] > 0]
+    want_order = sorted(live, key=lambda v: (-pi[v] / g.deg[v], v))
+    assert order.tolist() == want_order
+    phis = [_conductance_by_sets(n, src, dst, want_order[:i]) for i in range(1, min(len(live), n - 1) + 1)]
+    best = int(np.argmin(phis))
+    assert size == best + 1 and abs(phi - phis[best]) < 1e-12
+    # scaling pi does not change the answer
+    assert oracle.sweep_conductance(g, 7.5 * pi)[:2] == (size, phi)
