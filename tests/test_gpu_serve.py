@@ -86,7 +86,7 @@ def test_mix_equals_alone(agp, graph):
         drifted += 1
         exact, _ = agp.query_sources(g, _exact(agp, p), [s])
         assert equally_accurate(got, want, exact[0].cpu().numpy())
-    assert drifted <= len(reqs) // 4  # most requests are identical up to summation order
+    assert drifted <= len(reqs) // 2  # most requests are identical up to summation order
 
 
 def test_mix_exact_matches_oracle(agp, graph):
