@@ -24,6 +24,8 @@
  *                      replacement, rejection with probability 1 - p_v/p*.
  *   ora_power_lambda   largest eigenvalue of A by FP64 power iteration (Katz needs beta < 1/lambda_1,
  *                      Table 1 / Section 2).
+ *   ora_sweep_conductance  the local-clustering sweep of Section 6: nodes by pi(v)/d_v, the prefix
+ *                      of least conductance.
  *
  * Readings where the paper is silent (listed in the design notes as well):
  *   - isolated nodes (d_u = 0) have D^{-1} := 0, so their residue is reserved and never pushed;
