@@ -760,7 +760,6 @@ def main():
         e2e_value, h2d, d2h = end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev)
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
-    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         base = args.warmup * 2 * Q + Q
