@@ -61,6 +61,8 @@ def lib():
         L.ora_build_csr.restype = C.c_int64
         L.ora_build_csr_directed.argtypes = [C.c_int64, C.c_int64, _i32p, _i32p, C.c_int, _i64p, _i32p, _i32p]
         L.ora_build_csr_directed.restype = C.c_int64
+        L.ora_build_csr_directed_in.argtypes = [C.c_int64, C.c_int64, _i32p, _i32p, C.c_int, _i64p, _i32p, _i32p]
+        L.ora_build_csr_directed_in.restype = C.c_int64
         L.ora_sweep_conductance.argtypes = [C.c_int64, _i64p, _i32p, _i32p, _f64p, _i32p, C.POINTER(C.c_double)]
         L.ora_sweep_conductance.restype = C.c_int64
         L.ora_tail_sums.argtypes = [C.c_int, C.c_int, C.c_double, _f64p, _f64p, _f64p]
@@ -100,15 +102,24 @@ class CSR:
 
 
 def build_csr(n, src, dst, add_self_loops=False, directed=False) -> CSR:
-    """Section 4 pre-sorting: see ``ora_build_csr`` (``ora_build_csr_directed`` when directed:
-    rows are out-neighbours and degrees out-degrees, for the transposed adjacency)."""
+    """Section 4 pre-sorting: see ``ora_build_csr``. directed=True (or "transposed"): rows are
+    out-neighbours and degrees out-degrees (``ora_build_csr_directed``); directed="untransposed":
+    rows are in-neighbours, degrees still out-degrees (``ora_build_csr_directed_in``), so a row's
+    length is not its degree there."""
     src = np.ascontiguousarray(src, np.int32)
     dst = np.ascontiguousarray(dst, np.int32)
     m = src.size
     rowptr = np.zeros(n + 1, np.int64)
     colidx = np.zeros(max(2 * m + (n if add_self_loops else 0), 1), np.int32)
     deg = np.zeros(max(n, 1), np.int32)
-    fn = lib().ora_build_csr_directed if directed else lib().ora_build_csr
+    if directed == "untransposed":
+        fn = lib().ora_build_csr_directed_in
+    elif directed in (True, "transposed"):
+        fn = lib().ora_build_csr_directed
+    elif not directed:
+        fn = lib().ora_build_csr
+    else:
+        raise ValueError("directed must be False, True, 'transposed' or 'untransposed'")
     nnz = fn(n, m, src, dst, int(bool(add_self_loops)), rowptr, colidx, deg)
     if nnz < 0:
         raise ValueError("ora_build_csr: bad argument")

@@ -15,6 +15,8 @@
  *                      rows are sorted by neighbour degree (ties by neighbour id).
  *   ora_build_csr_directed  the same for a directed graph (Section 4, "Propagation on directed
  *                      graph", transposed adjacency): rows are out-neighbours, degrees out-degrees.
+ *   ora_build_csr_directed_in  the untransposed adjacency of that passage (single-target PPR): rows
+ *                      are in-neighbours, degrees still out-degrees.
  *   ora_tail_sums      Def. 3.1: Y_i = sum_{k>=i} w_k, for the weight sequences of Table 1.
  *   ora_basic          Algorithm 1 (Basic Propagation), exact truncated sum.
  *   ora_randomized     Algorithm 2 (Randomized Propagation), subset sampling done neighbour by
@@ -103,7 +105,10 @@ static int cmp_by_degree_then_id(const void *pa, const void *pb)
  * directed = 0: undirected graph as above. directed = 1: "Propagation on directed graph"
  * (end of Section 4) with the transposed adjacency of PageRank, PPR, HKPR and Katz: r^(i+1)(v)
  * sums over the in-neighbours u of v, so the push list of u is its out-neighbours, each edge
- * (u, v) gives v in N_u only, and d_u is the out-degree. Rows are sorted by (d_out(v), v). */
+ * (u, v) gives v in N_u only, and d_u is the out-degree. Rows are sorted by (d_out(v), v).
+ * directed = 2: the untransposed adjacency of the same passage (single-target PPR): r^(i+1)(v)
+ * sums over the out-neighbours u of v, so the push list of u is its in-neighbours, while d stays
+ * the out-degree; rows are sorted by (d_out(v), v) and their length is the in-degree. */
 static int64_t build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, int add_self_loops,
                          int directed, int64_t *rowptr, int32_t *colidx, int32_t *deg)
 {
@@ -115,8 +120,8 @@ static int64_t build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t
     int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t e = 0; e < m; ++e) {
         if (src[e] == dst[e]) continue;
-        cnt[src[e]]++;
-        if (!directed) cnt[dst[e]]++;
+        if (directed != 2) cnt[src[e]]++;
+        if (directed != 1) cnt[dst[e]]++;
     }
     int64_t *start = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     start[0] = 0;
@@ -126,34 +131,42 @@ static int64_t build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t
     for (int64_t u = 0; u < n; ++u) fill[u] = start[u];
     for (int64_t e = 0; e < m; ++e) {
         if (src[e] == dst[e]) continue;
-        tmp[fill[src[e]]++] = dst[e];
-        if (!directed) tmp[fill[dst[e]]++] = src[e];
+        if (directed != 2) tmp[fill[src[e]]++] = dst[e];
+        if (directed != 1) tmp[fill[dst[e]]++] = src[e];
     }
     if (add_self_loops)
         for (int64_t u = 0; u < n; ++u) tmp[fill[u]++] = (int32_t)u;
 
     /* 2. merge repeated neighbours: sort each row by id and keep the first of each run */
+    int64_t *rowlen = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     for (int64_t u = 0; u < n; ++u) {
         int64_t len = fill[u] - start[u];
         qsort(tmp + start[u], (size_t)len, sizeof(int32_t), cmp_by_id);
         int64_t k = 0;
         for (int64_t j = 0; j < len; ++j)
             if (j == 0 || tmp[start[u] + j] != tmp[start[u] + j - 1]) tmp[start[u] + k++] = tmp[start[u] + j];
-        deg[u] = (int32_t)k;
+        rowlen[u] = k;
     }
 
-    /* 3. compact into the output and sort every row by (degree, id) */
+    /* 3. degrees: the row length, except for in-neighbour rows, whose nodes keep their out-degree
+     *    (the number of rows a node appears in) */
+    for (int64_t u = 0; u < n; ++u) deg[u] = directed == 2 ? 0 : (int32_t)rowlen[u];
+    if (directed == 2)
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t j = 0; j < rowlen[u]; ++j) deg[tmp[start[u] + j]]++;
+
+    /* 4. compact into the output and sort every row by (degree, id) */
     rowptr[0] = 0;
-    for (int64_t u = 0; u < n; ++u) rowptr[u + 1] = rowptr[u] + deg[u];
+    for (int64_t u = 0; u < n; ++u) rowptr[u + 1] = rowptr[u] + rowlen[u];
     for (int64_t u = 0; u < n; ++u)
-        memcpy(colidx + rowptr[u], tmp + start[u], (size_t)deg[u] * sizeof(int32_t));
+        memcpy(colidx + rowptr[u], tmp + start[u], (size_t)rowlen[u] * sizeof(int32_t));
     g_sort_deg = deg;
     for (int64_t u = 0; u < n; ++u)
-        qsort(colidx + rowptr[u], (size_t)deg[u], sizeof(int32_t), cmp_by_degree_then_id);
+        qsort(colidx + rowptr[u], (size_t)rowlen[u], sizeof(int32_t), cmp_by_degree_then_id);
     g_sort_deg = NULL;
 
     int64_t nnz = rowptr[n];
-    free(cnt); free(start); free(tmp); free(fill);
+    free(cnt); free(start); free(tmp); free(fill); free(rowlen);
     return nnz;
 }
 
@@ -167,6 +180,12 @@ int64_t ora_build_csr_directed(int64_t n, int64_t m, const int32_t *src, const i
                                int add_self_loops, int64_t *rowptr, int32_t *colidx, int32_t *deg)
 {
     return build_csr(n, m, src, dst, add_self_loops, 1, rowptr, colidx, deg);
+}
+
+int64_t ora_build_csr_directed_in(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                  int add_self_loops, int64_t *rowptr, int32_t *colidx, int32_t *deg)
+{
+    return build_csr(n, m, src, dst, add_self_loops, 2, rowptr, colidx, deg);
 }
 
 /* ------------------------------------------------------------------------------------------ */

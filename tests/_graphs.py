@@ -94,14 +94,15 @@ def dense_directed_adjacency(n, src, dst, add_self_loops=False):
     return A
 
 
-def dense_directed_propagation(A, a, b, w, x):
-    """sum_i w_i (D^-a A^T D^-b)^i x with D the out-degree matrix (directed graphs, transposed
-    adjacency), dense FP64 powers; D^0 = I, and D^-p := 0 at out-degree 0 for p > 0."""
+def dense_directed_propagation(A, a, b, w, x, transposed=True):
+    """sum_i w_i (D^-a Ã D^-b)^i x with D the out-degree matrix, Ã = A^T (transposed, PageRank,
+    PPR, HKPR, Katz) or A (single-target PPR); dense FP64 powers; D^0 = I, and D^-p := 0 at
+    out-degree 0 for p > 0."""
     d = A.sum(1)
     with np.errstate(divide="ignore"):
         da = np.ones_like(d) if a == 0 else np.where(d > 0, d ** (-a), 0.0)
         db = np.ones_like(d) if b == 0 else np.where(d > 0, d ** (-b), 0.0)
-    M = da[:, None] * A.T * db[None, :]
+    M = da[:, None] * (A.T if transposed else A) * db[None, :]
     out = np.zeros(A.shape[0])
     v = np.asarray(x, np.float64).copy()
     for i, wi in enumerate(w):

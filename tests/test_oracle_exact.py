@@ -427,3 +427,50 @@ def test_sweep_matches_set_conductance(seed):
     assert size == best + 1 and abs(phi - phis[best]) < 1e-12
     # scaling pi does not change the answer
     assert oracle.sweep_conductance(g, 7.5 * pi)[:2] == (size, phi)
+
+
+# Untransposed adjacency (single-target PPR on a directed graph): r^(i+1)(v) sums over the
+# out-neighbours u of v, so u pushes to its in-neighbours; degrees stay out-degrees.
+@pytest.mark.parametrize("seed", [1, 2])
+def test_untransposed_csr_matches_set_construction(seed):
+    n, src, dst = G.random_multigraph(60, 150, seed)
+    g = oracle.build_csr(n, src, dst, directed="untransposed")
+    inn = [set() for _ in range(n)]
+    outdeg = np.zeros(n, np.int32)
+    pairs = {(s, d) for s, d in zip(src.tolist(), dst.tolist()) if s != d}
+    for s_, d_ in pairs:
+        inn[d_].add(s_)
+        outdeg[s_] += 1
+    np.testing.assert_array_equal(g.deg, outdeg)
+    assert np.array_equal(np.diff(g.rowptr), [len(r) for r in inn])
+    for u in range(n):
+        assert g.colidx[g.rowptr[u]:g.rowptr[u + 1]].tolist() == sorted(inn[u], key=lambda v: (outdeg[v], v))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_untransposed_basic_matches_dense_matrix_powers(seed):
+    rng = np.random.default_rng(500 + seed)
+    n, src, dst = G.random_multigraph(40, 70, seed)
+    g = oracle.build_csr(n, src, dst, directed="untransposed")
+    A = G.dense_directed_adjacency(n, src, dst)
+    a, b = (1.0, 0.0) if seed == 0 else (rng.random(), rng.random())  # seed 0: the preset
+    L = int(rng.integers(1, 9))
+    w = rng.random(L + 1)
+    x = rng.standard_normal(n)
+    wl, Y = oracle.tail_sums(oracle.FINITE, L, w=w)
+    got = oracle.basic(g, a, b, L, wl, Y, x)
+    want = G.dense_directed_propagation(A, a, b, w, x, transposed=False)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+def test_untransposed_cycle_goes_backwards():
+    """With the untransposed adjacency the directed cycle carries mass backwards: e_s -> e_{s-L}."""
+    n, s = 7, 2
+    src, dst = _directed_cycle(n)
+    g = oracle.build_csr(n, src, dst, directed="untransposed")
+    for L in (1, 4, 10):
+        w, Y = oracle.tail_sums(oracle.TRANSITION, L)
+        x = np.zeros(n); x[s] = 1.0
+        pi = oracle.basic(g, 0, 1, L, w, Y, x)
+        want = np.zeros(n); want[(s - L) % n] = 1.0
+        np.testing.assert_allclose(pi, want, atol=1e-15)
