@@ -130,7 +130,7 @@ typedef struct {
     double param;         /* alpha, t or beta for PPR, HKPR, KATZ                                 */
     const double *w;      /* FINITE only: host array of L+1 non-negative weights, sum > 0        */
     double eps;           /* error parameter of Algorithm 2, >= 0; 0 = exact (Algorithm 1)        */
-    uint64_t seed;        /* random stream of this query; results depend only on (inputs, seed) */
+    uint64_t seed;        /* random stream of this query (see agp_query_batch for shared params)  */
 } agp_params_t;
 
 /* Per-query counters (Theorem 4.3 counts cost as deterministic pushes plus accepted samples). */
@@ -170,7 +170,10 @@ typedef struct {
  * random stream, pi = ||x+||_1 pi(x+/||x+||_1) - ||x-||_1 pi(x-/||x-||_1). Weights are normalised
  * by Y_0 and the result rescaled (Section 3, "Assumptions on w_i"). eps applies to the normalised
  * residues.
- *   params    n_params == 1: shared by all queries; n_params == Q: one per query (host memory)
+ *   params    n_params == 1: shared by all queries, and query q draws its random numbers from the
+ *             stream (seed, q), so queries of one batch do not repeat one another's draws; n_params
+ *             == Q: one per query (host memory), each query drawing from its own seed alone, so a
+ *             query gives the same draws in any batch and at any position
  *   x_off     Q+1 int64 offsets; x_idx / x_val as above; host or device (AGP_INPUT_ON_DEVICE)
  *   pi_out    Q rows of ld_out >= n floats, row q = estimate of pi for query q (dense FP32);
  *             host or device (AGP_OUTPUT_ON_DEVICE). Every entry of each row [0, n) is written.
@@ -188,6 +191,25 @@ AGP_API int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n
 AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, const int32_t *x_idx,
               const float *x_val, float *pi_out, uint32_t flags, agp_stats_t *stats,
               void *stream);
+
+/*
+ * Batched queries with dense signals (Algorithm 2 per query; Table 1's PageRank row uses x = 1/n):
+ * query q has the dense signal x_q(u) = X[q * ldx + u], u < n, in FP32, or in bfloat16 (raw 16-bit
+ * patterns) with AGP_DENSE_BF16. Sign parts, normalisation, eps and output are as for
+ * agp_query_batch; the parts' L1 norms are reduced in a fixed order (no atomics), so they do not
+ * depend on scheduling.
+ *   X        Q rows of ldx >= n elements; host or device (AGP_INPUT_ON_DEVICE). Host rows are
+ *            copied to the graph's device staging first.
+ *   pi_out   Q rows of ld_out >= n floats; host or device (AGP_OUTPUT_ON_DEVICE)
+ *   flags    AGP_INPUT_ON_DEVICE, AGP_OUTPUT_ON_DEVICE, AGP_PLAIN, AGP_COLLECT_STATS, AGP_PROFILE,
+ *            AGP_EPS_ABSOLUTE, AGP_DENSE_BF16
+ * The call synchronises `stream` once after the norms, and at the end when pi_out or stats are host
+ * memory. Errors as agp_query_batch (a non-finite entry of X: AGP_EINVAL).
+ */
+#define AGP_DENSE_BF16 0x40u
+AGP_API int agp_query_dense(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const void *X,
+                            int64_t ldx, float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats,
+                            void *stream);
 
 /*
  * Feature propagation for GNNs (Section 5.2; SGC, APPNP and GDC rows of Table 1): every column
@@ -332,8 +354,10 @@ AGP_API int agp_profile_read(agp_graph_t g, double *ms, int64_t *launches, int64
  *           returns it); caller-owned, only read
  *   iters, tol as agp_katz_beta; lambda1: host output
  *   stream  the call enqueues on it and synchronises it every iteration
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. All calls share the one array and each starts by
+ * Every call looks up the array's device address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing), so a device reset or another current context is handled. The first call on a
+ * device may load the library's device code there: make that first call before any stream capture.
+ * All calls share the one array and each starts by
  * re-initialising it, so calls that overlap on the GPU (other threads or streams) race: callers
  * must serialise them.
  */
@@ -349,6 +373,22 @@ AGP_API int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int3
  */
 AGP_API int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes,
                   const float *c, int32_t *k_out, void *stream);
+
+/*
+ * Level coefficients of Def. 3.1 as the level pipeline computes them on the device (FP64), for a
+ * signal part of unit L1 norm: with Y_i = sum_{k>=i} w_k,
+ *     keep[i] = Y_0 * w_i / Y_i   (reserve factor of level i: pi(u) += keep[i] * r^(i)(u)),
+ *     push[i] = Y_{i+1} / Y_i     (factor of every increment pushed at level i; 0 at i = L),
+ * for i = 0..L, and *y0 = Y_0 (the normaliser of Section 3, "Assumptions on w_i"). Entries after a
+ * zero tail are zero (nothing reaches those levels). The level kernels store keep (times the sign
+ * part's norm) and push rounded to FP32. Exposes the step for parity checks.
+ *   params  as for agp_query_batch (host); keep, push: host arrays of L+1 doubles; y0 may be NULL
+ *   device  CUDA device ordinal to compute on; stream: enqueued there and synchronised
+ * Allocates a few hundred bytes of device memory for the call.
+ * Errors: AGP_EINVAL (parameters out of range, NULL arrays), AGP_ECUDA.
+ */
+AGP_API int agp_coefficients(const agp_params_t *params, double *keep, double *push, double *y0, int device,
+                             void *stream);
 
 #ifdef __cplusplus
 }

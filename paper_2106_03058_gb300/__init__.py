@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
-    "feature_propagate", "katz_beta", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
     "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "MAX_LEVELS",
@@ -28,6 +28,7 @@ __all__ = [
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+DENSE_BF16 = 0x40
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
 ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED = 0x1, 0x2, 0x4
 MAX_LEVELS = 64
@@ -109,6 +110,9 @@ def lib():
             L.agp_feature_propagate.argtypes = [_vp, C.POINTER(Params), _vp, _i64, _i64, _vp, _i64, _u32, _vp]
             L.agp_katz_beta.argtypes = [_vp, _dbl, _i32, _dbl, C.POINTER(_dbl), C.POINTER(_dbl), _vp]
             L.agp_threshold.argtypes = [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp]
+            L.agp_query_dense.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _i64, _vp, _i64, _u32,
+                                          C.POINTER(Stats), _vp]
+            L.agp_coefficients.argtypes = [C.POINTER(Params), _vp, _vp, C.POINTER(_dbl), C.c_int, _vp]
             L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
             L.agp_graph_set_wave_lanes.argtypes = [_vp, _i32]
             L.agp_katz_lambda_noalloc.argtypes = [_i64, _vp, _vp, _i32, _dbl, C.POINTER(_dbl), _vp]
@@ -128,7 +132,7 @@ def lib():
                 getattr(L, f).restype = C.c_int
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
-                      "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune"):
+                      "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -294,6 +298,30 @@ def query_batch(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=0, stats
     return st
 
 
+def query_dense(g, params, X, out=None, flags=0, stats=None, stream=None):
+    """``agp_query_dense``: X is [Q, >= n] float32 or bfloat16 (numpy on the host, torch CUDA on the
+    device); returns (out [Q, n] float32 on X's side, stats)."""
+    import torch
+    on_dev = torch.is_tensor(X) and X.is_cuda
+    Q = int(X.shape[0])
+    bf16 = (X.dtype == torch.bfloat16) if torch.is_tensor(X) else False
+    if torch.is_tensor(X) and not on_dev:
+        X = X.contiguous().numpy() if not bf16 else X.contiguous().view(torch.int16).numpy()
+    ldx = int(X.stride(0) if torch.is_tensor(X) else X.strides[0] // X.itemsize)
+    if out is None:
+        out = (torch.empty((Q, g.n), dtype=torch.float32, device=f"cuda:{g.device}") if on_dev
+               else np.zeros((Q, g.n), np.float32))
+    ld = int(out.stride(0) if torch.is_tensor(out) else out.strides[0] // 4)
+    fl = int(flags) | (INPUT_ON_DEVICE if on_dev else 0) | (DENSE_BF16 if bf16 else 0)
+    if torch.is_tensor(out) and out.is_cuda:
+        fl |= OUTPUT_ON_DEVICE
+    parr, np_, keep = _params_array(params, Q)
+    st = (Stats * Q)() if (fl & COLLECT_STATS) and stats is None else stats
+    _check("agp_query_dense", lib().agp_query_dense(g.handle, parr, np_, Q, _ptr(X), ldx, _ptr(out), ld, fl, st,
+                                                     _stream(stream)))
+    return out, st
+
+
 def autotune(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=INPUT_ON_DEVICE | OUTPUT_ON_DEVICE,
              candidates=None, stream=None):
     """``agp_autotune``: returns (best lanes, best ms or -1 when taken from the cache)."""
@@ -454,3 +482,14 @@ def threshold(g, a, eps, nodes, c, k_out, stream=None):
     _check("agp_threshold", lib().agp_threshold(g.handle, float(a), float(eps), int(nodes.numel()), nodes.data_ptr(),
                                                  c.data_ptr(), k_out.data_ptr(), _stream(stream)))
     return k_out
+
+
+def coefficients(params, device=0, stream=None):
+    """``agp_coefficients``: (keep[0..L], push[0..L], Y_0) in FP64 as the device computes them."""
+    L = int(params.L)
+    keep = np.zeros(L + 1, np.float64)
+    push = np.zeros(L + 1, np.float64)
+    y0 = _dbl()
+    _check("agp_coefficients", lib().agp_coefficients(C.byref(params), keep.ctypes.data, push.ctypes.data, C.byref(y0),
+                                                       int(device), _stream(stream)))
+    return keep, push, y0.value

@@ -31,11 +31,13 @@ int fail(int code, const std::string &msg);
     } while (0)
 
 // ---------------------------------------------------------------- launch geometry
-// GB300: 152 SMs. Grid-stride kernels use a multiple of the SM count so that every SM gets the
-// same number of resident blocks.
-constexpr int kNumSMs = 152;
+// Grid-stride kernels use a multiple of the SM count (152 on GB300, read from the device) so that
+// every SM gets the same number of resident blocks.
 constexpr int kBlock = 256;
-constexpr int kGridStrideBlocks = kNumSMs * 8;
+// SMs of the current device (cudaDevAttrMultiProcessorCount, cached per device ordinal).
+int sm_count();
+// Grid of the grid-stride kernels: 8 blocks of kBlock threads per SM.
+inline int grid_stride_blocks() { return 8 * sm_count(); }
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds
@@ -122,6 +124,8 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
               double *lambda1, cudaStream_t stream);
 int katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int iters, double tol,
                         double *lambda1, cudaStream_t stream);
+int coefficients(const agp_params_t *p, double *keep, double *push, double *y0, int device, cudaStream_t s);
+int validate_params(const agp_params_t &p);
 int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t *nodes,
               const float *c, int32_t *k_out, cudaStream_t stream);
 int wave_lanes(const agp_graph_s *g);
@@ -132,6 +136,8 @@ int autotune(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32
 int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q,
                 const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
                 int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);
+int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q, const void *X, int64_t ldx,
+                float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d,
                       int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t stream);
 

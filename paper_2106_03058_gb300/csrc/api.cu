@@ -1,11 +1,12 @@
 // api.cu -- the extern "C" entry points of include/agp.h, error reporting and the Katz bound.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
-#include "agp_internal.cuh"
+#include "lanes.cuh"
 
 namespace agp {
 
@@ -19,6 +20,25 @@ int fail(int code, const std::string &msg)
 {
     g_detail = msg;
     return code;
+}
+
+int sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
 
 // ---- Katz spectral bound: lambda_1(A) by FP64 power iteration on A + I --------------------------
@@ -89,14 +109,14 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
         cleanup();
         return fail(AGP_ENOMEM, "katz_beta: device allocation");
     }
-    k_fill<<<kGridStrideBlocks, kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
+    k_fill<<<grid_stride_blocks(), kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
     double lam = 0.0, prev = 0.0, h[2];
     int rc = AGP_OK;
     for (int it = 0; it < iters; ++it) {
-        k_spmv_shift<<<kGridStrideBlocks, kBlock, 0, s>>>(g->dev(), x, y);
+        k_spmv_shift<<<grid_stride_blocks(), kBlock, 0, s>>>(g->dev(), x, y);
         cudaMemsetAsync(acc, 0, sizeof(double) * 2, s);
-        k_dots<<<kGridStrideBlocks, kBlock, 0, s>>>(x, y, n, acc);
-        k_scale<<<kGridStrideBlocks, kBlock, 0, s>>>(y, x, n, acc);
+        k_dots<<<grid_stride_blocks(), kBlock, 0, s>>>(x, y, n, acc);
+        k_scale<<<grid_stride_blocks(), kBlock, 0, s>>>(y, x, n, acc);
         if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             rc = fail(AGP_ECUDA, std::string("katz_beta: ") + cudaGetErrorString(cudaGetLastError()));
@@ -124,28 +144,22 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
 //
 // The array is part of the loaded library: every GPU that loads it holds these 64 MiB until the
 // process exits. Host code must not use the symbol as an address (on the host it names a stand-in
-// variable); the device address is looked up once per device with cudaGetSymbolAddress.
+// variable); the device address is looked up with cudaGetSymbolAddress on every call, with the
+// caller's device current. The lookup allocates nothing, and doing it per call (rather than caching
+// it per device ordinal) keeps the address right after a device reset or when the caller has made
+// another context current on the same ordinal.
 constexpr int64_t kNoAllocMaxNodes = 4194304;  // 2^22 nodes: x and y of 32 MiB each
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxNodes + 64];
 
 namespace {
 
-std::mutex g_noalloc_mutex;
-double *g_noalloc_ptr[64] = {};  // device address of g_noalloc_scratch, per device ordinal
-
-// Called with `device` current. The first call on a device does the lookup.
-int noalloc_scratch(int device, double **out)
+int noalloc_scratch(double **out)
 {
-    if (device < 0 || device >= 64) return fail(AGP_EINVAL, "device ordinal outside [0, 64)");
-    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(AGP_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
-        g_noalloc_ptr[device] = (double *)p;
-    }
-    *out = g_noalloc_ptr[device];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(AGP_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+    *out = (double *)p;
     return AGP_OK;
 }
 
@@ -160,21 +174,19 @@ int katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx,
                                     " exceeds the fixed scratch of 4194304 nodes; use agp_katz_beta");
     if (!rowptr || !colidx || !lambda1) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: NULL argument");
     if (iters < 1 || !(tol >= 0.0)) return fail(AGP_EINVAL, "agp_katz_lambda_noalloc: need iters >= 1, tol >= 0");
-    int device = 0;
-    AGP_CUDA_TRY(cudaGetDevice(&device));
     double *base = nullptr;
-    AGP_TRY(noalloc_scratch(device, &base));
+    AGP_TRY(noalloc_scratch(&base));
     double *x = base, *y = base + kNoAllocMaxNodes, *acc = base + 2 * kNoAllocMaxNodes;
     DevGraph g{n, 0, rowptr, colidx, nullptr};
     // the scratch keeps the previous call's contents: x is re-initialised, acc cleared per step
-    k_fill<<<kGridStrideBlocks, kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
+    k_fill<<<grid_stride_blocks(), kBlock, 0, s>>>(x, n, 1.0 / std::sqrt((double)n));
     AGP_CUDA_TRY(cudaGetLastError());
     double lam = 0.0, prev = 0.0, h[2] = {0.0, 0.0};
     for (int it = 0; it < iters; ++it) {
-        k_spmv_shift<<<kGridStrideBlocks, kBlock, 0, s>>>(g, x, y);
+        k_spmv_shift<<<grid_stride_blocks(), kBlock, 0, s>>>(g, x, y);
         AGP_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 2, s));
-        k_dots<<<kGridStrideBlocks, kBlock, 0, s>>>(x, y, n, acc);
-        k_scale<<<kGridStrideBlocks, kBlock, 0, s>>>(y, x, n, acc);
+        k_dots<<<grid_stride_blocks(), kBlock, 0, s>>>(x, y, n, acc);
+        k_scale<<<grid_stride_blocks(), kBlock, 0, s>>>(y, x, n, acc);
         AGP_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
         AGP_CUDA_TRY(cudaStreamSynchronize(s));
         prev = lam;
@@ -277,6 +289,7 @@ int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n_params,
                     const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
                     agp_stats_t *stats, void *stream)
 {
+    if (flags & agp::kOffsetsOnHost) return agp::fail(AGP_EINVAL, "unknown flag");
     return agp::query_batch(g, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, stats,
                             (cudaStream_t)stream);
 }
@@ -286,23 +299,18 @@ int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, const in
 {
     if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
     if (x_nnz < 0) return agp::fail(AGP_EINVAL, "x_nnz < 0");
-    if (flags & AGP_INPUT_ON_DEVICE) {
-        // offsets must live where the signal lives: stage them through the graph's input buffer
-        int64_t *d_off = nullptr;
-        if (cudaMalloc(&d_off, 2 * sizeof(int64_t)) != cudaSuccess) {
-            cudaGetLastError();
-            return agp::fail(AGP_ENOMEM, "agp_query: offsets");
-        }
-        const int64_t h_off[2] = {0, x_nnz};
-        cudaMemcpy(d_off, h_off, sizeof(h_off), cudaMemcpyHostToDevice);
-        const int rc = agp::query_batch(g, params, 1, 1, d_off, x_idx, x_val, pi_out, g->n, flags, stats,
-                                        (cudaStream_t)stream);
-        cudaStreamSynchronize((cudaStream_t)stream);
-        cudaFree(d_off);
-        return rc;
-    }
+    if (flags & agp::kOffsetsOnHost) return agp::fail(AGP_EINVAL, "unknown flag");
+    // the two offsets are known here: they are passed from the host even when the signal is on the
+    // device (no per-call device allocation or synchronisation)
+    if (flags & AGP_INPUT_ON_DEVICE) flags |= agp::kOffsetsOnHost;
     const int64_t h_off[2] = {0, x_nnz};
     return agp::query_batch(g, params, 1, 1, h_off, x_idx, x_val, pi_out, g->n, flags, stats, (cudaStream_t)stream);
+}
+
+int agp_query_dense(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const void *X, int64_t ldx,
+                    float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, void *stream)
+{
+    return agp::query_dense(g, params, n_params, Q, X, ldx, pi_out, ld_out, flags, stats, (cudaStream_t)stream);
 }
 
 int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, const uint16_t *X, int64_t d, int64_t ldx,
@@ -336,6 +344,11 @@ int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col
                             double *lambda1, void *stream)
 {
     return agp::katz_lambda_noalloc(n, rowptr, colidx, iters, tol, lambda1, (cudaStream_t)stream);
+}
+
+int agp_coefficients(const agp_params_t *params, double *keep, double *push, double *y0, int device, void *stream)
+{
+    return agp::coefficients(params, keep, push, y0, device, (cudaStream_t)stream);
 }
 
 int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes, const float *c,

@@ -128,7 +128,7 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     const int ubits = bits_for(std::max<int64_t>(n, 2));
     const uint64_t sentinel = 1ull << (2 * ubits);
     const int64_t E = 2 * m + (loops ? n : 0);
-    const int grid = kGridStrideBlocks;
+    const int grid = grid_stride_blocks();
 
     DevBuf d_src, d_dst;
     const int32_t *s = src, *t = dst;

@@ -6,6 +6,7 @@
 // out[u * su].
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "agp_internal.cuh"
@@ -19,6 +20,8 @@ constexpr int kInlineDet = 32;       // prefixes up to this length stay with the
 constexpr float kLightSamples = 8.f; // tails expected to yield at most this many trials stay inline
 constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
 constexpr float kDenseP = 0.25f;     // tails whose largest probability is >= this are sampled per position
+constexpr uint32_t kOffsetsOnHost = 0x80000000u;  // internal query flag: x_off is host memory even
+                                                   // when x_idx / x_val are on the device
 constexpr uint32_t kSampleTag = 0x53414D50u;  // Philox counter word of the skip sampler
 constexpr uint32_t kDenseTag = 0x44534E53u;   // Philox counter word of the per-position sampler
 
@@ -97,7 +100,7 @@ struct KArgs {
     float *c_item;
     int2 *k_item;             // (prefix length, tail segment length)
     uint2 *nrec;              // per item: (prefix chunks, tail records | dense bit)
-    unsigned long long *rpart;  // [3][kGridStrideBlocks] per-block record counts / offsets
+    unsigned long long *rpart;  // [3][grid] per-block record counts / offsets
     uint2 *det_rec, *smp_rec, *dns_rec;
     unsigned long long cap_items, cap_det, cap_smp, cap_dns;
     const LaneParam *lanes;
@@ -106,12 +109,14 @@ struct KArgs {
     LaneStats *stats;
     int collect;
     int G;
+    int grid;                 // blocks of the grid-stride level kernels (8 per SM of the device)
     Ctrl *ctrl;
 };
 
 struct Workspace {
     int device = 0;
     int G = 0;
+    int grid = 0;                      // grid-stride blocks of the device (rpart holds 3 rows of it)
     int64_t n = 0;
     unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0, cap_dns = 0;
     float *R = nullptr;
@@ -173,6 +178,10 @@ struct ExecCtx {
 int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_t n_params, int32_t Q,
                     const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
                     int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s);
+int run_queries(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_t n_params, int32_t Q,
+                const std::vector<double> &norms,
+                const std::function<int(const KArgs &A, const int32_t *d_aux, cudaStream_t st)> &seed,
+                float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s);
 int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, const uint16_t *X, int64_t d,
                           int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t s);
 int exponent_mode(double p);

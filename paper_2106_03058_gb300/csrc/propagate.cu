@@ -718,70 +718,6 @@ __global__ void k_level_end(KArgs A)
     }
 }
 
-// ---- coefficients (Def. 3.1), FP64 on the device -------------------------------------------
-__global__ void k_coef(const CoefSpec *spec, const double *wts, float2 *coef, int nlanes)
-{
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nlanes) return;
-    const CoefSpec S = spec[l];
-    const int L = S.L;
-    double w[kMaxLevels], Y[kMaxLevels + 1];
-    switch (S.kind) {
-    case AGP_W_FINITE: {
-        for (int i = 0; i <= L; ++i) w[i] = wts[S.w_off + i];
-        double acc = 0.0;  // smallest terms last in the list are added first
-        Y[L + 1] = 0.0;
-        for (int i = L; i >= 0; --i) { acc += w[i]; Y[i] = acc; }
-        break;
-    }
-    case AGP_W_PPR: {
-        const double al = S.param;
-        for (int i = 0; i <= L + 1; ++i) {
-            const double t = pow(1.0 - al, (double)i);
-            if (i <= L) w[i] = al * t;
-            Y[i] = t;
-        }
-        break;
-    }
-    case AGP_W_HKPR: {
-        const double t = S.param;
-        int K = L + 2;
-        while (K < 100000 && (K < t + 1.0 || -t + K * log(t) - lgamma(K + 1.0) > -690.0)) ++K;
-        double acc = 0.0;
-        for (int k = K; k >= 0; --k) {
-            const double wk = exp(-t + k * log(t) - lgamma(k + 1.0));
-            acc += wk;
-            if (k <= L + 1) Y[k] = acc;
-            if (k <= L) w[k] = wk;
-        }
-        break;
-    }
-    case AGP_W_KATZ: {
-        const double be = S.param;
-        for (int i = 0; i <= L + 1; ++i) {
-            const double t = pow(be, (double)i);
-            if (i <= L) w[i] = t;
-            Y[i] = t / (1.0 - be);
-        }
-        break;
-    }
-    default: {  // TRANSITION
-        for (int i = 0; i <= L; ++i) { w[i] = (i == L) ? 1.0 : 0.0; Y[i] = 1.0; }
-        Y[L + 1] = 0.0;
-        break;
-    }
-    }
-    const double Y0 = Y[0];
-    for (int i = 0; i < kMaxLevels; ++i) {
-        float keep = 0.f, push = 0.f;
-        if (i <= L && Y[i] > 0.0) {
-            keep = (float)(S.scale * Y0 * (w[i] / Y[i]));
-            push = (i < L) ? (float)(Y[i + 1] / Y[i]) : 0.f;
-        }
-        coef[S.lane * kMaxLevels + i] = make_float2(keep, push);
-    }
-}
-
 // ---- seeds -------------------------------------------------------------------------------------
 __device__ __forceinline__ int query_of(const int64_t *off, int Q, int64_t t)
 {
@@ -868,6 +804,72 @@ __global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const
         float *R0 = A.R + (size_t)lane * A.ldR;
         const float r0 = (float)((double)fabsf(x) / norms[2 * col + part]);
         push_to(R0, (int32_t)u, r0);
+    }
+}
+
+// ---- dense signal rows (agp_query_dense) ----------------------------------------------------------
+__device__ __forceinline__ float load_x(const float *X, int64_t i) { return X[i]; }
+__device__ __forceinline__ float load_x(const uint16_t *X, int64_t i) { return __uint_as_float((uint32_t)X[i] << 16); }
+
+// Sign-part norms of the rows of X in a fixed order, so they do not depend on scheduling: row q is
+// cut into `chunks` ranges (blockIdx.x), each reduced by one block (per-thread sums in index order,
+// then a shuffle tree and the warp totals in order) into part[(q * chunks + c) * 2 + {0: x+, 1: x-}];
+// k_rownorm_sum adds a row's ranges in order. Non-finite entries set *bad.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_rownorm_part(const T *X, int64_t ldx, int64_t n, int chunks, double *part,
+                                                         unsigned int *bad)
+{
+    __shared__ double sm[2][kBlock / 32];
+    const int q = blockIdx.y, c = blockIdx.x;
+    const int64_t per = (n + chunks - 1) / chunks, r0 = (int64_t)c * per, r1 = min(n, r0 + per);
+    double sp = 0.0, sn = 0.0;
+    for (int64_t u = r0 + threadIdx.x; u < r1; u += kBlock) {
+        const float x = load_x(X, (int64_t)q * ldx + u);
+        if (!isfinite(x)) atomicOr(bad, 1u);
+        else if (x > 0.f) sp += (double)x;
+        else if (x < 0.f) sn -= (double)x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sp += __shfl_down_sync(0xffffffffu, sp, o);
+        sn += __shfl_down_sync(0xffffffffu, sn, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][threadIdx.x >> 5] = sp;
+        sm[1][threadIdx.x >> 5] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) t += sm[threadIdx.x][w];
+        part[((size_t)q * chunks + c) * 2 + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_rownorm_sum(const double *part, int chunks, int Q, double *norms)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // t = 2q + sign part
+    if (t >= 2 * Q) return;
+    const int q = t >> 1, sgn = t & 1;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += part[((size_t)q * chunks + c) * 2 + sgn];
+    norms[t] = s;
+}
+
+// r^(0) of the lanes of dense rows: entry (q, u) of sign part s goes to lane lane_of[2q + s] as
+// |x| / ||x_s||_1 (each (lane, u) receives exactly one value, so the seed is order-free).
+template <typename T>
+__global__ void k_seed_dense_rows(KArgs A, const T *X, int64_t ldx, int Q, const int32_t *lane_of, const double *norms)
+{
+    const int64_t n = A.g.n, total = (int64_t)Q * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t / n);
+        const int64_t u = t - (int64_t)q * n;
+        const float x = load_x(X, (int64_t)q * ldx + u);
+        if (!(x != 0.f) || !isfinite(x)) continue;
+        const int part = x < 0.f ? 1 : 0;
+        const int lane = lane_of[2 * q + part];
+        if (lane < 0) continue;
+        push_to(A.R + (size_t)lane * A.ldR, (int32_t)u, (float)((double)fabsf(x) / norms[2 * q + part]));
     }
 }
 
@@ -1056,7 +1058,8 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
     ws->ldR = ((int64_t)n + kScanUnit - 1) / kScanUnit * kScanUnit;
     const int64_t units = (int64_t)G * (ws->ldR / kScanUnit);
-    ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kNumSMs * 8, units));
+    ws->grid = grid_stride_blocks();
+    ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid, units));
     A(dev_alloc(&ws->R, (size_t)G * ws->ldR, acc));
     A(dev_alloc(&ws->items, ws->cap_items, acc));
     A(dev_alloc(&ws->rval, ws->cap_items, acc));
@@ -1064,7 +1067,7 @@ int create_workspace(agp_graph_s *g, int G, Workspace **out)
     A(dev_alloc(&ws->c_item, ws->cap_items, acc));
     A(dev_alloc(&ws->k_item, ws->cap_items, acc));
     A(dev_alloc(&ws->nrec, ws->cap_items, acc));
-    A(dev_alloc(&ws->rpart, (size_t)3 * kGridStrideBlocks, acc));
+    A(dev_alloc(&ws->rpart, (size_t)3 * ws->grid, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
     A(dev_alloc(&ws->dns_rec, ws->cap_dns, acc));
@@ -1188,6 +1191,7 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.stats = ws->stats;
     A.collect = collect;
     A.G = ws->G;
+    A.grid = ws->grid;
     A.ctrl = ws->ctrl;
     return A;
 }
@@ -1214,9 +1218,9 @@ void launch_compact(const KArgs &A, cudaStream_t s)
 // must run on the same grid: they walk the same item ranges.
 void launch_expand(const KArgs &A, cudaStream_t s)
 {
-    k_expand<<<kGridStrideBlocks, kBlock, 0, s>>>(A);
-    k_rec_scan<<<1, 1024, 0, s>>>(A, kGridStrideBlocks);
-    k_rec_emit<<<kGridStrideBlocks, kBlock, 0, s>>>(A);
+    k_expand<<<A.grid, kBlock, 0, s>>>(A);
+    k_rec_scan<<<1, 1024, 0, s>>>(A, A.grid);
+    k_rec_emit<<<A.grid, kBlock, 0, s>>>(A);
 }
 
 // One level: compact, expand, push, sample, level end. With `ev` (profiling) every step is
@@ -1243,7 +1247,7 @@ void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_bl
 int blocks_for(unsigned long long work, int per_block)
 {
     const unsigned long long b = (work + per_block - 1) / per_block;
-    return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(b, (unsigned long long)kGridStrideBlocks * 4));
+    return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(b, (unsigned long long)grid_stride_blocks() * 4));
 }
 
 // Accumulate the profiled kernel times of levels [0, levels) (the stream has been synchronised).
@@ -1271,7 +1275,7 @@ int capture_levels_ev(const KArgs &A, int levels, Workspace *ws_events, cudaGrap
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int lvl = 0; lvl < levels; ++lvl)
-            launch_level(A, cs, kGridStrideBlocks, kGridStrideBlocks, kGridStrideBlocks,
+            launch_level(A, cs, A.grid, A.grid, A.grid,
                          ws_events ? ws_events->ev[lvl] : nullptr);
         e = cudaStreamEndCapture(cs, &graph);
     }
@@ -1289,11 +1293,6 @@ int capture_levels_ev(const KArgs &A, int levels, Workspace *ws_events, cudaGrap
 
 int capture_levels(const KArgs &A, int levels, cudaGraphExec_t *out) { return capture_levels_ev(A, levels, nullptr, out); }
 
-void launch_coef(const CoefSpec *spec, const double *wts, float2 *coef, int nspec, cudaStream_t s)
-{
-    if (nspec > 0) k_coef<<<(nspec + 127) / 128, 128, 0, s>>>(spec, wts, coef, nspec);
-}
-
 void launch_seed_sources(const KArgs &A, const int32_t *lanes, const int32_t *sources, int count, cudaStream_t s)
 {
     if (count > 0) k_seed_sources<<<blocks_for((unsigned long long)count, kBlock), kBlock, 0, s>>>(A, lanes, sources, count);
@@ -1302,14 +1301,15 @@ void launch_seed_sources(const KArgs &A, const int32_t *lanes, const int32_t *so
 void launch_colnorms_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ldx, double *norms, cudaStream_t s)
 {
     if (n <= 0 || d <= 0) return;
-    const int64_t rows_per_block = std::max<int64_t>(64, (n + kGridStrideBlocks - 1) / kGridStrideBlocks);
+    const int grid = grid_stride_blocks();
+    const int64_t rows_per_block = std::max<int64_t>(64, (n + grid - 1) / grid);
     k_colnorms_bf16<<<(int)((n + rows_per_block - 1) / rows_per_block), kBlock, 0, s>>>(X, n, d, ldx, rows_per_block, norms);
 }
 
 void launch_seed_dense_bf16(const KArgs &A, const uint16_t *X, int64_t ldx, const int32_t *lane_of,
                             const int32_t *col_of, const int32_t *part_of, const double *norms, int nl, cudaStream_t s)
 {
-    if (nl > 0) k_seed_dense_bf16<<<kGridStrideBlocks, kBlock, 0, s>>>(A, X, ldx, lane_of, col_of, part_of, norms, nl);
+    if (nl > 0) k_seed_dense_bf16<<<A.grid, kBlock, 0, s>>>(A, X, ldx, lane_of, col_of, part_of, norms, nl);
 }
 
 // Run the levels of the current wave (lanes already seeded, level 0 frontier in items[cur]).
@@ -1608,8 +1608,10 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     if (!x_off || !pi_out) return fail(AGP_EINVAL, "x_off / pi_out NULL");
     if (ld_out < g->n) return fail(AGP_EINVAL, "ld_out < n");
     if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
-                  AGP_EPS_ABSOLUTE))
+                  AGP_EPS_ABSOLUTE | kOffsetsOnHost))
         return fail(AGP_EINVAL, "unknown flag");
+    // offsets on the device only when the inputs are and the caller did not pass them from the host
+    const bool off_dev = (flags & AGP_INPUT_ON_DEVICE) && !(flags & kOffsetsOnHost);
     if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
     for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
     AGP_CUDA_TRY(cudaSetDevice(g->device));
@@ -1620,7 +1622,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
 
     // --- inputs on the device
     int64_t total = 0;
-    if (flags & AGP_INPUT_ON_DEVICE) {
+    if (off_dev) {
         AGP_CUDA_TRY(cudaMemcpyAsync(&total, x_off + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AGP_CUDA_TRY(cudaStreamSynchronize(s));
     } else {
@@ -1650,6 +1652,10 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     const float *val_src = x_val;
     if (flags & AGP_INPUT_ON_DEVICE) {
         off_src = x_off; idx_src = x_idx; val_src = x_val;
+        if (!off_dev) {
+            AGP_CUDA_TRY(cudaMemcpyAsync(d_off, x_off, off_b, cudaMemcpyHostToDevice, s));
+            off_src = d_off;
+        }
     } else {
         AGP_CUDA_TRY(cudaMemcpyAsync(d_off, x_off, off_b, cudaMemcpyHostToDevice, s));
         if (total) AGP_CUDA_TRY(cudaMemcpyAsync(d_idx, x_idx, sizeof(int32_t) * total, cudaMemcpyHostToDevice, s));
@@ -1671,6 +1677,28 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     AGP_CUDA_TRY(cudaStreamSynchronize(s));
     if (bad) return fail(AGP_EINVAL, "signal index outside [0, n) or non-finite value");
 
+    auto seed = [&](const KArgs &A, const int32_t *d_aux, cudaStream_t st) -> int {
+        k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, st>>>(A, off_src, idx_src, val_src, Q,
+                                                                                       d_aux, d_norm);
+        AGP_CUDA_TRY(cudaGetLastError());
+        return AGP_OK;
+    };
+    return run_queries(g, ctx, params, n_params, Q, norms, seed, pi_out, ld_out, flags, stats, s);
+}
+
+// The lanes of Q queries whose sign-part norms are known (norms[2q + part], host): one lane per
+// non-empty part, waves of lanes, output rows zeroed first and, for host output, copied back as their
+// queries finish. `seed` adds the normalised signal parts of a wave's lanes to their residue vectors
+// (d_aux: lane of part (q, s) at 2q + s, or -1).
+int run_queries(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_t n_params, int32_t Q,
+                const std::vector<double> &norms,
+                const std::function<int(const KArgs &A, const int32_t *d_aux, cudaStream_t st)> &seed,
+                float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s)
+{
+    const bool plain = flags & AGP_PLAIN;
+    const bool profile = flags & AGP_PROFILE;
+    const int collect = (flags & AGP_COLLECT_STATS) ? 1 : 0;
+    const int64_t n = g->n;
     // --- lanes: one per non-empty sign part
     std::vector<LaneSpec> lanes;
     for (int q = 0; q < Q; ++q)
@@ -1696,7 +1724,10 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     job.out = out;
     job.su = 1;
     job.sr = ld;
-    job.stream_base_is_query = 0;  // a query's random stream depends on its seed, not its position
+    // n_params == Q: a query's random stream depends on its own seed, not on its position, so it draws
+    // the same numbers in any batch; n_params == 1: the queries share one seed, and query q draws
+    // from the stream (seed, q), so that they do not repeat one another's draws on common nodes
+    job.stream_base_is_query = (n_params == 1) ? 1 : 0;
     job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.assign(2 * (size_t)Q, -1);
@@ -1704,10 +1735,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     };
     job.seed = [&](const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st) -> int {
         (void)count;
-        k_seed_sparse<<<blocks_for((unsigned long long)total, kBlock), kBlock, 0, st>>>(A, off_src, idx_src, val_src, Q,
-                                                                                       d_aux, d_norm);
-        AGP_CUDA_TRY(cudaGetLastError());
-        return AGP_OK;
+        return seed(A, d_aux, st);
     };
     // host output: the rows of the queries whose lanes have all run are copied after each wave, on
     // that wave's stream, so the copies overlap the next waves (lanes are sorted by query)
@@ -1734,6 +1762,65 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     }
     AGP_CUDA_TRY(cudaGetLastError());
     return AGP_OK;
+}
+
+// ------------------------------------------------------------------------------------ dense signals
+int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q, const void *X, int64_t ldx,
+                float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t s)
+{
+    if (!g) return fail(AGP_EINVAL, "graph is NULL");
+    if (Q < 0) return fail(AGP_EINVAL, "Q < 0");
+    if (Q == 0) return AGP_OK;
+    if (!params || !(n_params == 1 || n_params == Q)) return fail(AGP_EINVAL, "n_params must be 1 or Q");
+    const int64_t n = g->n;
+    if (ldx < n || ld_out < n) return fail(AGP_EINVAL, "ldx and ld_out must be >= n");
+    if (n > 0 && (!X || !pi_out)) return fail(AGP_EINVAL, "X / pi_out NULL");
+    if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
+                  AGP_EPS_ABSOLUTE | AGP_DENSE_BF16))
+        return fail(AGP_EINVAL, "unknown flag");
+    if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
+    for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
+    AGP_CUDA_TRY(cudaSetDevice(g->device));
+    if (n == 0) return AGP_OK;
+    const bool bf16 = flags & AGP_DENSE_BF16;
+    const size_t esz = bf16 ? 2 : 4;
+    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 65535) / 65536));
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const bool host_in = !(flags & AGP_INPUT_ON_DEVICE);
+    const size_t x_b = host_in ? al(esz * (size_t)Q * (size_t)n) : 0;
+    const size_t part_b = al(sizeof(double) * 2 * (size_t)Q * chunks), norm_b = al(sizeof(double) * 2 * Q);
+    ExecCtx ctx{nullptr, &g->in_stage, &g->in_bytes};
+    AGP_TRY(grow(ctx.stage, ctx.stage_bytes, x_b + part_b + norm_b + 256));
+    char *p = (char *)*ctx.stage;
+    const void *Xd = X;
+    int64_t ld = ldx;
+    if (host_in) {  // rows are packed to stride n on the device
+        AGP_CUDA_TRY(cudaMemcpy2DAsync(p, esz * n, X, esz * ldx, esz * n, Q, cudaMemcpyHostToDevice, s));
+        Xd = p;
+        ld = n;
+    }
+    double *d_part = (double *)(p + x_b), *d_norm = (double *)(p + x_b + part_b);
+    unsigned int *d_bad = (unsigned int *)(p + x_b + part_b + norm_b);
+    AGP_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), s));
+    const dim3 grid(chunks, Q);
+    if (bf16) k_rownorm_part<<<grid, kBlock, 0, s>>>((const uint16_t *)Xd, ld, n, chunks, d_part, d_bad);
+    else k_rownorm_part<<<grid, kBlock, 0, s>>>((const float *)Xd, ld, n, chunks, d_part, d_bad);
+    k_rownorm_sum<<<(2 * Q + 127) / 128, 128, 0, s>>>(d_part, chunks, Q, d_norm);
+    __atomic_fetch_add(&g->kernel_launches, (int64_t)2, __ATOMIC_RELAXED);
+    AGP_CUDA_TRY(cudaGetLastError());
+    std::vector<double> norms(2 * Q);
+    unsigned int bad = 0;
+    AGP_CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm, sizeof(double) * 2 * Q, cudaMemcpyDeviceToHost, s));
+    AGP_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    AGP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return fail(AGP_EINVAL, "non-finite value in a dense signal");
+    auto seed = [&](const KArgs &A, const int32_t *d_aux, cudaStream_t st) -> int {
+        if (bf16) k_seed_dense_rows<<<A.grid, kBlock, 0, st>>>(A, (const uint16_t *)Xd, ld, Q, d_aux, d_norm);
+        else k_seed_dense_rows<<<A.grid, kBlock, 0, st>>>(A, (const float *)Xd, ld, Q, d_aux, d_norm);
+        AGP_CUDA_TRY(cudaGetLastError());
+        return AGP_OK;
+    };
+    return run_queries(g, &ctx, params, n_params, Q, norms, seed, pi_out, ld_out, flags, stats, s);
 }
 
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d, int64_t ldx,

@@ -10,7 +10,7 @@
 namespace agp {
 namespace {
 
-constexpr int kPartBlocks = kNumSMs * 4;  // 608 partitions
+constexpr int kPartBlocks = 608;  // partitions (4 per SM on a 152-SM GB300; any count is correct)
 constexpr int kRadix = 256;
 constexpr int kWarps = kBlock / 32;
 

@@ -218,16 +218,39 @@ def test_threshold_bit_exact(agp, rmat14, a):
 
 # ---------------------------------------------------------------- eps > 0: statistics
 STAT_CASES = [
-    # a, b, kind, L, param, eps
-    (0.0, 1.0, oracle.PPR, 10, 0.2, 2e-6),
-    (0.5, 0.5, oracle.PPR, 10, 0.1, 1e-6),
-    (0.0, 0.0, oracle.KATZ, 8, None, 1e-6),
+    # a, b, kind, L, param, eps (sampling active), eps_g (Definition 1.1 at the Chebyshev delta)
+    (0.0, 1.0, oracle.PPR, 10, 0.2, 2e-6, 2e-9),
+    (0.5, 0.5, oracle.PPR, 10, 0.1, 1e-6, 1e-9),
+    (0.0, 0.0, oracle.KATZ, 8, None, 1e-6, 1e-8),
 ]
+
+
+def _runs(agp, g, a, b, kind, L, param, eps, s, N, seed0):
+    params = [_agp_params(agp, a, b, kind, L, param, eps, seed=seed0 + k) for k in range(N)]
+    out, _ = agp.query_sources(g, params, np.full(N, s))
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _soft_measures(runs, exact, eps, L, y0):
+    """Section 8 reading of the eps <-> delta constants, reported (not bounded by the paper): the
+    smallest delta at which every node with pi >= delta has a 99th-percentile relative error <= 0.1
+    over the runs, and the failure rate at the paper's experimental delta = eps L(L+1)/2."""
+    live = exact > 0
+    rel = np.abs(runs[:, live] - exact[live]) / exact[live]
+    p99 = np.percentile(rel, 99, axis=0)
+    order = np.argsort(-exact[live])
+    ok = p99[order] <= 0.1
+    first_bad = int(np.argmin(ok)) if not ok.all() else ok.size
+    delta_soft = float(exact[live][order][first_bad - 1]) if first_bad > 0 else float("inf")
+    d_paper = eps * L * (L + 1) / 2 * y0
+    big = exact[live] >= d_paper
+    fail_paper = float(np.mean(rel[:, big] > 0.1)) if big.any() else float("nan")
+    return delta_soft, d_paper, int(big.sum()), fail_paper
 
 
 @pytest.mark.parametrize("case", STAT_CASES, ids=["ppr", "appnp", "katz"])
 def test_unbiased_variance_guarantee(agp, rmat14, case):
-    a, b, kind, L, param, eps = case
+    a, b, kind, L, param, eps, eps_g = case
     n, u, v = rmat14
     g = agp.build_graph(n, u, v)
     og = oracle.build_csr(n, u, v)
@@ -235,28 +258,35 @@ def test_unbiased_variance_guarantee(agp, rmat14, case):
         param = 0.85 / oracle.power_lambda(og)
     s = int(np.argsort(og.deg)[-200])
     N = 200
-    params = [_agp_params(agp, a, b, kind, L, param, eps, seed=1000 + k) for k in range(N)]
-    out, _ = agp.query_sources(g, params, np.full(N, s))
-    runs = out.cpu().numpy().astype(np.float64)
     w, Y = oracle.tail_sums(kind, L, param)
+    y0 = Y[0]
     x = np.zeros(n); x[s] = 1.0
     exact = oracle.basic(og, a, b, L, w, Y, x)
+    # Lemma 4.1 and Lemma 4.2 where sampling is active
+    runs = _runs(agp, g, a, b, kind, L, param, eps, s, N, 1000)
     mean, var = runs.mean(0), runs.var(0, ddof=1)
     sd = np.sqrt(var / N)
     live = sd > 0
+    assert live.sum() >= 1000  # many entries carry sampled mass
     z = (mean[live] - exact[live]) / sd[live]
     assert np.mean(np.abs(z) > 2.576) <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / max(live.sum(), 1)) + 1e-9
     assert np.abs(z).max() < 6.0
     # Lemma 4.2 (normalised problem: ||x||_1 = 1, pi / Y_0), sampling noise allowance 35%
-    y0 = Y[0]
     bound = L * (L + 1) * eps * (exact / y0) / 2 * y0 * y0
     assert np.all(var <= 1.35 * bound + 1e-24)
-    # Definition 1.1 at delta = 5000 L(L+1) eps (Chebyshev on Lemma 4.2, <= 1% failures)
-    delta = 5000 * L * (L + 1) * eps * y0
+    delta_soft, d_paper, n_paper, fail_paper = _soft_measures(runs, exact, eps, L, y0)
+    print(f"[guarantee] case={kind},{a},{b} eps={eps:g}: 99th-percentile rel err <= 0.1 for every pi >= "
+          f"{delta_soft:.3e}; at the paper's delta={d_paper:.3e} ({n_paper} nodes) failure rate {fail_paper:.4f}")
+    # Definition 1.1 at delta = 5000 L(L+1) eps (Chebyshev on Lemma 4.2: each node fails in <= 1% of
+    # the runs). eps_g is chosen so that at least 50 nodes reach this delta.
+    runs_g = _runs(agp, g, a, b, kind, L, param, eps_g, s, N, 5000)
+    delta = 5000 * L * (L + 1) * eps_g * y0
     big = exact >= delta
-    if big.any():
-        fails = np.mean(np.abs(runs[:, big] - exact[big]) > 0.1 * exact[big], axis=0)
-        assert np.all(fails <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / N))
+    assert big.sum() >= 50, f"only {big.sum()} nodes reach delta = {delta:.3e}"
+    fails = np.mean(np.abs(runs_g[:, big] - exact[big]) > 0.1 * exact[big], axis=0)
+    assert np.all(fails <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / N))
+    print(f"[guarantee] case={kind},{a},{b} eps={eps_g:g}: {int(big.sum())} nodes >= delta={delta:.3e}, "
+          f"worst per-node failure rate {fails.max():.4f}")
 
 
 @pytest.mark.parametrize("p", [0.02, 0.05, 0.3, 0.9])
