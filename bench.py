@@ -167,16 +167,39 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------------- host description
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 # ------------------------------------------------------------------------------- oracle baseline
-def oracle_sample(n, u, v, sources, eps, L=4, threads=None):
+def oracle_sample(og, n, sources, eps, L=4, threads=None):
     """Time the FP64 oracle (Algorithm 2, as it stands) on transition queries in parallel threads."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
-    t0 = time.perf_counter()
-    og = oracle.build_csr(n, u, v)
     w, Y = oracle.tail_sums(oracle.TRANSITION, L)
-    t_csr = time.perf_counter() - t0
-    threads = threads or min(len(sources), os.cpu_count() or 1)
+    threads = threads or min(len(sources), host_cores())
 
     def one(s):
         x = np.zeros(n)
@@ -187,7 +210,7 @@ def oracle_sample(n, u, v, sources, eps, L=4, threads=None):
     with ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(one, [int(s) for s in sources[:threads]]))
     dt = time.perf_counter() - t0
-    return og, threads, dt, t_csr
+    return threads, dt
 
 
 def run_reference(args, wl, rank):
@@ -201,7 +224,7 @@ def run_reference(args, wl, rank):
     from concurrent.futures import ThreadPoolExecutor
     og = oracle.build_csr(n, u, v)
     w, Y = oracle.tail_sums(oracle.TRANSITION, 4)
-    threads = min(os.cpu_count() or 1, 16)
+    threads = host_cores()
 
     def one(s):
         x = np.zeros(n)
@@ -222,8 +245,9 @@ def run_reference(args, wl, rank):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = threads * args.steps / total
-    sample = (f"{threads} of the 256 L=4 transition queries of each step, one per host thread (the oracle "
-              f"runs per-neighbour Bernoulli trials; its eps=1e-8 Katz queries take minutes each and are left out)")
+    sample = (f"{threads} of the 256 L=4 transition queries of each step, one per host thread on all "
+              f"{threads} cores ({cpu_model()}); the oracle runs per-neighbour Bernoulli trials, and its eps=1e-8 "
+              f"Katz queries take minutes each and are left out")
     line = {"impl": "reference", "metric": "queries/s", "value": value, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -231,6 +255,68 @@ def run_reference(args, wl, rank):
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- accuracy
+def accuracy_vs_oracle(og, checks, eps, beta, L_katz, threads):
+    """Relative error of GPU results against the exact FP64 propagation (the oracle's Algorithm 1).
+    checks: list of (kind, source, gpu_row). Reported per query: the fraction of nodes with
+    pi(v) >= delta whose relative error is <= 0.1, at the paper's experimental delta = eps L(L+1)/2
+    (times Y_0) and at the Chebyshev delta 5000 L(L+1) eps Y_0 of Lemma 4.2, and the relative L1
+    error. The oracle runs on the host outside the timed region."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    n = og.n
+    tables = {"katz": (0.0, 0.0, L_katz) + oracle.tail_sums(oracle.KATZ, L_katz, beta),
+              "transition": (0.0, 1.0, 4) + oracle.tail_sums(oracle.TRANSITION, 4)}
+
+    def one(item):
+        kind, s_, row = item
+        a, b, L, w, Y = tables[kind]
+        x = np.zeros(n)
+        x[s_] = 1.0
+        exact = oracle.basic(og, a, b, L, w, Y, x)
+        res = {"kind": kind, "source": int(s_)}
+        rel = np.abs(row.astype(np.float64) - exact) / np.maximum(exact, 1e-300)
+        for name, delta in (("paper", eps * L * (L + 1) / 2 * Y[0]), ("chebyshev", 5000 * L * (L + 1) * eps * Y[0])):
+            big = exact >= delta
+            res[f"delta_{name}"] = float(delta)
+            res[f"nodes_{name}"] = int(big.sum())
+            res[f"frac_ok_{name}"] = float(np.mean(rel[big] <= 0.1)) if big.any() else None
+        res["rel_l1"] = float(np.abs(row - exact).sum() / np.abs(exact).sum())
+        # the smallest delta at which >= 99% of the nodes with pi >= delta have relative error <= 0.1
+        order = np.argsort(-exact)
+        order = order[exact[order] > 0]
+        ok = np.cumsum(rel[order] <= 0.1) / np.arange(1, order.size + 1)
+        good = np.flatnonzero(ok >= 0.99)
+        res["delta_99"] = float(exact[order[good[-1]]]) if good.size else None
+        return res
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=max(1, min(threads, len(checks)))) as ex:
+        per = list(ex.map(one, checks))
+    secs = time.perf_counter() - t0
+    summ = {}
+    for name in ("paper", "chebyshev"):
+        vals = [r[f"frac_ok_{name}"] for r in per if r[f"frac_ok_{name}"] is not None]
+        summ[f"frac_ok_at_delta_{name}"] = {"min": float(min(vals)) if vals else None,
+                                           "mean": float(np.mean(vals)) if vals else None,
+                                           "queries": len(vals)}
+    summ["rel_l1_max"] = float(max(r["rel_l1"] for r in per))
+    for kind in ("katz", "transition"):
+        d99 = [r["delta_99"] for r in per if r["kind"] == kind and r["delta_99"] is not None]
+        summ[f"delta_99_{kind}"] = {"max": float(max(d99)) if d99 else None,
+                                    "median": float(np.median(d99)) if d99 else None}
+    summ["queries_checked"] = len(per)
+    summ["oracle_s"] = secs
+    summ["per_query"] = per
+    return summ
+
+
+def latency_summary(ms):
+    ms = np.asarray(ms, np.float64)
+    return {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "max_ms": float(ms.max()), "queries": int(ms.size)}
 
 
 # ------------------------------------------------------------------------------- multi-rank
@@ -408,9 +494,9 @@ def run_large(args):
     flags = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
     # wave width by timing on the first 32 PPR queries
     qs = min(Q, 32)
-    lanes, tuned_ms = agp.autotune(g, [agp.ppr(0.2, 30, 1e-8, seed=S + q) for q in range(qs)], off[:qs + 1],
+    lanes, width, tuned_ms = agp.autotune(g, [agp.ppr(0.2, 30, 1e-8, seed=S + q) for q in range(qs)], off[:qs + 1],
                                    d_srcs[:qs], None, out, n, candidates=[1, 2, 4, 8, 16])
-    log(f"[large] autotuned wave width {lanes} lanes")
+    log(f"[large] autotuned wave width {lanes} lanes, group width {width}")
     res = {}
     for name, mk, mass in (("ppr", lambda sd: agp.ppr(0.2, 30, 1e-8, seed=sd), w_ppr),
                            ("hkpr", lambda sd: agp.hkpr(5.0, 30, 1e-8, seed=sd), w_hk)):
@@ -452,7 +538,8 @@ def run_large(args):
     line = {"metric": "queries/s", "value": 2 * Q / ((res["ppr"]["ms_per_launch"] + res["hkpr"]["ms_per_launch"]) / 1e3),
             "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"chung-lu-2.0 n={n} m={m} ppr(0.2)+hkpr(5), L=30, eps=1e-8, {Q} uniform sources per launch",
-                       "generate_s": t_gen, "build_s": t_build, "wave_lanes": lanes, "autotune_ms": tuned_ms},
+                       "generate_s": t_gen, "build_s": t_build, "wave_lanes": lanes, "group_width": width,
+                       "autotune_ms": tuned_ms},
             "checks": checks, "models": res,
             "note": "a = 0, b = 1 keeps mass: E[sum pi] = sum_{i<=L} w_i for every source with degree >= 1"}
     print(json.dumps(line), flush=True)
@@ -578,9 +665,11 @@ def main():
     ap.add_argument("--impl", default="agp", choices=["agp", "reference"])
     ap.add_argument("--small", action="store_true", help="small R-MAT workload (quick check)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain-queries", type=int, default=16)
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle check of timed queries")
+    ap.add_argument("--plain-queries", type=int, default=64)
     ap.add_argument("--queries", type=int, default=0, help="sources per launch (default: the workload's 256)")
-    ap.add_argument("--lanes", type=int, default=0, help="wave width; 0 = autotune")
+    ap.add_argument("--lanes", type=int, default=0, help="wave width; 0 = autotune (with the group width)")
+    ap.add_argument("--width", type=int, default=0, help="group width with --lanes (1, 2, 4; 0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving trace instead of the batched step")
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -596,8 +685,19 @@ def main():
     wl = workload(args.small)
     if args.queries:
         wl["Q"] = args.queries
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # N GPUs asked for outside torchrun: launch the N ranks here (one process per GPU)
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus and rank == 0:
+        log(f"[bench] --gpus {args.gpus} but WORLD_SIZE {world}: running {world} rank(s)")
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, wl, rank)
@@ -658,20 +758,27 @@ def main():
         st = agp.query_batch(g, pt, off, d_srcs[base + Q:base + 2 * Q], None, out_t, n, f)
         return sk, st
 
+    # accuracy sample: 4 Katz and 4 transition queries of each of the first two timed steps, their
+    # rows copied to the host after the step (outside the timed region), checked against the oracle
+    acc_steps = min(2, args.steps) if not args.no_accuracy else 0
+    acc_rows = []
+
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     # wave width: given, or tuned on a sample of the first step's Katz launch (cached)
     tuned_ms = None
+    width = args.width
     if args.lanes > 0:
         g.set_wave_lanes(args.lanes)
+        g.set_group_width(args.width)
         lanes = args.lanes
     else:
         qs = min(Q, 32)
         pk, _ = all_params[0]
         t0 = time.perf_counter()
-        lanes, tuned_ms = agp.autotune(g, pk[:qs], off[:qs + 1], d_srcs[:qs], None, out_k, n,
+        lanes, width, tuned_ms = agp.autotune(g, pk[:qs], off[:qs + 1], d_srcs[:qs], None, out_k, n,
                                        candidates=[c for c in (1, 2, 4, 8, 16, 32) if c <= 2 * qs])
-        log(f"[bench] autotuned wave width {lanes} lanes ({tuned_ms:.1f} ms for {qs} Katz queries, "
+        log(f"[bench] autotuned wave width {lanes} lanes, group width {width} ({tuned_ms:.1f} ms for {qs} Katz queries, "
             f"{time.perf_counter() - t0:.1f}s)")
 
     for k in range(args.warmup):
@@ -680,6 +787,7 @@ def main():
     agp.profile_read(g, reset=True)
     stream = torch.cuda.current_stream()
     step_ms = []
+    lat_k, lat_t = [], []
     with ClockSampler(local) as clocks:
         barrier_sync()
         for k in range(args.steps):
@@ -687,10 +795,18 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            run_step(args.warmup + k, agp.PROFILE)
+            sk, st = run_step(args.warmup + k, agp.PROFILE | agp.QUERY_TIMES)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
+            lat_k += [x.done_ms for x in sk]
+            lat_t += [x.done_ms for x in st]
+            if k < acc_steps:
+                base = (args.warmup + k) * 2 * Q
+                for j in range(4):
+                    q = j * (Q // 4)
+                    acc_rows.append(("katz", int(srcs[base + q]), out_k[q].cpu().numpy()))
+                    acc_rows.append(("transition", int(srcs[base + Q + q]), out_t[q].cpu().numpy()))
         barrier_sync()
     clk = clocks.summary()
     kern_ms, kern_launches, total_launches = agp.profile_read(g, reset=True)
@@ -738,44 +854,69 @@ def main():
                    "note": "push time from CUDA events around every k_push of the timed steps, which "
                            "include the other wave's kernels sharing the GPU (an upper bound on its time)"}
 
-    # ---- plain path: one query per launch sequence, host-synchronised frontier sizes
+    # ---- plain path: one query per launch sequence, host-synchronised frontier sizes. The same
+    # queries run on both paths after a warm-up of each; a query's latency is its completion time
+    # from the start of its launch (one CUDA event per wave), and throughput is queries over the
+    # host wall time of both launches.
     plain_qps = None
     if args.plain_queries > 0 and rank == 0:
         k = args.warmup
         pk, pt = all_params[k]
         base = k * 2 * Q
-        half = args.plain_queries // 2
-        pf = flags | agp.PLAIN
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        agp.query_batch(g, pk[:half], off[:half + 1], d_srcs[base:base + half], None, out_k, n, pf)
-        agp.query_batch(g, pt[:half], off[:half + 1], d_srcs[base + Q:base + Q + half], None, out_t, n, pf)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        # the batched path on exactly the same queries, for a like-for-like ratio
-        t0 = time.perf_counter()
-        agp.query_batch(g, pk[:half], off[:half + 1], d_srcs[base:base + half], None, out_k, n, flags)
-        agp.query_batch(g, pt[:half], off[:half + 1], d_srcs[base + Q:base + Q + half], None, out_t, n, flags)
-        torch.cuda.synchronize()
-        dtb = time.perf_counter() - t0
-        plain_qps = {"plain_queries_per_s": 2 * half / dt, "batched_same_queries_per_s": 2 * half / dtb,
-                     "queries": 2 * half}
+        half = min(args.plain_queries // 2, Q)
+
+        def both(fl):
+            a_ = agp.query_batch(g, pk[:half], off[:half + 1], d_srcs[base:base + half], None, out_k, n,
+                                 fl | agp.QUERY_TIMES)
+            b_ = agp.query_batch(g, pt[:half], off[:half + 1], d_srcs[base + Q:base + Q + half], None, out_t, n,
+                                 fl | agp.QUERY_TIMES)
+            return [x.done_ms for x in a_] + [x.done_ms for x in b_]
+
+        res = {}
+        for name, fl in (("plain", flags | agp.PLAIN), ("batched", flags)):
+            both(fl)  # warm-up (captured graphs, workspaces)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat = both(fl)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            res[name] = {"queries_per_s": 2 * half / dt, **latency_summary(lat)}
+        plain_qps = {"queries": 2 * half, "plain": res["plain"], "batched": res["batched"],
+                     "speedup_queries_per_s": res["batched"]["queries_per_s"] / res["plain"]["queries_per_s"],
+                     "note": "same Katz + transition queries on both paths, each after one untimed run"}
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e_value, h2d, d2h = None, 0, 0
     if not args.no_e2e:
         e2e_value, h2d, d2h = end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev)
 
+    # ---- the oracle's CSR (host), for the accuracy check and the CPU baseline
+    og, t_csr = None, 0.0
+    need_oracle = rank == 0 and (acc_rows or (not args.no_cpu_baseline and world == 1))
+    if need_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        og = oracle.build_csr(n, u, v)
+        t_csr = time.perf_counter() - t0
+
+    # ---- accuracy of the timed queries against the exact FP64 propagation
+    accuracy = None
+    if acc_rows and rank == 0:
+        accuracy = accuracy_vs_oracle(og, acc_rows, eps, beta, wl["L_katz"], host_cores())
+        log(f"[bench] accuracy vs oracle: {json.dumps({k_: v_ for k_, v_ in accuracy.items() if k_ != 'per_query'})}")
+
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         base = args.warmup * 2 * Q + Q
-        threads = min(os.cpu_count() or 1, 16)
-        _, used, dt, t_csr = oracle_sample(n, u, v, srcs[base:base + threads], eps, 4, threads)
-        cpu = {"value": used / dt, "unit": "queries/s", "cores": used, "kind": "oracle",
-               "sample": f"{used} of the 256 L=4 transition queries of one step, one per host thread, FP64 "
-                         f"Algorithm 2 with per-neighbour Bernoulli trials ({dt:.1f}s; CSR build {t_csr:.1f}s "
-                         f"excluded; Katz queries at eps=1e-8 take minutes each in the oracle and are left out)"}
+        threads = host_cores()
+        used, dt = oracle_sample(og, n, srcs[base:base + threads], eps, 4, threads)
+        cpu = {"value": used / dt, "unit": "queries/s", "cores": used, "nproc": host_cores(), "cpu_model": cpu_model(),
+               "kind": "oracle",
+               "sample": f"{used} of the 256 L=4 transition queries of one step, one per host thread on all "
+                         f"{used} cores, FP64 Algorithm 2 with per-neighbour Bernoulli trials ({dt:.1f}s; CSR build "
+                         f"{t_csr:.1f}s excluded; Katz queries at eps=1e-8 take minutes each in the oracle and are "
+                         f"left out)"}
 
     if rank == 0:
         line = {
@@ -783,11 +924,15 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "parallelism": f"replicas{world}", "queries_per_step": 2 * Q,
-                       "wave_lanes": lanes, "autotune_ms": tuned_ms,
+                       "wave_lanes": lanes, "group_width": width, "autotune_ms": tuned_ms,
                        "lambda_1": lam, "beta": beta,
                        "l2": "flushed before every timed step (256 MB write); CSR 0.96 GB and 8 GB of residues exceed L2"},
-            "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)), "p99_step": float(np.percentile(step_ms, 99)),
-                           "note": "a query's latency is its launch's completion time"},
+            "latency_ms": {"per_query": latency_summary(lat_k + lat_t), "katz": latency_summary(lat_k),
+                           "transition": latency_summary(lat_t),
+                           "p50_step": float(np.percentile(step_ms, 50)), "p99_step": float(np.percentile(step_ms, 99)),
+                           "note": "a query's latency is the end of the wave that finished it, from the start of its "
+                                   "launch (CUDA events, timed steps)"},
+            "accuracy": accuracy,
             "edges_pushed_per_s": rank_reduce(edge_ops, "sum", world, dev) / (total_ms / 1e3),
             "work_per_step": {"frontier_items": items / args.steps,
                               "deterministic_pushes": float(work[:, 0].sum()) / args.steps,

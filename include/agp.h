@@ -108,6 +108,13 @@ AGP_API int agp_graph_set_memory_budget(agp_graph_t g, int64_t bytes);
  * as many as keep their residue vectors within ~96 MB of L2. agp_autotune picks it by timing. */
 AGP_API int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes);
 
+/* Lanes per residue group: 1, 2 or 4 (0 = automatic: 4 when the wave width is a multiple of 4,
+ * else 2 when it is even, else 1). The residues of a group's lanes are interleaved per node, so a
+ * frontier node's row is walked once for all lanes of the group that hold it, and their increments
+ * at a neighbour leave as one vector reduction. Results do not depend on it (a lane's random draws
+ * are its own). The plain path always uses 1. agp_autotune picks it by timing. */
+AGP_API int agp_graph_set_group_width(agp_graph_t g, int32_t width);
+
 /* ---- propagation parameters ---------------------------------------------------------------- */
 /* Weight sequences of Table 1. FINITE takes w_0..w_L from `w`; the others are generated with
  * their infinite tails Y_i = sum_{k>=i} w_k (Def. 3.1):
@@ -144,7 +151,9 @@ typedef struct {
      * appends]                                                                                   */
     int64_t by_kernel[3][4];
     int32_t levels;                   /* L + 1 entries of `frontier` are meaningful              */
-    int32_t reserved;
+    float done_ms;                    /* AGP_QUERY_TIMES: device time from the start of the call's
+                                         first wave to the end of the wave that finished this query
+                                         (CUDA events); 0 otherwise                              */
 } agp_stats_t;
 
 /* Memory-location flags of the query entry points. */
@@ -157,6 +166,8 @@ typedef struct {
 #define AGP_PROFILE 0x10u         /* record CUDA events around every kernel of the level loop
                                      (inside the captured graph as well); read the per-kernel
                                      device time with agp_profile_read                          */
+#define AGP_QUERY_TIMES 0x80u     /* fill stats[q].done_ms: one CUDA event per wave (no counter
+                                     atomics); needs stats                                      */
 #define AGP_EPS_ABSOLUTE 0x20u    /* eps is in the raw units of the signal: a sign part x+- runs
                                      with eps / ||x+-||_1 on its normalised residues. Default
                                      (flag clear): eps applies to the normalised residues, the
@@ -177,7 +188,8 @@ typedef struct {
  *   x_off     Q+1 int64 offsets; x_idx / x_val as above; host or device (AGP_INPUT_ON_DEVICE)
  *   pi_out    Q rows of ld_out >= n floats, row q = estimate of pi for query q (dense FP32);
  *             host or device (AGP_OUTPUT_ON_DEVICE). Every entry of each row [0, n) is written.
- *   stats     NULL or Q entries (host memory; needs AGP_COLLECT_STATS)
+ *   stats     NULL or Q entries (host memory): counters with AGP_COLLECT_STATS, completion times
+ *             with AGP_QUERY_TIMES (either flag needs stats)
  * The call synchronises `stream` when pi_out or stats are host memory.
  * Errors: AGP_EINVAL (parameter out of range, index out of range when inputs are on the host),
  * AGP_ENOMEM / AGP_EBUDGET (work buffers), AGP_ECUDA, AGP_EINTERNAL (device-side check).
@@ -202,7 +214,7 @@ AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, 
  *            copied to the graph's device staging first.
  *   pi_out   Q rows of ld_out >= n floats; host or device (AGP_OUTPUT_ON_DEVICE)
  *   flags    AGP_INPUT_ON_DEVICE, AGP_OUTPUT_ON_DEVICE, AGP_PLAIN, AGP_COLLECT_STATS, AGP_PROFILE,
- *            AGP_EPS_ABSOLUTE, AGP_DENSE_BF16
+ *            AGP_QUERY_TIMES, AGP_EPS_ABSOLUTE, AGP_DENSE_BF16
  * The call synchronises `stream` once after the norms, and at the end when pi_out or stats are host
  * memory. Errors as agp_query_batch (a non-finite entry of X: AGP_EINVAL).
  */
@@ -315,17 +327,19 @@ AGP_API int agp_serve_stats(agp_server_t s, int64_t *completed, int64_t *sweeps,
 AGP_API int agp_serve_destroy(agp_server_t s);
 
 /*
- * Autotuner of the wave width: runs the given batch (arguments as agp_query_batch, output on the
- * device) once per candidate lane count in `candidates` (n_candidates > 0; NULL = powers of two up
- * to the batch's lane count), times each second run with CUDA events, keeps the fastest on the
- * graph (agp_graph_set_wave_lanes) and returns it. With the environment variable AGP_TUNE_CACHE
- * naming a file, results are cached there, keyed by graph size and parameter signature, and a
- * cached entry is used without timing. best_lanes / best_ms: host pointers (may be NULL).
+ * Autotuner of the wave width and the group width: runs the given batch (arguments as
+ * agp_query_batch, output on the device) once per candidate pair (lanes from `candidates`,
+ * n_candidates > 0, NULL = powers of two up to the batch's lane count; group width 1, 2 or 4
+ * dividing the lanes), times each second run with CUDA events, keeps the fastest pair on the graph
+ * (agp_graph_set_wave_lanes, agp_graph_set_group_width) and returns it. With the environment
+ * variable AGP_TUNE_CACHE naming a file, results are cached there, keyed by graph size and parameter
+ * signature, and a cached entry is used without timing. best_lanes / best_width / best_ms: host
+ * pointers (may be NULL; best_ms = -1 for a cached entry).
  */
 AGP_API int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q,
                          const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
                          int64_t ld_out, uint32_t flags, const int32_t *candidates, int32_t n_candidates,
-                         int32_t *best_lanes, double *best_ms, void *stream);
+                         int32_t *best_lanes, int32_t *best_width, double *best_ms, void *stream);
 
 /*
  * Kernel accounting of a graph handle since the last reset.

@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
-    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "QUERY_TIMES", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
     "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "MAX_LEVELS",
@@ -28,7 +28,7 @@ __all__ = [
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
-DENSE_BF16 = 0x40
+DENSE_BF16, QUERY_TIMES = 0x40, 0x80
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
 ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED = 0x1, 0x2, 0x4
 MAX_LEVELS = 64
@@ -52,7 +52,7 @@ class Stats(C.Structure):
     """``agp_stats_t``: per-query frontier sizes and cost counters."""
     _fields_ = [("frontier", C.c_int64 * MAX_LEVELS), ("det_edge_ops", C.c_int64),
                 ("samples_drawn", C.c_int64), ("samples_accepted", C.c_int64),
-                ("by_kernel", (C.c_int64 * 4) * 3), ("levels", C.c_int32), ("reserved", C.c_int32)]
+                ("by_kernel", (C.c_int64 * 4) * 3), ("levels", C.c_int32), ("done_ms", C.c_float)]
 
     def as_dict(self):
         return {"frontier": list(self.frontier)[: self.levels], "det_edge_ops": self.det_edge_ops,
@@ -118,7 +118,8 @@ def lib():
             L.agp_katz_lambda_noalloc.argtypes = [_i64, _vp, _vp, _i32, _dbl, C.POINTER(_dbl), _vp]
             L.agp_katz_lambda_noalloc.restype = C.c_int
             L.agp_autotune.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _i32,
-                                       C.POINTER(_i32), C.POINTER(_dbl), _vp]
+                                       C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_dbl), _vp]
+            L.agp_graph_set_group_width.argtypes = [_vp, _i32]
             L.agp_serve_create.argtypes = [_vp, C.POINTER(ServeConfig), C.POINTER(_vp)]
             L.agp_serve_submit.argtypes = [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
             L.agp_serve_poll.argtypes = [_vp, C.c_uint64, C.POINTER(Result)]
@@ -132,7 +133,8 @@ def lib():
                 getattr(L, f).restype = C.c_int
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
-                      "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense"):
+                      "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense",
+                      "agp_graph_set_group_width"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -230,6 +232,10 @@ class Graph:
         """``agp_graph_set_wave_lanes`` (0 = automatic)."""
         _check("agp_graph_set_wave_lanes", lib().agp_graph_set_wave_lanes(self.handle, int(lanes)))
 
+    def set_group_width(self, width):
+        """``agp_graph_set_group_width`` (0 = automatic; 1, 2 or 4)."""
+        _check("agp_graph_set_group_width", lib().agp_graph_set_group_width(self.handle, int(width)))
+
     def set_memory_budget(self, nbytes):
         _check("agp_graph_set_memory_budget", lib().agp_graph_set_memory_budget(self.handle, int(nbytes)))
 
@@ -291,7 +297,7 @@ def query_batch(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=0, stats
     """``agp_query_batch`` with raw arrays (numpy = host, torch CUDA = device)."""
     Q = int(x_off.shape[0]) - 1
     parr, np_, keep = _params_array(params, Q)
-    st = (Stats * Q)() if (flags & COLLECT_STATS) and stats is None else stats
+    st = (Stats * Q)() if (flags & (COLLECT_STATS | QUERY_TIMES)) and stats is None else stats
     ld = int(ld_out if ld_out is not None else g.n)
     _check("agp_query_batch", lib().agp_query_batch(g.handle, parr, np_, Q, _ptr(x_off), _ptr(x_idx), _ptr(x_val),
                                                      _ptr(out), ld, int(flags), st, _stream(stream)))
@@ -316,7 +322,7 @@ def query_dense(g, params, X, out=None, flags=0, stats=None, stream=None):
     if torch.is_tensor(out) and out.is_cuda:
         fl |= OUTPUT_ON_DEVICE
     parr, np_, keep = _params_array(params, Q)
-    st = (Stats * Q)() if (fl & COLLECT_STATS) and stats is None else stats
+    st = (Stats * Q)() if (fl & (COLLECT_STATS | QUERY_TIMES)) and stats is None else stats
     _check("agp_query_dense", lib().agp_query_dense(g.handle, parr, np_, Q, _ptr(X), ldx, _ptr(out), ld, fl, st,
                                                      _stream(stream)))
     return out, st
@@ -324,16 +330,16 @@ def query_dense(g, params, X, out=None, flags=0, stats=None, stream=None):
 
 def autotune(g, params, x_off, x_idx, x_val, out, ld_out=None, flags=INPUT_ON_DEVICE | OUTPUT_ON_DEVICE,
              candidates=None, stream=None):
-    """``agp_autotune``: returns (best lanes, best ms or -1 when taken from the cache)."""
+    """``agp_autotune``: returns (best lanes, best group width, best ms or -1 when taken from the cache)."""
     Q = int(x_off.shape[0]) - 1
     parr, np_, keep = _params_array(params, Q)
     cand = None if candidates is None else (C.c_int32 * len(candidates))(*candidates)
-    best, ms = _i32(), _dbl()
+    best, width, ms = _i32(), _i32(), _dbl()
     _check("agp_autotune", lib().agp_autotune(g.handle, parr, np_, Q, _ptr(x_off), _ptr(x_idx), _ptr(x_val), _ptr(out),
                                                int(ld_out if ld_out is not None else g.n), int(flags), cand,
-                                               0 if candidates is None else len(candidates), C.byref(best), C.byref(ms),
-                                               _stream(stream)))
-    return best.value, ms.value
+                                               0 if candidates is None else len(candidates), C.byref(best),
+                                               C.byref(width), C.byref(ms), _stream(stream)))
+    return best.value, width.value, ms.value
 
 
 class Server:

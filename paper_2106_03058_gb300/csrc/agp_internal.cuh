@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/agp.h"
 
@@ -103,8 +104,10 @@ struct agp_graph_s {
     int32_t *deg = nullptr;
     int64_t mem_budget = 0;        // 0 = default
     int32_t wave_lanes = 0;        // lanes in flight per wave, 0 = automatic (L2 residency)
+    int32_t group_width = 0;       // lanes per residue group (1, 2, 4), 0 = automatic
     agp::Workspace *ws = nullptr;
     agp::Workspace *ws2 = nullptr; // second workspace: two waves in flight on two streams
+    agp::Workspace *ws_plain = nullptr;  // one-lane workspace of the plain path
     cudaStream_t side = nullptr;   // stream of the second wave slot
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_wave[2] = {nullptr, nullptr};  // end of the last wave on stream k (result copies)
@@ -113,6 +116,7 @@ struct agp_graph_s {
     double prof_ms[5] = {0, 0, 0, 0, 0};   // AGP_PROFILE: device time per level-loop step
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     int64_t kernel_launches = 0;           // all kernels launched for this graph
+    std::vector<cudaEvent_t> wave_ev;      // AGP_QUERY_TIMES: call start + one event per wave
     agp::DevGraph dev() const { return agp::DevGraph{n, nnz, rowptr, colidx, deg}; }
 };
 
@@ -131,8 +135,8 @@ int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t
 int wave_lanes(const agp_graph_s *g);
 int autotune(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
              const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
-             const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, double *best_ms,
-             cudaStream_t s);
+             const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, int32_t *best_width,
+             double *best_ms, cudaStream_t s);
 int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q,
                 const int64_t *x_off, const int32_t *x_idx, const float *x_val, float *pi_out,
                 int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);

@@ -248,11 +248,13 @@ int agp_graph_destroy(agp_graph_t g)
     cudaDeviceSynchronize();
     agp::free_workspace(g->ws);
     agp::free_workspace(g->ws2);
+    agp::free_workspace(g->ws_plain);
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
     for (int k = 0; k < 2; ++k)
         if (g->ev_wave[k]) cudaEventDestroy(g->ev_wave[k]);
+    for (cudaEvent_t e : g->wave_ev) cudaEventDestroy(e);
     cudaFree(g->rowptr);
     cudaFree(g->colidx);
     cudaFree(g->deg);
@@ -279,10 +281,19 @@ int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes)
 
 int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,
                  const int32_t *x_idx, const float *x_val, float *pi_out, int64_t ld_out, uint32_t flags,
-                 const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, double *best_ms, void *stream)
+                 const int32_t *candidates, int32_t n_candidates, int32_t *best_lanes, int32_t *best_width,
+                 double *best_ms, void *stream)
 {
     return agp::autotune(g, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, candidates, n_candidates,
-                         best_lanes, best_ms, (cudaStream_t)stream);
+                         best_lanes, best_width, best_ms, (cudaStream_t)stream);
+}
+
+int agp_graph_set_group_width(agp_graph_t g, int32_t width)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (width != 0 && width != 1 && width != 2 && width != 4) return agp::fail(AGP_EINVAL, "group width must be 0, 1, 2 or 4");
+    g->group_width = width;
+    return AGP_OK;
 }
 
 int agp_query_batch(agp_graph_t g, const agp_params_t *params, int32_t n_params, int32_t Q, const int64_t *x_off,

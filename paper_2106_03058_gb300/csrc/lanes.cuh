@@ -76,7 +76,7 @@ struct LaneStats {
 
 struct Ctrl {
     unsigned long long n_items;  // frontier size of the current level (set by the compaction)
-    unsigned long long n_det, n_smp, n_dns;
+    unsigned long long n_det, n_smp;  // walk-chunk and segment records of the current level
     unsigned int error;          // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 16: bad level
     unsigned int lanes_used;     // lanes [0, lanes_used) hold work; the compaction scans only those
 };
@@ -84,25 +84,34 @@ struct Ctrl {
 constexpr int kProfKernels = 5;  // compact, expand, push, sample, level end
 constexpr int kKernelsPerLevel = 9;  // compaction 3, expansion 3 (expand, record scan, record emit),
                                      // push, sample, level end
-constexpr int kScanUnit = 1024;  // floats of a lane's residue vector scanned by one CTA step (256 x float4)
+constexpr int kScanUnit = 1024;  // floats of a group's residue block scanned by one CTA step (256 x float4)
+constexpr int kMaxGroupWidth = 4;  // lanes per group: a node's residues of a group fill one float4
 
+// Residue layout: lanes are taken W at a time (W = 1, 2 or 4: the workspace's group width) into
+// groups; group g owns the block R[g][ldR][W] (node-major, the W lanes of a node contiguous), so one
+// frontier item is one (group, node) with W residues, its row is walked once for all W lanes, and
+// the lanes' increments at a neighbour leave as one vector reduction.
 struct KArgs {
     DevGraph g;
     int ubits;
     uint32_t umask;
-    float *R;                 // [G][ldR]
-    uint32_t *items;          // current frontier, ascending (lane << ubits | u)
-    float *rval;              // r^(i)(u) of each frontier item
-    int64_t ldR;              // lane stride of R (n rounded up to kScanUnit floats)
-    int64_t units;            // kScanUnit-float units per lane
+    int W;                    // lanes per group
+    float *R;                 // [G / W][ldR][W]
+    uint32_t *items;          // current frontier, ascending (group << ubits | u)
+    float *rval;              // [item][W]: r^(i)(u) of the group's lanes
+    int64_t ldR;              // nodes per group block (n rounded up to kScanUnit / W)
+    int64_t units;            // kScanUnit-float units per group block
     int64_t *part;            // per-range counts / offsets of the compaction
     int part_blocks;          // compaction ranges (blocks)
-    float *c_item;
-    int2 *k_item;             // (prefix length, tail segment length)
-    uint2 *nrec;              // per item: (prefix chunks, tail records | dense bit)
-    unsigned long long *rpart;  // [3][grid] per-block record counts / offsets
-    uint2 *det_rec, *smp_rec, *dns_rec;
-    unsigned long long cap_items, cap_det, cap_smp, cap_dns;
+    float *c_item;            // [item][W] c = (Y_{i+1}/Y_i) r / d_u^b per lane (records only)
+    int32_t *k_item;          // [item][W] deterministic prefix length per lane
+    int32_t *seg_item;        // [item][W] sparse-tail segment length per lane
+    uint32_t *flag_item;      // [item] bit j: lane j's tail is dense (per-position trials in the walk);
+                              // bit 8 + j: lane j is in the walk; bit 16 + j: lane j has segments
+    uint2 *nrec;              // per item: (walk chunks, sparse-tail segments)
+    unsigned long long *rpart;  // [2][grid] per-block record counts / offsets
+    uint2 *det_rec, *smp_rec;   // walk-chunk records (item, chunk), segment records (item, segment)
+    unsigned long long cap_items, cap_det, cap_smp;
     const LaneParam *lanes;
     const float2 *coef;       // [G][kMaxLevels] (keep_i = scale * w_i/Y_i, push_i = Y_{i+1}/Y_i)
     int32_t *level;           // [G], -1 = idle
@@ -116,9 +125,10 @@ struct KArgs {
 struct Workspace {
     int device = 0;
     int G = 0;
-    int grid = 0;                      // grid-stride blocks of the device (rpart holds 3 rows of it)
+    int W = 1;                         // lanes per group (G is a multiple of W)
+    int grid = 0;                      // grid-stride blocks of the device (rpart holds 2 rows of it)
     int64_t n = 0;
-    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0, cap_dns = 0;
+    unsigned long long cap_items = 0, cap_det = 0, cap_smp = 0;
     float *R = nullptr;
     uint32_t *items = nullptr;
     float *rval = nullptr;
@@ -126,10 +136,12 @@ struct Workspace {
     int64_t *part = nullptr;
     int part_blocks = 1;
     float *c_item = nullptr;
-    int2 *k_item = nullptr;
+    int32_t *k_item = nullptr;
+    int32_t *seg_item = nullptr;
+    uint32_t *flag_item = nullptr;
     uint2 *nrec = nullptr;
     unsigned long long *rpart = nullptr;
-    uint2 *det_rec = nullptr, *smp_rec = nullptr, *dns_rec = nullptr;
+    uint2 *det_rec = nullptr, *smp_rec = nullptr;
     LaneParam *lanes = nullptr;
     float2 *coef = nullptr;
     int32_t *level = nullptr;
@@ -190,7 +202,9 @@ int validate_params_for(const agp_graph_s *g, const agp_params_t &p);
 void lane_key(uint64_t seed, uint64_t stream, int part, uint32_t &k0, uint32_t &k1);
 size_t bytes_per_lane(const agp_graph_s *g);
 int lane_capacity(const agp_graph_s *g);
-int create_workspace(agp_graph_s *g, int G, Workspace **out);
+// Group width of a wave of G lanes: 4 when G is a multiple of 4, else 2 when even, else 1.
+inline int group_width(int G) { return (G % 4 == 0) ? 4 : (G % 2 == 0) ? 2 : 1; }
+int create_workspace(agp_graph_s *g, int G, int W, Workspace **out);
 KArgs make_args(agp_graph_s *g, Workspace *ws, int collect);
 int blocks_for(unsigned long long work, int per_block);
 void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,

@@ -43,17 +43,6 @@ namespace cg = cooperative_groups;
 namespace agp {
 
 // ------------------------------------------------------------------------------------ helpers
-__device__ __forceinline__ float deg_pow_neg_f(int32_t d, int mode, float p)
-{
-    // d^-p in FP32 for d >= 1
-    switch (mode) {
-    case 0: return 1.f;
-    case 1: return __frcp_rn((float)d);
-    case 2: return __frcp_rn(__fsqrt_rn((float)d));
-    default: return powf((float)d, -p);
-    }
-}
-
 __device__ __forceinline__ float apply_deg(float c, int32_t d, int mode, float p)
 {
     // c / d^p in FP32
@@ -114,20 +103,59 @@ __device__ __forceinline__ int32_t ld_col(const int32_t *p)
     return v;
 }
 
-// Pushes are fire-and-forget atomic adds (no value returned, so no thread waits on them). The next
-// frontier is not tracked during the pushes: each level starts by scanning the residue vectors of
-// the active lanes (see k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
-// Fire-and-forget FP32 add into global memory. Written as red.global explicitly: for a pointer
-// loaded from memory (an output row of the lane parameters) the compiler cannot prove the global
-// space and would issue a returning generic atomic, which the warp waits for.
+// Pushes are fire-and-forget reductions (no value returned, so no thread waits on them), written
+// as red.global explicitly: for a pointer loaded from memory (an output row of the lane parameters)
+// the compiler cannot prove the global space and would issue a returning generic atomic. The next
+// frontier is not tracked during the pushes: each level starts by scanning the residue vectors (see
+// k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
 __device__ __forceinline__ void red_add(float *p, float v)
 {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
 }
 
-__device__ __forceinline__ void push_to(float *Rn, int32_t v, float inc)
+// The W residues of one node are contiguous and W-float aligned (vectors start 4 KB-aligned), so the
+// increments of several lanes at one neighbour go out as one vector reduction.
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b)
 {
-    if (inc != 0.f) red_add(Rn + v, inc);
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void push_to(float *p, float inc)
+{
+    if (inc != 0.f) red_add(p, inc);
+}
+
+// Increments inc[0..W) of the W lanes of a group at neighbour v (Rg: the group's residue block). One
+// non-zero lane takes a scalar reduction, several a vector one.
+template <int W>
+__device__ __forceinline__ void push_node(float *Rg, int32_t v, const float (&inc)[W])
+{
+    float *p = Rg + (size_t)v * W;
+    if constexpr (W == 1) {
+        push_to(p, inc[0]);
+    } else {
+        int nz = 0, last = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (inc[j] != 0.f) {
+                ++nz;
+                last = j;
+            }
+        if (nz == 1) {
+            red_add(p + last, inc[last]);
+        } else if (nz > 1) {
+            if constexpr (W == 2) red_add_v2(p, inc[0], inc[1]);
+            else red_add_v4(p, inc[0], inc[1], inc[2], inc[3]);
+        }
+    }
 }
 
 struct Uniforms {
@@ -148,9 +176,10 @@ struct Uniforms {
     }
 };
 
-// Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane.
-template <int kSampleBatch>
-__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int32_t u, int lvl, uint32_t seg,
+// Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane. Rs is
+// the lane's residue at node 0 (group block + slot); node v's residue is Rs[v * W].
+template <int kSampleBatch, int W>
+__device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rs, int32_t u, int lvl, uint32_t seg,
                              const int32_t *row, int j0, int j1, float c, unsigned long long &drawn,
                              unsigned long long &accepted)
 {
@@ -214,39 +243,162 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rn, int3
                 if (P.a_mode != 0) keep = acc[t] * pstar < apply_deg(ce, A.g.deg[v[t]], P.a_mode, P.a);
                 if (keep) {
                     ++accepted;
-                    push_to(Rn, v[t], P.eps);
+                    push_to(Rs + (size_t)v[t] * W, P.eps);
                 }
             }
         }
     }
 }
 
+// ---- row walks: deterministic prefixes and dense tails of all lanes of a group at once -------------
+// A lane's part of the walk of row N_u: positions j < k (the deterministic prefix) get c / d_{v_j}^a;
+// if its tail is dense, every position j >= k is an independent Bernoulli trial with probability
+// p_j = (c / eps) / d_{v_j}^a (subset sampling by definition, Section 4) and adds eps when kept. The
+// uniform of position j is word j & 3 of the Philox block (u, level, j >> 2, kDenseTag) under the
+// lane's key, so a lane's draws do not depend on the other lanes of its group or on who walks.
+struct WalkLane {
+    float c, ce, eps, a;
+    int k;          // deterministic prefix length; positions [k, d) are trials when `dense`
+    int a_mode;
+    int dense;      // 1: dense tail; -1: the lane takes no part in the walk
+    int lvl;
+    uint32_t key0, key1;
+};
+
+__device__ __forceinline__ WalkLane walk_lane(const LaneParam &P, float c, int k, bool dense, int lvl)
+{
+    WalkLane L;
+    L.c = c;
+    L.ce = c * P.inv_eps;
+    L.eps = P.eps;
+    L.a = P.a;
+    L.k = k;
+    L.a_mode = P.a_mode;
+    L.dense = dense ? 1 : 0;
+    L.lvl = lvl;
+    L.key0 = P.key0;
+    L.key1 = P.key1;
+    return L;
+}
+
+__device__ __forceinline__ WalkLane idle_walk_lane()
+{
+    WalkLane L{};
+    L.dense = -1;
+    return L;
+}
+
+// Increment of one lane at walk position pos (neighbour degree dv), with the lane's uniform word.
+__device__ __forceinline__ float walk_inc(const WalkLane &L, int pos, int32_t dv, uint32_t word, unsigned int &acc)
+{
+    if (pos < L.k) return (L.a_mode == 0) ? L.c : apply_deg(L.c, dv, L.a_mode, L.a);
+    if (L.dense > 0) {
+        const float p = (L.a_mode == 0) ? L.ce : apply_deg(L.ce, dv, L.a_mode, L.a);
+        if (u01_open(word) < p) {
+            ++acc;
+            return L.eps;
+        }
+    }
+    return 0.f;
+}
+
+// Positions [p0, p1) of the walk (p0 a multiple of 4, p1 - p0 <= 4) for the W lanes L[0..W) (shared
+// or local memory). acc[j] counts lane j's kept dense-tail trials.
+template <int W>
+__device__ __forceinline__ void walk4(const KArgs &A, float *Rg, const WalkLane *L, int32_t u, const int32_t *row,
+                                      int p0, int p1, bool need_deg, unsigned int (&acc)[W])
+{
+    int32_t v[4], dv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        v[t] = 0;
+        dv[t] = 1;
+        if (p0 + t < p1) v[t] = ld_col(row + p0 + t);
+    }
+    if (need_deg)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (p0 + t < p1) dv[t] = A.g.deg[v[t]];
+    float inc[4][W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) inc[t][j] = 0.f;
+        const int k = L[j].k;
+        const int dn = L[j].dense;
+        if (dn < 0 || (dn == 0 && k <= p0)) continue;  // no part in these positions
+        Philox4 q{0u, 0u, 0u, 0u};
+        if (dn > 0 && p1 > k)
+            q = philox4x32_10((uint32_t)u, (uint32_t)L[j].lvl, (uint32_t)(p0 >> 2), kDenseTag, L[j].key0, L[j].key1);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (p0 + t < p1) inc[t][j] = walk_inc(L[j], p0 + t, dv[t], w4[t], acc[j]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (p0 + t < p1) push_node<W>(Rg, v[t], inc[t]);
+}
+
+// The walk of one lane alone over positions [0, J) (a short row, done by the expanding thread):
+// the same increments and uniforms as in a group walk, scalar reductions.
+template <int W>
+__device__ __forceinline__ void walk_lane_inline(const KArgs &A, float *Rs, const WalkLane &L, int32_t u,
+                                                 const int32_t *row, int J, unsigned int &acc)
+{
+    for (int p0 = 0; p0 < J; p0 += 4) {
+        const int p1 = min(p0 + 4, J);
+        Philox4 q{0u, 0u, 0u, 0u};
+        if (L.dense > 0 && p1 > L.k)
+            q = philox4x32_10((uint32_t)u, (uint32_t)L.lvl, (uint32_t)(p0 >> 2), kDenseTag, L.key0, L.key1);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        int32_t v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (p0 + t < p1) v[t] = ld_col(row + p0 + t);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (p0 + t >= p1) break;
+            const int32_t dv = (L.a_mode != 0) ? A.g.deg[v[t]] : 1;
+            push_to(Rs + (size_t)v[t] * W, walk_inc(L, p0 + t, dv, w4[t], acc));
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------ kernels
-// ---- frontier compaction: F_i = {u : r^(i)(u) != 0} in ascending (lane, u) order ----------------
-// The residue vectors of lanes [0, lanes_used) are cut into units of kScanUnit floats; the units are
-// split into part_blocks contiguous ranges. Pass 1 counts the non-zeros of every range, pass 2
-// scans the counts, pass 3 writes (lane << ubits | u, r) of every non-zero and clears the vector.
-// Idle lanes (level < 0) are skipped; their vectors are zero.
+// ---- frontier compaction: F_i = {(group, u) : r^(i)(u) != 0 for a lane of the group} ------------
+// The residue blocks of the groups holding lanes [0, lanes_used) are cut into units of kScanUnit
+// floats (1024 / W nodes); the units are split into part_blocks contiguous ranges. Pass 1 counts the
+// frontier items of every range, pass 2 scans the counts, pass 3 writes (group << ubits | u) and the
+// W residues of every item, and clears the block. Groups whose lanes are all idle are skipped (their
+// residues are zero).
 __device__ __forceinline__ void compact_range(const KArgs &A, int64_t &begin, int64_t &end)
 {
-    const int64_t U = (int64_t)min((int)A.ctrl->lanes_used, A.G) * A.units;
+    const int groups = (min((int)A.ctrl->lanes_used, A.G) + A.W - 1) / A.W;
+    const int64_t U = (int64_t)groups * A.units;
     const int64_t per = (U + A.part_blocks - 1) / A.part_blocks;
     begin = (int64_t)blockIdx.x * per;
     end = min(U, begin + per);
 }
 
-__device__ __forceinline__ float4 *unit_ptr(const KArgs &A, int64_t unit, int &lane, bool &live)
+template <int W>
+__device__ __forceinline__ float4 *unit_ptr(const KArgs &A, int64_t unit, int &grp, int64_t &off_f, bool &live)
 {
-    lane = (int)(unit / A.units);
-    const int lvl = A.level[lane];
-    live = lvl >= 0;
-    const int64_t off = (unit - (int64_t)lane * A.units) * kScanUnit;
-    return (float4 *)(A.R + (size_t)lane * A.ldR + off);
+    grp = (int)(unit / A.units);
+    live = false;
+#pragma unroll
+    for (int j = 0; j < W; ++j) live |= A.level[grp * W + j] >= 0;
+    off_f = (unit - (int64_t)grp * A.units) * kScanUnit;  // float offset of the unit in its group block
+    return (float4 *)(A.R + (size_t)grp * A.ldR * W + off_f);
 }
 
-__device__ __forceinline__ int nz4(float4 v)
+// frontier items in one float4 of a group block: nodes with a non-zero lane
+template <int W>
+__device__ __forceinline__ int nz_items(float4 v)
 {
-    return (v.x != 0.f) + (v.y != 0.f) + (v.z != 0.f) + (v.w != 0.f);
+    if constexpr (W == 4) return (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) ? 1 : 0;
+    else if constexpr (W == 2) return (v.x != 0.f || v.y != 0.f) + (v.z != 0.f || v.w != 0.f);
+    else return (v.x != 0.f) + (v.y != 0.f) + (v.z != 0.f) + (v.w != 0.f);
 }
 
 // Exclusive scan across a block of 1024 threads (32 warps): warp shuffles, then one warp scans the
@@ -276,6 +428,7 @@ __device__ __forceinline__ unsigned long long block_scan_1024(unsigned long long
     return (warp > 0 ? sm[warp - 1] : 0ull) + x - v;
 }
 
+template <int W>
 __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
 {
     __shared__ unsigned long long red[kBlock / 32];
@@ -283,10 +436,11 @@ __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
     compact_range(A, begin, end);
     unsigned long long c = 0;
     for (int64_t unit = begin; unit < end; ++unit) {
-        int lane;
+        int grp;
+        int64_t off_f;
         bool live;
-        const float4 *p = unit_ptr(A, unit, lane, live);
-        if (live) c += nz4(p[threadIdx.x]);
+        const float4 *p = unit_ptr<W>(A, unit, grp, off_f, live);
+        if (live) c += nz_items<W>(p[threadIdx.x]);
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -320,9 +474,10 @@ __global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
 
 // Pass 3: units are taken four at a time. The four float4 loads of a thread are issued together,
 // and one block scan of the four per-thread counts (packed in 16-bit fields of a 64-bit word: a
-// unit holds at most 1024 non-zeros, so no field carries into the next) places every non-zero.
-// The warp totals are double-buffered, so a batch needs a single __syncthreads.
+// unit holds at most 1024 items, so no field carries into the next) places every item. The warp
+// totals are double-buffered, so a batch needs a single __syncthreads.
 constexpr int kEmitBatch = 4;
+template <int W>
 __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
 {
     __shared__ unsigned long long wsum[2][kBlock / 32];
@@ -334,16 +489,18 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
     for (int64_t u0 = begin; u0 < end; u0 += kEmitBatch, parity ^= 1) {
         float4 v[kEmitBatch];
         float4 *ptr[kEmitBatch];
-        int lanes[kEmitBatch];
+        int grps[kEmitBatch];
+        int64_t offs[kEmitBatch];
         unsigned long long packed = 0;
 #pragma unroll
         for (int j = 0; j < kEmitBatch; ++j) {
             v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             ptr[j] = nullptr;
-            lanes[j] = 0;
+            grps[j] = 0;
+            offs[j] = 0;
             if (u0 + j < end) {
                 bool live;
-                float4 *p = unit_ptr(A, u0 + j, lanes[j], live);
+                float4 *p = unit_ptr<W>(A, u0 + j, grps[j], offs[j], live);
                 if (live) {
                     ptr[j] = p;
                     v[j] = p[threadIdx.x];
@@ -351,7 +508,7 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
             }
         }
 #pragma unroll
-        for (int j = 0; j < kEmitBatch; ++j) packed |= (unsigned long long)nz4(v[j]) << (16 * j);
+        for (int j = 0; j < kEmitBatch; ++j) packed |= (unsigned long long)nz_items<W>(v[j]) << (16 * j);
         unsigned long long x = packed;  // inclusive warp scan of the packed counts
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -373,99 +530,127 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
             unsigned long long off = unit_base + ((excl >> (16 * j)) & 0xFFFFull);
             unit_base += (total >> (16 * j)) & 0xFFFFull;
             if (c == 0) continue;
-            const int lane = lanes[j];
-            const uint32_t ub = (uint32_t)((u0 + j - (int64_t)lane * A.units) * kScanUnit + 4 * threadIdx.x);
-            const uint32_t hi = (uint32_t)lane << A.ubits;
+            const int grp = grps[j];
+            const uint32_t hi = (uint32_t)grp << A.ubits;
+            const uint32_t node0 = (uint32_t)((offs[j] + 4 * threadIdx.x) / W);  // first node of this float4
             const float e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (e[k] == 0.f) continue;
+            for (int k = 0; k < 4 / W; ++k) {
+                bool any = false;
+#pragma unroll
+                for (int s = 0; s < W; ++s) any |= e[k * W + s] != 0.f;
+                if (!any) continue;
                 if (off < A.cap_items) {
-                    A.items[off] = hi | (ub + (uint32_t)k);
-                    A.rval[off] = e[k];
+                    A.items[off] = hi | (node0 + (uint32_t)k);
+                    if constexpr (W == 4) reinterpret_cast<float4 *>(A.rval)[off] = v[j];
+                    else if constexpr (W == 2)
+                        reinterpret_cast<float2 *>(A.rval)[off] = make_float2(e[2 * k], e[2 * k + 1]);
+                    else A.rval[off] = e[k];
                 } else {
                     atomicOr(&A.ctrl->error, 1u);
                 }
                 ++off;
+                if (A.collect)
+#pragma unroll
+                    for (int s = 0; s < W; ++s)
+                        if (e[k * W + s] != 0.f) {
+                            const int lane = grp * W + s;
+                            const int lvl = A.level[lane];
+                            if (lvl >= 0 && lvl < kMaxLevels) atomicAdd(&A.stats[lane].frontier[lvl], 1ull);
+                        }
             }
             ptr[j][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (A.collect) atomicAdd(&A.stats[lane].frontier[A.level[lane]], (unsigned long long)c);
         }
         run = unit_base;
     }
 }
 
-// Record counts of one frontier item: x = long-prefix chunks, y = tail records (bit 31 set: dense
-// per-position chunks; clear: sparse segments). Written for every item; k_rec_* turn them into
-// record lists without a shared counter.
-constexpr uint32_t kDenseBit = 0x80000000u;
-
+// Record counts of one frontier item: x = walk chunks (kChunk positions of the row walk that covers
+// the deterministic prefixes and dense tails of the item's walking lanes), y = sparse-tail segments
+// (over all lanes of the item). A lane whose own walk is short (<= kInlineDet positions) is walked
+// here, alone. Written for every item; k_rec_* turn them into record lists without a shared counter.
+// flag_item bits: j = lane j's tail is dense, 8 + j = lane j is in the walk, 16 + j = lane j has
+// segments; c_item / k_item / seg_item are written for the lanes named there.
+template <int W>
 __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long idx)
 {
     Ctrl *ctrl = A.ctrl;
     // every array read here is written only by earlier kernels: read-only path
     const uint32_t item = __ldg(A.items + idx);
-    const int lane = (int)(item >> A.ubits);
+    const int grp = (int)(item >> A.ubits);
     const int32_t u = (int32_t)(item & A.umask);
     const int32_t d = __ldg(A.g.deg + u);
     const int64_t e0 = __ldg(A.g.rowptr + u);
-    const float r = __ldg(A.rval + idx);  // the compaction read r^(i)(u) and cleared it
-    const int lvl = __ldg(A.level + lane);
-    if (lvl < 0 || lvl >= kMaxLevels) {
-        atomicOr(&ctrl->error, 16u);
-        return make_uint2(0u, 0u);
-    }
-    const LaneParam &P = A.lanes[lane];
-    float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
-    const float2 cf = __ldg(A.coef + lane * kMaxLevels + lvl);
-    // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
-    red_add(P.out + (int64_t)u * P.su, cf.x * r);
-    if (lvl >= P.L || d == 0) return make_uint2(0u, 0u);
-    const float c = apply_deg(cf.y * r, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
-    if (!(c > 0.f)) return make_uint2(0u, 0u);
+    float *Rg = A.R + (size_t)grp * A.ldR * W;  // r^(i+1): the compaction emptied r^(i)
     const int32_t *row = A.g.colidx + e0;
-    const int k = det_prefix(c, P, row, d, A.g.deg);
-    unsigned long long drawn = 0, accepted = 0;
-    uint2 nrec = make_uint2(0u, 0u);
-    if (k > 0) {
-        if (k <= kInlineDet) {
-#pragma unroll 4
-            for (int j = 0; j < k; ++j) {
-                const int32_t v = ld_col(row + j);
-                const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
-                push_to(Rn, v, inc);
+    int J = 0, nseg = 0;
+    uint32_t flags = 0;
+    // the lanes one after the other (a rolled loop keeps the per-lane state out of spilled registers)
+#pragma unroll 1
+    for (int j = 0; j < W; ++j) {
+        const float rj = __ldg(A.rval + idx * W + j);  // the compaction read r^(i)(u) and cleared it
+        if (rj == 0.f) continue;
+        const int lane = grp * W + j;
+        const int lvl = __ldg(A.level + lane);
+        if (lvl < 0 || lvl >= kMaxLevels) {
+            atomicOr(&ctrl->error, 16u);
+            continue;
+        }
+        const LaneParam &P = A.lanes[lane];
+        const float2 cf = __ldg(A.coef + lane * kMaxLevels + lvl);
+        // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
+        red_add(P.out + (int64_t)u * P.su, cf.x * rj);
+        if (lvl >= P.L || d == 0) continue;
+        const float c = apply_deg(cf.y * rj, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
+        if (!(c > 0.f)) continue;
+        const int k = det_prefix(c, P, row, d, A.g.deg);
+        const int tail = d - k;
+        bool is_dense = false;
+        int seglen = 0;
+        unsigned long long drawn = 0, accepted = 0;
+        if (tail > 0) {
+            const float ce = c * P.inv_eps;
+            const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
+            const float expect = p0 * (float)tail;  // upper bound on the trials reached
+            if (expect <= kLightSamples) {
+                sample_range<2, W>(A, P, Rg + j, u, lvl, 0u, row, k, d, c, drawn, accepted);
+            } else if (p0 >= kDenseP) {
+                is_dense = true;  // most positions are kept: one Bernoulli per position in the walk
+            } else {
+                int ns = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
+                ns = max(ns, 1);
+                seglen = (tail + ns - 1) / ns;
+                nseg += (tail + seglen - 1) / seglen;
             }
-            if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
-        } else {
-            nrec.x = (unsigned int)((k + kChunk - 1) / kChunk);
+        }
+        // a short deterministic prefix is pushed here; a longer one, and every dense tail, joins the
+        // group's walk (warps, coalesced neighbour loads, one reduction per neighbour for the group)
+        const int wlen = is_dense ? d : k;
+        bool in_walk = false;
+        if (wlen > 0) {
+            if (!is_dense && wlen <= kInlineDet) {
+                unsigned int acc = 0;
+                walk_lane_inline<W>(A, Rg + j, walk_lane(P, c, k, false, lvl), u, row, wlen, acc);
+                if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
+            } else {
+                in_walk = true;
+                J = max(J, wlen);
+            }
+        }
+        if (in_walk || seglen > 0) {
+            A.c_item[idx * W + j] = c;
+            A.k_item[idx * W + j] = k;
+            A.seg_item[idx * W + j] = seglen;
+            flags |= (in_walk ? (1u << (8 + j)) : 0u) | ((in_walk && is_dense) ? (1u << j) : 0u) |
+                     (seglen > 0 ? (1u << (16 + j)) : 0u);
+        }
+        if (A.collect && (drawn | accepted)) {
+            atomicAdd(&A.stats[lane].by_kernel[0][1], drawn);
+            atomicAdd(&A.stats[lane].by_kernel[0][2], accepted);
         }
     }
-    const int tail = d - k;
-    int seglen = 0;
-    if (tail > 0) {
-        const float ce = c * P.inv_eps;
-        const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
-        const float expect = p0 * (float)tail;  // upper bound on the trials reached
-        if (expect <= kLightSamples) {
-            sample_range<2>(A, P, Rn, u, lvl, 0u, row, k, d, c, drawn, accepted);
-        } else if (p0 >= kDenseP) {
-            // most positions are kept: one Bernoulli per position, by warps, coalesced colidx reads
-            nrec.y = kDenseBit | (unsigned int)((tail + kChunk - 1) / kChunk);
-        } else {
-            int nseg = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
-            nseg = max(nseg, 1);
-            seglen = (tail + nseg - 1) / nseg;
-            nrec.y = (unsigned int)((tail + seglen - 1) / seglen);
-        }
-    }
-    if (nrec.x | nrec.y) {
-        A.c_item[idx] = c;
-        A.k_item[idx] = make_int2(k, seglen);
-    }
-    if (A.collect && (drawn | accepted)) {
-        atomicAdd(&A.stats[lane].by_kernel[0][1], drawn);
-        atomicAdd(&A.stats[lane].by_kernel[0][2], accepted);
-    }
+    const uint2 nrec = make_uint2(J > 0 ? (unsigned int)((J + kChunk - 1) / kChunk) : 0u, (unsigned int)nseg);
+    if (nrec.x | nrec.y) A.flag_item[idx] = flags;
     return nrec;
 }
 
@@ -479,48 +664,39 @@ __device__ __forceinline__ void item_range(const KArgs &A, unsigned long long &b
     end = min(n, begin + per);
 }
 
-__device__ __forceinline__ void rec_split(uint2 nr, unsigned int &det, unsigned int &dns, unsigned int &smp)
-{
-    det = nr.x;
-    dns = (nr.y & kDenseBit) ? (nr.y & ~kDenseBit) : 0u;
-    smp = (nr.y & kDenseBit) ? 0u : nr.y;
-}
-
+template <int W>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
 {
-    __shared__ unsigned long long tot_s[3][kBlock / 32];
+    __shared__ unsigned long long tot_s[2][kBlock / 32];
     unsigned long long begin, end;
     item_range(A, begin, end);
     // per-thread record totals (32-bit: a thread's items have far fewer than 2^32 records; the
     // block sums are 64-bit)
-    unsigned int tot[3] = {0u, 0u, 0u};
+    unsigned int tot[2] = {0u, 0u};
     for (unsigned long long idx = begin + threadIdx.x; idx < end; idx += kBlock) {
-        const uint2 nr = expand_item(A, idx);
+        const uint2 nr = expand_item<W>(A, idx);
         A.nrec[idx] = nr;
-        unsigned int det, dns, smp;
-        rec_split(nr, det, dns, smp);
-        tot[0] += det;
-        tot[1] += dns;
-        tot[2] += smp;
+        tot[0] += nr.x;
+        tot[1] += nr.y;
     }
-    // block totals of the three record kinds, for k_rec_scan
-    unsigned long long wt[3];
+    // block totals of the two record kinds, for k_rec_scan
+    unsigned long long wt[2];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 2; ++t) {
         wt[t] = tot[t];
         for (int o = 16; o > 0; o >>= 1) wt[t] += __shfl_down_sync(0xffffffffu, wt[t], o);
     }
     if ((threadIdx.x & 31) == 0)
-        for (int t = 0; t < 3; ++t) tot_s[t][threadIdx.x >> 5] = wt[t];
+        for (int t = 0; t < 2; ++t) tot_s[t][threadIdx.x >> 5] = wt[t];
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 2) {
         unsigned long long s = 0;
         for (int w = 0; w < kBlock / 32; ++w) s += tot_s[threadIdx.x][w];
         A.rpart[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
     }
 }
 
-// One block of 1024 threads: exclusive scan of the per-block record counts of k_expand (three kinds,
+// One block of 1024 threads: exclusive scan of the per-block record counts of k_expand (two kinds,
 // each a row of nb entries); the totals become the record list sizes.
 __global__ void __launch_bounds__(1024) k_rec_scan(KArgs A, int nb)
 {
@@ -528,7 +704,7 @@ __global__ void __launch_bounds__(1024) k_rec_scan(KArgs A, int nb)
     const int t = threadIdx.x;
     const int chunk = (nb + blockDim.x - 1) / blockDim.x;
     const int b0 = min(nb, t * chunk), b1 = min(nb, b0 + chunk);
-    for (int kind = 0; kind < 3; ++kind) {
+    for (int kind = 0; kind < 2; ++kind) {
         unsigned long long *row = A.rpart + (size_t)kind * nb;
         unsigned long long s = 0;
         for (int b = b0; b < b1; ++b) s += row[b];
@@ -541,25 +717,24 @@ __global__ void __launch_bounds__(1024) k_rec_scan(KArgs A, int nb)
         }
         if (t == 0) {
             if (kind == 0) A.ctrl->n_det = total;
-            else if (kind == 1) A.ctrl->n_dns = total;
             else A.ctrl->n_smp = total;
         }
         __syncthreads();  // sm is reused by the next kind
     }
 }
 
-// Writes the records of every item at its block's offset plus its place in the block: prefix
-// chunks (item, chunk), dense-tail chunks (item, chunk) and sparse segments (item, segment), in
-// item order. Same grid and ranges as k_expand.
+// Writes the records of every item at its block's offset plus its place in the block: walk chunks
+// (item, chunk) and sparse-tail segments (item, segment over the item's lanes), in item order. Same
+// grid and ranges as k_expand.
 __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
 {
-    __shared__ unsigned int wsum[2][3][kBlock / 32];
+    __shared__ unsigned int wsum[2][2][kBlock / 32];
     unsigned long long begin, end;
     item_range(A, begin, end);
     const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long base[3];
+    unsigned long long base[2];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) base[t] = A.rpart[(size_t)t * gridDim.x + blockIdx.x];
+    for (int t = 0; t < 2; ++t) base[t] = A.rpart[(size_t)t * gridDim.x + blockIdx.x];
     int parity = 0;
     // the counts of the next tile are loaded while the current one is scanned and written
     uint2 nr_next = (begin + threadIdx.x < end) ? A.nrec[begin + threadIdx.x] : make_uint2(0u, 0u);
@@ -568,11 +743,10 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
         const uint2 nr = nr_next;
         const unsigned long long nidx = idx + kBlock;
         nr_next = (nidx < end) ? A.nrec[nidx] : make_uint2(0u, 0u);
-        unsigned int cnt[3] = {0u, 0u, 0u};
-        rec_split(nr, cnt[0], cnt[1], cnt[2]);
-        unsigned int x[3];
+        const unsigned int cnt[2] = {nr.x, nr.y};
+        unsigned int x[2];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < 2; ++t) {
             x[t] = cnt[t];  // inclusive warp scan
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned int y = __shfl_up_sync(0xffffffffu, x[t], o);
@@ -581,9 +755,9 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
             if (lane_id == 31) wsum[parity][t][warp] = x[t];
         }
         __syncthreads();
-        unsigned long long off[3], total[3];
+        unsigned long long off[2], total[2];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < 2; ++t) {
             unsigned long long before = 0, all = 0;
             for (int w = 0; w < kBlock / 32; ++w) {
                 const unsigned int v = wsum[parity][t][w];
@@ -598,104 +772,119 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
             else atomicOr(&A.ctrl->error, 2u);
         }
         for (unsigned int r = 0; r < cnt[1]; ++r) {
-            if (off[1] + r < A.cap_dns) A.dns_rec[off[1] + r] = make_uint2((uint32_t)idx, r);
-            else atomicOr(&A.ctrl->error, 8u);
-        }
-        for (unsigned int r = 0; r < cnt[2]; ++r) {
-            if (off[2] + r < A.cap_smp) A.smp_rec[off[2] + r] = make_uint2((uint32_t)idx, r);
+            if (off[1] + r < A.cap_smp) A.smp_rec[off[1] + r] = make_uint2((uint32_t)idx, r);
             else atomicOr(&A.ctrl->error, 4u);
         }
 #pragma unroll
-        for (int t = 0; t < 3; ++t) base[t] += total[t];
+        for (int t = 0; t < 2; ++t) base[t] += total[t];
     }
 }
 
-// Per-position subset sampling of tail positions [k + chunk * kChunk, ...) of a dense tail: every
-// position is an independent Bernoulli trial with its own probability p_v = (c / eps) / d_v^a. Lane
-// l takes positions 4 l .. 4 l + 3 of every 128, with the 4 uniforms of Philox block
-// (u, level, (position - k) / 4, kDenseTag).
-__device__ __forceinline__ void dense_tail_chunk(const KArgs &A, const LaneParam &P, float *Rn, int32_t u, int lvl,
-                                                 const int32_t *row, int k, int d, int chunk, float c, int lane_id,
-                                                 unsigned long long &drawn, unsigned long long &accepted)
-{
-    const float ce = c * P.inv_eps;
-    const int r0 = chunk * kChunk, r1 = min(d - k, r0 + kChunk);
-    for (int rel = r0 + 4 * lane_id; rel < r1; rel += 128) {
-        const Philox4 q = philox4x32_10((uint32_t)u, (uint32_t)lvl, (uint32_t)(rel >> 2), kDenseTag, P.key0, P.key1);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (rel + t >= r1) break;
-            const int32_t v = ld_col(row + k + rel + t);
-            const float p = (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
-            ++drawn;
-            if (u01_open(w[t]) < p) {
-                ++accepted;
-                push_to(Rn, v, P.eps);
-            }
-        }
-    }
-}
-
-// One warp per record: 512-edge chunks of long deterministic prefixes, then 512-position chunks of
-// dense tails.
+// One warp per walk chunk: positions [chunk * kChunk, ...) of the item's row walk, 4 consecutive
+// positions per thread (one Philox block per dense lane), coalesced neighbour loads. The record's
+// lane states sit in shared memory, one slot per warp.
+template <int W>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
 {
-    const unsigned long long n_det = min(A.ctrl->n_det, A.cap_det);
-    const unsigned long long n_all = n_det + min(A.ctrl->n_dns, A.cap_dns);
-    const int lane_id = threadIdx.x & 31;
+    __shared__ WalkLane sL[kBlock / 32][W];
+    const unsigned long long n_rec = min(A.ctrl->n_det, A.cap_det);
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long rec = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; rec < n_all; rec += nwarps) {
-        const bool det = rec < n_det;
-        const uint2 R = det ? A.det_rec[rec] : A.dns_rec[rec - n_det];
-        const uint32_t item = A.items[R.x];
-        const int lane = (int)(item >> A.ubits);
+    for (unsigned long long rec = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; rec < n_rec; rec += nwarps) {
+        const uint2 Rc = A.det_rec[rec];
+        const unsigned long long idx = Rc.x;
+        const uint32_t item = A.items[idx];
+        const int grp = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
-        const int lvl = A.level[lane];
-        const LaneParam &P = A.lanes[lane];
-        float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
-        const float c = A.c_item[R.x];
-        const int k = A.k_item[R.x].x;
-        const int32_t *row = A.g.colidx + A.g.rowptr[u];
-        if (det) {
-            const int j0 = (int)R.y * kChunk, j1 = min(k, j0 + kChunk);
-#pragma unroll 4
-            for (int j = j0 + lane_id; j < j1; j += 32) {
-                const int32_t v = ld_col(row + j);
-                const float inc = (P.a_mode == 0) ? c : apply_deg(c, A.g.deg[v], P.a_mode, P.a);
-                push_to(Rn, v, inc);
+        const int d = A.g.deg[u];
+        const uint32_t flags = A.flag_item[idx];
+        __syncwarp();
+        if (lane_id < W) {
+            const int j = lane_id;
+            WalkLane L = idle_walk_lane();
+            if ((flags >> (8 + j)) & 1u) {
+                const int lane = grp * W + j;
+                L = walk_lane(A.lanes[lane], A.c_item[idx * W + j], A.k_item[idx * W + j], (flags >> j) & 1u,
+                              A.level[lane]);
             }
-            if (A.collect && lane_id == 0) atomicAdd(&A.stats[lane].by_kernel[1][0], (unsigned long long)(j1 - j0));
-        } else {
-            unsigned long long drawn = 0, accepted = 0;
-            dense_tail_chunk(A, P, Rn, u, lvl, row, k, A.g.deg[u], (int)R.y, c, lane_id, drawn, accepted);
-            if (A.collect) {
-                atomicAdd(&A.stats[lane].by_kernel[1][1], drawn);
-                atomicAdd(&A.stats[lane].by_kernel[1][2], accepted);
+            sL[warp][j] = L;
+        }
+        __syncwarp();
+        int J = 0;
+        bool need_deg = false;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const WalkLane &L = sL[warp][j];
+            if (L.dense < 0) continue;
+            J = max(J, L.dense > 0 ? d : L.k);
+            need_deg |= L.a_mode != 0;
+        }
+        float *Rg = A.R + (size_t)grp * A.ldR * W;
+        const int32_t *row = A.g.colidx + A.g.rowptr[u];
+        const int c0 = (int)Rc.y * kChunk, c1 = min(J, c0 + kChunk);
+        unsigned int acc[W] = {};
+        for (int p0 = c0 + 4 * lane_id; p0 < c1; p0 += 128) walk4<W>(A, Rg, sL[warp], u, row, p0, min(p0 + 4, c1), need_deg, acc);
+        if (A.collect) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const WalkLane &L = sL[warp][j];
+                if (L.dense < 0) continue;
+                const int lane = grp * W + j;
+                if (lane_id == 0) {
+                    const int det = max(0, min(L.k, c1) - c0);
+                    const int trials = (L.dense > 0) ? max(0, c1 - max(c0, L.k)) : 0;
+                    atomicAdd(&A.stats[lane].by_kernel[1][0], (unsigned long long)det);
+                    atomicAdd(&A.stats[lane].by_kernel[1][1], (unsigned long long)trials);
+                }
+                if (acc[j]) atomicAdd(&A.stats[lane].by_kernel[1][2], (unsigned long long)acc[j]);
             }
         }
     }
 }
 
+// One thread per sparse-tail segment: record (item, s), s counting the segments of the item's lanes
+// in slot order.
+template <int W>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
 {
     const unsigned long long n_smp = min(A.ctrl->n_smp, A.cap_smp);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long rec = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; rec < n_smp; rec += stride) {
-        const uint2 R = A.smp_rec[rec];
-        const uint32_t item = A.items[R.x];
-        const int lane = (int)(item >> A.ubits);
+        const uint2 Rc = A.smp_rec[rec];
+        const unsigned long long idx = Rc.x;
+        const uint32_t item = A.items[idx];
+        const int grp = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
+        const int d = A.g.deg[u];
+        const uint32_t flags = A.flag_item[idx];
+        int s = (int)Rc.y, slot = -1, k = 0, seglen = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (slot >= 0 || !((flags >> (16 + j)) & 1u)) continue;
+            const int sl = A.seg_item[idx * W + j];
+            const int kj = A.k_item[idx * W + j];
+            const int ns = (d - kj + sl - 1) / sl;
+            if (s < ns) {
+                slot = j;
+                k = kj;
+                seglen = sl;
+            } else {
+                s -= ns;
+            }
+        }
+        if (slot < 0) {
+            atomicOr(&A.ctrl->error, 4u);
+            continue;
+        }
+        const int lane = grp * W + slot;
         const int lvl = A.level[lane];
         const LaneParam &P = A.lanes[lane];
-        float *Rn = A.R + (size_t)lane * A.ldR;  // r^(i+1): the compaction emptied r^(i)
-        const float c = A.c_item[R.x];
-        const int2 ks = A.k_item[R.x];
-        const int d = A.g.deg[u];
-        const int j0 = ks.x + (int)R.y * ks.y, j1 = min(d, j0 + ks.y);
+        float *Rs = A.R + (size_t)grp * A.ldR * W + slot;
+        const float c = A.c_item[idx * W + slot];
+        const int j0 = k + s * seglen, j1 = min(d, j0 + seglen);
         const int32_t *row = A.g.colidx + A.g.rowptr[u];
         unsigned long long drawn = 0, accepted = 0;
-        sample_range<4>(A, P, Rn, u, lvl, R.y, row, j0, j1, c, drawn, accepted);
+        sample_range<4, W>(A, P, Rs, u, lvl, (uint32_t)s, row, j0, j1, c, drawn, accepted);
         if (A.collect && (drawn | accepted)) {
             atomicAdd(&A.stats[lane].by_kernel[2][1], drawn);
             atomicAdd(&A.stats[lane].by_kernel[2][2], accepted);
@@ -714,11 +903,16 @@ __global__ void k_level_end(KArgs A)
     if (threadIdx.x == 0) {
         ctrl->n_det = 0;
         ctrl->n_smp = 0;
-        ctrl->n_dns = 0;
     }
 }
 
 // ---- seeds -------------------------------------------------------------------------------------
+// Residue of `lane` at node u: lane / W is its group, lane % W its slot in the group's block.
+__device__ __forceinline__ float *lane_res(const KArgs &A, int lane, int64_t u)
+{
+    return A.R + ((size_t)(lane / A.W) * A.ldR + (size_t)u) * A.W + (lane % A.W);
+}
+
 __device__ __forceinline__ int query_of(const int64_t *off, int Q, int64_t t)
 {
     int lo = 0, hi = Q;  // last q with off[q] <= t
@@ -756,9 +950,7 @@ __global__ void k_seed_sparse(KArgs A, const int64_t *off, const int32_t *idx, c
         const int lane = lane_of[2 * q + part];
         const int32_t u = idx[t];
         if (lane < 0 || u < 0 || u >= A.g.n) continue;
-        float *R0 = A.R + (size_t)lane * A.ldR;
-        const float r0 = (float)((double)fabsf(x) / norms[2 * q + part]);
-        push_to(R0, u, r0);
+        push_to(lane_res(A, lane, u), (float)((double)fabsf(x) / norms[2 * q + part]));
     }
 }
 
@@ -768,7 +960,7 @@ __global__ void k_seed_sources(KArgs A, const int32_t *lanes, const int32_t *sou
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
         const int lane = lanes[t];
         const int32_t u = sources[t];
-        if (u >= 0 && u < A.g.n) push_to(A.R + (size_t)lane * A.ldR, u, 1.f);
+        if (u >= 0 && u < A.g.n) push_to(lane_res(A, lane, u), 1.f);
     }
 }
 
@@ -801,9 +993,7 @@ __global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const
         const int part = part_of[l];
         if (!((part == 0 && x > 0.f) || (part == 1 && x < 0.f))) continue;
         const int lane = lane_of ? lane_of[l] : l;
-        float *R0 = A.R + (size_t)lane * A.ldR;
-        const float r0 = (float)((double)fabsf(x) / norms[2 * col + part]);
-        push_to(R0, (int32_t)u, r0);
+        push_to(lane_res(A, lane, u), (float)((double)fabsf(x) / norms[2 * col + part]));
     }
 }
 
@@ -869,7 +1059,7 @@ __global__ void k_seed_dense_rows(KArgs A, const T *X, int64_t ldx, int Q, const
         const int part = x < 0.f ? 1 : 0;
         const int lane = lane_of[2 * q + part];
         if (lane < 0) continue;
-        push_to(A.R + (size_t)lane * A.ldR, (int32_t)u, (float)((double)fabsf(x) / norms[2 * q + part]));
+        push_to(lane_res(A, lane, u), (float)((double)fabsf(x) / norms[2 * q + part]));
     }
 }
 
@@ -972,11 +1162,14 @@ size_t bytes_per_lane(const agp_graph_s *g)
 {
     const size_t n = (size_t)g->n;
     const double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
-    // R (4) + items (4) + r values (4) + c (4) + k (8) + record counts (8) + prefix-chunk,
-    // dense-tail-chunk and segment records (8 each, with the extra records of long rows) per (lane, node)
-    return n * (4 + 4 + 4 + 4 + 8 + 8) + (size_t)(n * 16 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
+    // per (lane, node): R (4), the item's residue, c, k and segment length (16), and the lane's share
+    // of the item id, flags and record counts (16, as if every lane were its own group); walk-chunk
+    // records (8, with the extra records of long rows) and segment records (8, likewise)
+    return n * (4 + 16 + 16) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
+// Lanes a workspace can hold: the group index of an item has 32 - ubits bits, and the item lists
+// are indexed with 32-bit record fields.
 int lane_capacity(const agp_graph_s *g)
 {
     const int by_bits = (g->ubits >= 31) ? 1 : (int)std::min<int64_t>(4096, 1ll << (32 - g->ubits));
@@ -998,11 +1191,12 @@ void free_workspace(Workspace *ws)
     cudaFree(ws->part);
     cudaFree(ws->c_item);
     cudaFree(ws->k_item);
+    cudaFree(ws->seg_item);
+    cudaFree(ws->flag_item);
     cudaFree(ws->nrec);
     cudaFree(ws->rpart);
     cudaFree(ws->det_rec);
     cudaFree(ws->smp_rec);
-    cudaFree(ws->dns_rec);
     cudaFree(ws->lanes);
     cudaFree(ws->coef);
     cudaFree(ws->level);
@@ -1016,15 +1210,18 @@ void free_workspace(Workspace *ws)
     delete ws;
 }
 
-// Lanes in flight per wave. Every lane scatters atomics into its own dense n-vector r^(i+1); the
-// automatic choice keeps those vectors of all lanes in flight within ~96 MB of the 129 MB L2, so
-// that the random atomics are served by L2 rather than DRAM (measured: 16 lanes of 4M nodes ran
-// slower than one lane at a time).
+// Lanes in flight per wave. Every lane scatters atomics into its own residues; the automatic choice
+// keeps the residue blocks of all lanes in flight within ~96 MB of the 129 MB L2, so that the
+// random reductions are served by L2 rather than DRAM (measured: 16 lanes of 4M nodes ran slower
+// than one lane at a time), rounded down to a multiple of 4 lanes (one full group) when it is 4 or
+// more.
 int wave_lanes(const agp_graph_s *g)
 {
     if (g->wave_lanes > 0) return g->wave_lanes;
     const int64_t per_lane = 4 * std::max<int64_t>(g->n, 1);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (96ll << 20) / per_lane));
+    int64_t l = std::max<int64_t>(1, std::min<int64_t>(4096, (96ll << 20) / per_lane));
+    if (l >= 4) l = l / 4 * 4;
+    return (int)l;
 }
 
 // Lanes that fit the graph's memory budget (default: 60% of the free device memory, counting the
@@ -1042,35 +1239,42 @@ int lanes_for_budget(agp_graph_s *g, int64_t held, int *lanes)
     return AGP_OK;
 }
 
-int create_workspace(agp_graph_s *g, int G, Workspace **out)
+int create_workspace(agp_graph_s *g, int G, int W, Workspace **out)
 {
+    if (W != 1 && W != 2 && W != 4) return fail(AGP_EINTERNAL, "group width must be 1, 2 or 4");
+    G = (G + W - 1) / W * W;
     Workspace *ws = new Workspace();
     ws->device = g->device;
     ws->G = G;
+    ws->W = W;
     ws->n = g->n;
     const unsigned long long n = (unsigned long long)std::max<int64_t>(g->n, 1);
-    ws->cap_items = (unsigned long long)G * n;
-    ws->cap_det = ws->cap_items + (unsigned long long)G * (unsigned long long)g->nnz / kChunk + 1;
-    ws->cap_smp = ws->cap_items + (unsigned long long)G * (unsigned long long)g->nnz / kMinSeg + 1;
-    ws->cap_dns = ws->cap_det;
+    const unsigned long long groups = (unsigned long long)(G / W), nnz = (unsigned long long)g->nnz;
+    ws->cap_items = groups * n;
+    // a row is walked at most once per group and level: ceil(d_u / kChunk) <= 1 + d_u / kChunk chunks
+    ws->cap_det = ws->cap_items + groups * nnz / kChunk + 1;
+    // segments of a lane's tail: at most 1 + d_u / kMinSeg per (lane, node)
+    ws->cap_smp = (unsigned long long)G * n + (unsigned long long)G * nnz / kMinSeg + 1;
     size_t acc = 0;
     int rc = AGP_OK;
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
-    ws->ldR = ((int64_t)n + kScanUnit - 1) / kScanUnit * kScanUnit;
-    const int64_t units = (int64_t)G * (ws->ldR / kScanUnit);
+    const int64_t node_unit = kScanUnit / W;  // nodes per scanned unit of a group block
+    ws->ldR = ((int64_t)n + node_unit - 1) / node_unit * node_unit;
+    const int64_t units = (int64_t)groups * (ws->ldR * W / kScanUnit);
     ws->grid = grid_stride_blocks();
     ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid, units));
     A(dev_alloc(&ws->R, (size_t)G * ws->ldR, acc));
     A(dev_alloc(&ws->items, ws->cap_items, acc));
-    A(dev_alloc(&ws->rval, ws->cap_items, acc));
+    A(dev_alloc(&ws->rval, ws->cap_items * W, acc));
     A(dev_alloc(&ws->part, (size_t)ws->part_blocks + 1, acc));
-    A(dev_alloc(&ws->c_item, ws->cap_items, acc));
-    A(dev_alloc(&ws->k_item, ws->cap_items, acc));
+    A(dev_alloc(&ws->c_item, ws->cap_items * W, acc));
+    A(dev_alloc(&ws->k_item, ws->cap_items * W, acc));
+    A(dev_alloc(&ws->seg_item, ws->cap_items * W, acc));
+    A(dev_alloc(&ws->flag_item, ws->cap_items, acc));
     A(dev_alloc(&ws->nrec, ws->cap_items, acc));
-    A(dev_alloc(&ws->rpart, (size_t)3 * ws->grid, acc));
+    A(dev_alloc(&ws->rpart, (size_t)2 * ws->grid, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
-    A(dev_alloc(&ws->dns_rec, ws->cap_dns, acc));
     A(dev_alloc(&ws->lanes, (size_t)G, acc));
     A(dev_alloc(&ws->coef, (size_t)G * kMaxLevels, acc));
     A(dev_alloc(&ws->level, (size_t)G, acc));
@@ -1103,16 +1307,38 @@ void drop_workspace(agp_graph_s *g)
     cudaGetLastError();
     free_workspace(g->ws);
     free_workspace(g->ws2);
+    free_workspace(g->ws_plain);
     g->ws = nullptr;
     g->ws2 = nullptr;
+    g->ws_plain = nullptr;
 }
 
-int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
+// The graph's work buffers for waves of `lanes_wanted` lanes: the batched workspace (group width
+// from the wave width), or for the plain path a one-lane workspace of its own (group width 1, so
+// the baseline scans one lane's residues, not a group's).
+int ensure_workspace(agp_graph_s *g, int lanes_wanted, bool plain, Workspace **out)
 {
+    if (plain) {
+        if (!g->ws_plain) AGP_TRY(create_workspace(g, 1, 1, &g->ws_plain));
+        *out = g->ws_plain;
+        return AGP_OK;
+    }
     int by_budget = 0;
     AGP_TRY(lanes_for_budget(g, g->ws ? (int64_t)g->ws->bytes : 0, &by_budget));
-    const int G = std::max(1, std::min(lanes_wanted, by_budget));
-    if (g->ws && g->ws->G >= G) {
+    int G = std::max(1, std::min(lanes_wanted, by_budget));
+    int W;
+    if (g->group_width > 0) {  // the graph's setting: whole groups of that width
+        W = std::min(g->group_width, std::max(1, by_budget));
+        while (W > 1 && W > G) W /= 2;
+        G = (G + W - 1) / W * W;
+    } else {
+        if (G >= 3) {  // whole groups of four lanes: round up when the budget allows, else down
+            const int up = (G + 3) / 4 * 4;
+            G = (up <= by_budget) ? up : std::max(G / 4 * 4, std::min(G, 2));
+        }
+        W = group_width(G);
+    }
+    if (g->ws && g->ws->G >= G && g->ws->W == W) {
         *out = g->ws;
         return AGP_OK;
     }
@@ -1123,7 +1349,7 @@ int ensure_workspace(agp_graph_s *g, int lanes_wanted, Workspace **out)
         free_workspace(g->ws2);
         g->ws2 = nullptr;
     }
-    AGP_TRY(create_workspace(g, G, &g->ws));
+    AGP_TRY(create_workspace(g, G, W, &g->ws));
     *out = g->ws;
     return AGP_OK;
 }
@@ -1167,24 +1393,25 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.g = g->dev();
     A.ubits = g->ubits;
     A.umask = (g->ubits >= 32) ? 0xffffffffu : ((1u << g->ubits) - 1u);
+    A.W = ws->W;
     A.R = ws->R;
     A.items = ws->items;
     A.rval = ws->rval;
     A.ldR = ws->ldR;
-    A.units = ws->ldR / kScanUnit;
+    A.units = ws->ldR * ws->W / kScanUnit;
     A.part = ws->part;
     A.part_blocks = ws->part_blocks;
     A.c_item = ws->c_item;
     A.k_item = ws->k_item;
+    A.seg_item = ws->seg_item;
+    A.flag_item = ws->flag_item;
     A.nrec = ws->nrec;
     A.rpart = ws->rpart;
     A.det_rec = ws->det_rec;
     A.smp_rec = ws->smp_rec;
-    A.dns_rec = ws->dns_rec;
     A.cap_items = ws->cap_items;
     A.cap_det = ws->cap_det;
     A.cap_smp = ws->cap_smp;
-    A.cap_dns = ws->cap_dns;
     A.lanes = ws->lanes;
     A.coef = ws->coef;
     A.level = ws->level;
@@ -1206,28 +1433,44 @@ int ensure_events(Workspace *ws)
     return AGP_OK;
 }
 
-// Frontier compaction: residue vectors of the lanes -> ascending item list, size in ctrl->n_items.
-void launch_compact(const KArgs &A, cudaStream_t s)
+// Frontier compaction: residue blocks of the groups -> ascending item list, size in ctrl->n_items.
+template <int W> void launch_compact_w(const KArgs &A, cudaStream_t s)
 {
-    k_compact_count<<<A.part_blocks, kBlock, 0, s>>>(A);
+    k_compact_count<W><<<A.part_blocks, kBlock, 0, s>>>(A);
     k_compact_scan<<<1, 1024, 0, s>>>(A);
-    k_compact_emit<<<A.part_blocks, kBlock, 0, s>>>(A);
+    k_compact_emit<W><<<A.part_blocks, kBlock, 0, s>>>(A);
 }
 
-// Expansion and its record lists (sizes in ctrl->n_det, n_dns, n_smp). k_expand and k_rec_emit
-// must run on the same grid: they walk the same item ranges.
-void launch_expand(const KArgs &A, cudaStream_t s)
+// Expansion and its record lists (sizes in ctrl->n_det, n_smp). k_expand and k_rec_emit must run on
+// the same grid: they walk the same item ranges.
+template <int W> void launch_expand_w(const KArgs &A, cudaStream_t s)
 {
-    k_expand<<<A.grid, kBlock, 0, s>>>(A);
+    k_expand<W><<<A.grid, kBlock, 0, s>>>(A);
     k_rec_scan<<<1, 1024, 0, s>>>(A, A.grid);
     k_rec_emit<<<A.grid, kBlock, 0, s>>>(A);
 }
+
+template <int W> void launch_push_w(const KArgs &A, cudaStream_t s, int blocks) { k_push<W><<<blocks, kBlock, 0, s>>>(A); }
+template <int W> void launch_sample_w(const KArgs &A, cudaStream_t s, int blocks) { k_sample<W><<<blocks, kBlock, 0, s>>>(A); }
+
+#define AGP_BY_WIDTH(fn, ...)                         \
+    do {                                              \
+        if (A.W == 4) fn<4>(__VA_ARGS__);             \
+        else if (A.W == 2) fn<2>(__VA_ARGS__);        \
+        else fn<1>(__VA_ARGS__);                      \
+    } while (0)
+
+void launch_compact(const KArgs &A, cudaStream_t s) { AGP_BY_WIDTH(launch_compact_w, A, s); }
+void launch_expand(const KArgs &A, cudaStream_t s) { AGP_BY_WIDTH(launch_expand_w, A, s); }
+void launch_push(const KArgs &A, cudaStream_t s, int blocks) { AGP_BY_WIDTH(launch_push_w, A, s, blocks); }
+void launch_sample(const KArgs &A, cudaStream_t s, int blocks) { AGP_BY_WIDTH(launch_sample_w, A, s, blocks); }
 
 // One level: compact, expand, push, sample, level end. With `ev` (profiling) every step is
 // bracketed by event records on the same stream.
 void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,
                   cudaEvent_t (*ev)[2])
 {
+    (void)expand_blocks;
     // External records become event nodes when captured into a graph (plain records during
     // capture only express dependencies and never fire).
     auto rec = [&](cudaEvent_t e) { cudaEventRecordWithFlags(e, s, cudaEventRecordExternal); };
@@ -1236,9 +1479,9 @@ void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_bl
     if (ev) { rec(ev[0][1]); rec(ev[1][0]); }
     launch_expand(A, s);
     if (ev) { rec(ev[1][1]); rec(ev[2][0]); }
-    k_push<<<push_blocks, kBlock, 0, s>>>(A);
+    launch_push(A, s, push_blocks);
     if (ev) { rec(ev[2][1]); rec(ev[3][0]); }
-    k_sample<<<sample_blocks, kBlock, 0, s>>>(A);
+    launch_sample(A, s, sample_blocks);
     if (ev) { rec(ev[3][1]); rec(ev[4][0]); }
     k_level_end<<<1, kBlock, 0, s>>>(A);
     if (ev) rec(ev[4][1]);
@@ -1338,11 +1581,11 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             ran[lvl * kProfKernels + 1] = true;
             AGP_CUDA_TRY(cudaMemcpyAsync(ws->h_ctrl, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
             AGP_CUDA_TRY(cudaStreamSynchronize(s));
-            const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det) + std::min(ws->h_ctrl->n_dns, ws->cap_dns),
+            const unsigned long long nd = std::min(ws->h_ctrl->n_det, ws->cap_det),
                                      ns = std::min(ws->h_ctrl->n_smp, ws->cap_smp);
             __atomic_fetch_add(&g->kernel_launches, (int64_t)(4 + (nd ? 1 : 0) + (ns ? 1 : 0)), __ATOMIC_RELAXED);
-            if (nd) { rec(2, 0); k_push<<<blocks_for(nd, kBlock / 32), kBlock, 0, s>>>(A); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
-            if (ns) { rec(3, 0); k_sample<<<blocks_for(ns, kBlock), kBlock, 0, s>>>(A); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
+            if (nd) { rec(2, 0); launch_push(A, s, blocks_for(nd, kBlock / 32)); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
+            if (ns) { rec(3, 0); launch_sample(A, s, blocks_for(ns, kBlock)); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
             rec(4, 0);
             k_level_end<<<1, kBlock, 0, s>>>(A);
             rec(4, 1);
@@ -1497,6 +1740,9 @@ struct WaveJob {
     // optional: called on the wave's stream after its levels, once every earlier wave is complete
     // on that stream too (result rows that are final can be copied out while later waves compute)
     std::function<int(size_t first, int count, cudaStream_t st)> after_wave;
+    // optional (AGP_QUERY_TIMES): done_ms[lanes[i].query] = device time from the first wave's start to
+    // the end of the wave that ran lane i, largest over the query's lanes
+    agp_stats_t *times = nullptr;
 };
 
 // Runs the waves (G lanes each) of a call. Unless the call is on the plain path or on a fixed
@@ -1512,12 +1758,12 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
     Workspace *wss[2] = {ws0, nullptr};
     cudaStream_t ss[2] = {s, nullptr};
     if (two) {
-        if (g->ws2 && g->ws2->G < ws0->G) {
+        if (g->ws2 && (g->ws2->G < ws0->G || g->ws2->W != ws0->W)) {
             AGP_CUDA_TRY(cudaDeviceSynchronize());
             free_workspace(g->ws2);
             g->ws2 = nullptr;
         }
-        if (!g->ws2) AGP_TRY(create_workspace(g, ws0->G, &g->ws2));
+        if (!g->ws2) AGP_TRY(create_workspace(g, ws0->G, ws0->W, &g->ws2));
         if (!g->side) {
             AGP_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
             AGP_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
@@ -1530,6 +1776,17 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
     }
     size_t wfirst[2] = {0, 0};
     int wcount[2] = {0, 0};
+    // AGP_QUERY_TIMES: event 0 at the start, event 1 + w at the end of wave w
+    const size_t n_waves = (lanes.size() + G - 1) / G;
+    if (job.times) {
+        while (g->wave_ev.size() < n_waves + 1) {
+            cudaEvent_t e;
+            AGP_CUDA_TRY(cudaEventCreate(&e));
+            g->wave_ev.push_back(e);
+        }
+        AGP_CUDA_TRY(cudaEventRecord(g->wave_ev[0], s));
+        if (two) AGP_CUDA_TRY(cudaStreamWaitEvent(g->side, g->wave_ev[0], 0));
+    }
     auto finish = [&](int k) -> int {
         Workspace *W = wss[k];
         if (!W || !W->pending) return AGP_OK;
@@ -1568,6 +1825,7 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
             if ((rc = job.after_wave(first, count, st)) != AGP_OK) break;
             AGP_CUDA_TRY(cudaEventRecord(g->ev_wave[k], st));
         }
+        if (job.times) AGP_CUDA_TRY(cudaEventRecord(g->wave_ev[1 + w], st));
         W->pending = true;
         wfirst[k] = first;
         wcount[k] = count;
@@ -1579,6 +1837,21 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
     if (two) {
         cudaEventRecord(g->ev_join, g->side);
         cudaStreamWaitEvent(s, g->ev_join, 0);
+    }
+    if (rc == AGP_OK && job.times && n_waves > 0) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = fail(AGP_ECUDA, "waiting for the waves");
+        for (size_t w = 0; rc == AGP_OK && w < n_waves; ++w) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, g->wave_ev[0], g->wave_ev[1 + w]) != cudaSuccess) {
+                rc = fail(AGP_ECUDA, "reading the wave events");
+                break;
+            }
+            const size_t end = std::min(lanes.size(), (w + 1) * (size_t)G);
+            for (size_t i = w * (size_t)G; i < end; ++i) {
+                float &d = job.times[lanes[i].query].done_ms;
+                d = std::max(d, ms);
+            }
+        }
     }
     if (rc != AGP_OK) {
         if (!ctx->ws) drop_workspace(g);
@@ -1608,11 +1881,12 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     if (!x_off || !pi_out) return fail(AGP_EINVAL, "x_off / pi_out NULL");
     if (ld_out < g->n) return fail(AGP_EINVAL, "ld_out < n");
     if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
-                  AGP_EPS_ABSOLUTE | kOffsetsOnHost))
+                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | kOffsetsOnHost))
         return fail(AGP_EINVAL, "unknown flag");
     // offsets on the device only when the inputs are and the caller did not pass them from the host
     const bool off_dev = (flags & AGP_INPUT_ON_DEVICE) && !(flags & kOffsetsOnHost);
-    if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
+    if ((flags & (AGP_COLLECT_STATS | AGP_QUERY_TIMES)) && !stats)
+        return fail(AGP_EINVAL, "AGP_COLLECT_STATS / AGP_QUERY_TIMES need stats");
     for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     const bool plain = flags & AGP_PLAIN;
@@ -1705,7 +1979,7 @@ int run_queries(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_
         for (int part = 0; part < 2; ++part)
             if (norms[2 * q + part] > 0.0) lanes.push_back(LaneSpec{q, part, norms[2 * q + part], n_params == 1 ? 0 : q});
     Workspace *ws = ctx->ws;
-    if (!ws) AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<size_t>(std::max<size_t>(1, lanes.size()), (size_t)wave_lanes(g)), &ws));
+    if (!ws) AGP_TRY(ensure_workspace(g, (int)std::min<size_t>(std::max<size_t>(1, lanes.size()), (size_t)wave_lanes(g)), plain, &ws));
 
     // --- output rows start at zero
     float *out = pi_out;
@@ -1729,6 +2003,7 @@ int run_queries(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_
     // from the stream (seed, q), so that they do not repeat one another's draws on common nodes
     job.stream_base_is_query = (n_params == 1) ? 1 : 0;
     job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
+    if (flags & AGP_QUERY_TIMES) job.times = stats;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.assign(2 * (size_t)Q, -1);
         for (int l = 0; l < count; ++l) aux[2 * lanes[first + l].query + lanes[first + l].part] = l;
@@ -1776,9 +2051,10 @@ int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
     if (ldx < n || ld_out < n) return fail(AGP_EINVAL, "ldx and ld_out must be >= n");
     if (n > 0 && (!X || !pi_out)) return fail(AGP_EINVAL, "X / pi_out NULL");
     if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
-                  AGP_EPS_ABSOLUTE | AGP_DENSE_BF16))
+                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | AGP_DENSE_BF16))
         return fail(AGP_EINVAL, "unknown flag");
-    if ((flags & AGP_COLLECT_STATS) && !stats) return fail(AGP_EINVAL, "AGP_COLLECT_STATS needs stats");
+    if ((flags & (AGP_COLLECT_STATS | AGP_QUERY_TIMES)) && !stats)
+        return fail(AGP_EINVAL, "AGP_COLLECT_STATS / AGP_QUERY_TIMES need stats");
     for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     if (n == 0) return AGP_OK;
@@ -1845,7 +2121,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     const bool plain = flags & AGP_PLAIN;
     const int64_t n = g->n;
     Workspace *ws = ctx->ws;
-    if (!ws) AGP_TRY(ensure_workspace(g, plain ? 1 : (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), &ws));
+    if (!ws) AGP_TRY(ensure_workspace(g, (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), plain, &ws));
     // column norms of the sign parts
     const size_t norm_b = sizeof(double) * 2 * d;
     AGP_TRY(grow(ctx->stage, ctx->stage_bytes, norm_b + 256));

@@ -1,16 +1,20 @@
 // serve.cu -- continuous-batching server: admission into lanes, shared level sweeps, completion.
 //
-// The server owns a lane workspace (its "slots") and a host thread that drives the device on the
-// server's stream. One sweep = one level of Algorithm 2 for every admitted lane (the captured
-// expand/push/sample/level-end graph); lanes carry their own level, coefficients, L and random key,
-// so requests admitted at different times share sweeps. Between sweeps the thread
-//   1. admits waiting requests (cost-aware or FIFO) while free slots and result memory allow, seeds
-//      them into the current frontier and starts them at level 0,
-//   2. runs one sweep,
-//   3. reads the lanes' levels back; a lane whose level became -1 has reserved its last level, and
-//      a request whose lanes are all finished completes (its result is copied to the host first
-//      when results live there).
-// Waits of host threads on results are bounded by the caller's timeout.
+// The server keeps requests in two pools of lanes ("slots"): light requests and heavy ones, split by
+// the estimated cost of Theorem 4.3's bound. Each pool owns a lane workspace, a stream and a captured
+// sweep: one level of Algorithm 2 for every lane of the pool (compact / expand / push / sample /
+// level end). Lanes carry their own level, coefficients, L and random key, so requests admitted at
+// different times share sweeps. A host thread drives both pools:
+//   1. it admits waiting requests of each pool (cost-aware or FIFO) while the pool's free slots and
+//      the result memory allow, seeds them and starts them at level 0 (the heavy pool only between
+//      its sweeps),
+//   2. it launches the heavy pool's sweep without waiting for it, then runs light sweeps back to
+//      back on the light pool's higher-priority stream, retiring finished light requests after each,
+//   3. when the heavy sweep's event has fired, it retires finished heavy requests and starts the next
+//      heavy sweep.
+// A light request therefore never waits for a sweep of heavy lanes (eps = 1e-9, L = 40: ~140 ms a
+// level on the 4M-node graph), only for its own pool's short sweeps. Waits of host threads on results
+// are bounded by the caller's timeout.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -45,7 +49,7 @@ struct Request {
     bool done = false, cancelled = false, released = false, cut = false, counted = false;
     int lanes_left = 0;
     double cost = 0.0;              // estimated operations (admission priority)
-    bool heavy = false;
+    int pool = 0;                   // kLight or kHeavy
     bool in_queue = false;          // waiting for admission (queue entries of other requests are dropped lazily)
     int refs = 0;                   // queue entries that still point at this request
     bool zombie = false;            // released while queue entries remained: deleted with the last one
@@ -55,46 +59,57 @@ struct Request {
     size_t bytes = 0;
 };
 
-}  // namespace
-}  // namespace agp
+constexpr int kLight = 0, kHeavy = 1;
 
-struct agp_server_s {
-    agp_graph_s *g = nullptr;
-    agp_serve_config_t cfg{};
-    agp::Workspace *ws = nullptr;
-    agp::KArgs A{};
+// One pool of lanes with its own workspace, stream, sweep and seed staging. free_slots is guarded
+// by the server mutex; the rest belongs to the server thread.
+struct Pool {
+    Workspace *ws = nullptr;
+    KArgs A{};
     cudaStream_t stream = nullptr;
     cudaGraphExec_t sweep = nullptr;
-    std::thread th;
-    std::mutex m;
-    std::condition_variable cv_work, cv_done;
-    bool stop = false;
-    uint64_t next_ticket = 1;
-    // Waiting requests. `queue` is in arrival order (FIFO admission, the oldest request, the FIFO
-    // plain mode); `cls[c]` holds the requests of cost class c = floor(log2 cost), in arrival order.
-    // Entries of requests that left the queue (admitted, cancelled, expired) are dropped lazily when
-    // they reach a front, so every operation is O(1) or O(classes) however long the queue grows.
-    std::deque<agp::Request *> queue;
-    std::deque<agp::Request *> cls[64];
-    std::vector<agp::Request *> with_deadline;  // waiting requests that carry a deadline
-    int64_t queued = 0;                          // waiting requests
-    std::unordered_map<uint64_t, agp::Request *> all;
-    std::vector<agp::Request *> slot_owner;
+    cudaEvent_t done = nullptr;    // end of the sweep in flight
+    bool in_flight = false;
+    std::vector<Request *> slot_owner;
     std::vector<int> free_slots;
     std::vector<int32_t> h_level;
-    int64_t result_bytes = 0;
-    int64_t completed = 0, sweeps = 0;
     int active_lanes = 0;
-    int heavy_lanes = 0;
-    // device staging for seeds
     int32_t *d_seed_lane = nullptr, *d_seed_src = nullptr;
-    agp::CoefSpec *d_spec = nullptr;
+    CoefSpec *d_spec = nullptr;
     double *d_w = nullptr;
     size_t d_w_cap = 0;
     uint16_t *d_X = nullptr;
     size_t d_X_cap = 0;
     double *d_norm = nullptr;
     int32_t *d_col = nullptr, *d_part = nullptr, *d_lane_of = nullptr;
+};
+
+}  // namespace
+}  // namespace agp
+
+struct agp_server_s {
+    agp_graph_s *g = nullptr;
+    agp_serve_config_t cfg{};
+    agp::Pool pool[2];
+    int npools = 2;                 // 1 in FIFO-plain mode (its one-lane workspace)
+    std::thread th;
+    std::mutex m;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    // Waiting requests. `queue[p]` is pool p's arrival order (FIFO admission, the oldest request, the
+    // FIFO plain mode); `cls[c]` holds the requests of cost class c = floor(log2 cost), in arrival
+    // order (a class belongs to one pool). Entries of requests that left the queue (admitted,
+    // cancelled, expired) are dropped lazily when they reach a front, so every operation is O(1) or
+    // O(classes) however long the queue grows.
+    std::deque<agp::Request *> queue[2];
+    std::deque<agp::Request *> cls[64];
+    std::vector<agp::Request *> with_deadline;  // waiting requests that carry a deadline
+    int64_t queued = 0;                          // waiting requests
+    int64_t queued_pool[2] = {0, 0};
+    std::unordered_map<uint64_t, agp::Request *> all;
+    int64_t result_bytes = 0;
+    int64_t completed = 0, sweeps = 0;
     void *fifo_stage = nullptr;  // input staging of the FIFO-plain path (never the graph's own)
     size_t fifo_stage_bytes = 0;
     int fatal = AGP_OK;
@@ -104,7 +119,8 @@ namespace agp {
 namespace {
 
 constexpr int kMaxCols = 1024;
-constexpr double kHeavyCost = 1e8;     // estimated operations above which a request is "heavy"
+constexpr int kCostClasses = 64;
+constexpr int kHeavyClass = 27;        // cost classes >= this (estimated operations >= 2^27 ~ 1.3e8) are heavy
 constexpr double kAgingUs = 1e6;       // a request's priority doubles every second it waits
 constexpr double kStarveUs = 30e6;     // a request waiting longer than this reserves the lanes it needs
 
@@ -129,6 +145,12 @@ double estimate_cost(const agp_request_t &r, int64_t nnz)
     return parts * std::min(per_lane, (double)(L + 1) * (double)nnz) + 1e5;
 }
 
+int cost_class(double cost)
+{
+    const int c = cost >= 1.0 ? (int)std::floor(std::log2(cost)) : 0;
+    return std::min(kCostClasses - 1, std::max(0, c));
+}
+
 void finish(agp_server_s *S, Request *q, int status)
 {
     q->status = status;
@@ -138,7 +160,7 @@ void finish(agp_server_s *S, Request *q, int status)
     S->cv_done.notify_all();
 }
 
-int alloc_result(agp_server_s *S, Request *q)
+int alloc_result(agp_server_s *S, Request *q, cudaStream_t st)
 {
     const int64_t n = S->g->n;
     const size_t elems = (size_t)n * (size_t)(q->r.source >= 0 ? 1 : q->r.cols);
@@ -155,7 +177,7 @@ int alloc_result(agp_server_s *S, Request *q)
         q->h_out = nullptr;
         return fail(AGP_ENOMEM, "server: pinned result buffer");
     }
-    AGP_CUDA_TRY(cudaMemsetAsync(q->d_out, 0, q->bytes, S->stream));
+    AGP_CUDA_TRY(cudaMemsetAsync(q->d_out, 0, q->bytes, st));
     return AGP_OK;
 }
 
@@ -167,30 +189,31 @@ void free_result(Request *q)
     q->h_out = nullptr;
 }
 
-// Fill lane `slot` for request q (column `col` / sign `part`, L1 norm `norm`); returns its CoefSpec.
-CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, double norm, int w_off)
+// Fill lane `slot` of pool P for request q (column `col` / sign `part`, L1 norm `norm`); returns its
+// CoefSpec.
+CoefSpec start_lane(Pool &P, Request *q, int slot, int col, int part, double norm, int w_off)
 {
     const agp_params_t &p = q->r.params;
-    LaneParam P{};
-    P.eps_d = (q->r.flags & AGP_REQ_EPS_ABSOLUTE) ? lane_eps_absolute(p.eps, norm) : p.eps;
-    P.eps = (float)P.eps_d;
-    P.a = (float)p.a;
-    P.b = (float)p.b;
-    P.a_d = p.a;
-    P.a_mode = exponent_mode(p.a);
-    P.b_mode = exponent_mode(p.b);
-    P.L = p.L;
-    P.out_row = col;
+    LaneParam L{};
+    L.eps_d = (q->r.flags & AGP_REQ_EPS_ABSOLUTE) ? lane_eps_absolute(p.eps, norm) : p.eps;
+    L.eps = (float)L.eps_d;
+    L.a = (float)p.a;
+    L.b = (float)p.b;
+    L.a_d = p.a;
+    L.a_mode = exponent_mode(p.a);
+    L.b_mode = exponent_mode(p.b);
+    L.L = p.L;
+    L.out_row = col;
     if (q->r.source >= 0) {
-        P.out = q->d_out;
-        P.su = 1;
+        L.out = q->d_out;
+        L.su = 1;
     } else {
-        P.out = q->d_out + col;
-        P.su = q->r.cols;
+        L.out = q->d_out + col;
+        L.su = q->r.cols;
     }
-    lane_key(p.seed, q->r.source >= 0 ? 0ull : (uint64_t)col, part, P.key0, P.key1);
-    lane_param_derive(P);
-    S->ws->h_lanes[slot] = P;
+    lane_key(p.seed, q->r.source >= 0 ? 0ull : (uint64_t)col, part, L.key0, L.key1);
+    lane_param_derive(L);
+    P.ws->h_lanes[slot] = L;
     CoefSpec c{};
     c.lane = slot;
     c.kind = p.kind;
@@ -199,14 +222,6 @@ CoefSpec start_lane(agp_server_s *S, Request *q, int slot, int col, int part, do
     c.w_off = w_off;
     c.scale = (part ? -1.0 : 1.0) * norm;
     return c;
-}
-
-constexpr int kCostClasses = 64;
-
-int cost_class(double cost)
-{
-    const int c = cost >= 1.0 ? (int)std::floor(std::log2(cost)) : 0;
-    return std::min(kCostClasses - 1, std::max(0, c));
 }
 
 // One queue entry of q is gone; a released request is deleted with its last entry.
@@ -231,6 +246,7 @@ void dequeue(agp_server_s *S, Request *q)
     if (q->in_queue) {
         q->in_queue = false;
         --S->queued;
+        --S->queued_pool[q->pool];
     }
 }
 
@@ -245,7 +261,7 @@ void drain_queues(agp_server_s *S)
             unref(q);
         }
     };
-    drain(S->queue);
+    for (auto &d : S->queue) drain(d);
     for (auto &d : S->cls) drain(d);
     for (Request *q : S->with_deadline) {
         q->in_queue = false;
@@ -253,6 +269,7 @@ void drain_queues(agp_server_s *S)
     }
     S->with_deadline.clear();
     S->queued = 0;
+    S->queued_pool[0] = S->queued_pool[1] = 0;
 }
 
 // Waiting requests past their deadline finish with AGP_ETIMEDOUT (cancelled waiting requests are
@@ -271,49 +288,48 @@ void expire_waiting(agp_server_s *S, double t)
     S->with_deadline.resize(keep);
 }
 
-// Admit queued requests while slots and result memory allow. Called by the server thread.
-int admit(agp_server_s *S)
+int need_of(const Request *q) { return q->r.source >= 0 ? 1 : 2 * q->r.cols; }
+
+// Admit queued requests of pool p while its slots and the result memory allow. Called by the server
+// thread, between sweeps of that pool.
+int admit(agp_server_s *S, int p)
 {
+    Pool &P = S->pool[p];
     std::vector<Request *> take;
     std::vector<int> cut;
     {
         std::lock_guard<std::mutex> lk(S->m);
         // cancelled requests in flight: their lanes stop after the next sweep (L lowered to 0, so
         // the lanes only reserve what they hold and finish)
-        for (int sl = 0; sl < (int)S->slot_owner.size(); ++sl) {
-            Request *q = S->slot_owner[sl];
+        for (int sl = 0; sl < (int)P.slot_owner.size(); ++sl) {
+            Request *q = P.slot_owner[sl];
             if (q && q->cancelled && !q->cut) cut.push_back(sl);
         }
-        for (int sl : cut) S->slot_owner[sl]->cut = true;
+        for (int sl : cut) P.slot_owner[sl]->cut = true;
         const double t = now_us();
         expire_waiting(S, t);
         const bool fifo = S->cfg.admission == AGP_ADMIT_FIFO;
-        // The heavy cap keeps lanes for light requests, but it only binds while another heavy
-        // request holds lanes: a request wider than the cap is still admitted once it is alone.
-        auto need_of = [](const Request *q) { return q->r.source >= 0 ? 1 : 2 * q->r.cols; };
-        auto fits = [&](const Request *q) {
-            const int need = need_of(q);
-            if ((int)S->free_slots.size() < need) return false;
-            return !q->heavy || S->heavy_lanes == 0 || S->heavy_lanes + need <= (3 * S->cfg.max_lanes) / 4;
-        };
-        while (S->queued > 0) {
-            // FIFO: the oldest request. Cost-aware: among the oldest request of every cost class
-            // (floor(log2 cost)), the one that fits now with the best aged priority
-            // cost / (1 + seconds waited). Within a class requests start in arrival order. A
-            // request that has waited past kStarveUs goes next under either policy, and nothing
-            // else starts until its slots are free (no starvation of wide requests).
-            pop_dead(S->queue);
-            if (S->queue.empty()) break;
+        const int c_lo = (p == kHeavy) ? kHeavyClass : 0, c_hi = (p == kHeavy) ? kCostClasses : kHeavyClass;
+        auto fits = [&](const Request *q) { return (int)P.free_slots.size() >= need_of(q); };
+        while (S->queued_pool[p] > 0) {
+            // FIFO: the pool's oldest request. Cost-aware: among the oldest request of every cost
+            // class of the pool (floor(log2 cost)), the one that fits now with the best aged priority
+            // cost / (1 + seconds waited). Within a class requests start in arrival order. A request
+            // that has waited past kStarveUs goes next under either policy, and nothing else of its
+            // pool starts until its slots are free (no starvation of wide requests).
+            pop_dead(S->queue[p]);
+            if (S->queue[p].empty()) break;
             Request *q = nullptr;
             std::deque<Request *> *from = nullptr;
-            Request *oldest = S->queue.front();
+            Request *oldest = S->queue[p].front();
             if (fifo || t - oldest->t_submit > kStarveUs) {
                 if (!fits(oldest)) break;
                 q = oldest;
-                from = &S->queue;
+                from = &S->queue[p];
             } else {
                 double best = 0.0;
-                for (auto &d : S->cls) {
+                for (int c = c_lo; c < c_hi; ++c) {
+                    std::deque<Request *> &d = S->cls[c];
                     pop_dead(d);
                     if (d.empty() || !fits(d.front())) continue;
                     Request *h = d.front();
@@ -335,10 +351,13 @@ int admit(agp_server_s *S)
             q->t_admit = t;
             q->slots.clear();
             for (int k = 0; k < need; ++k) {
-                q->slots.push_back(S->free_slots.back());
-                S->free_slots.pop_back();
+                // the lowest free slot: admitted lanes pack into as few groups of four as possible,
+                // so more of them share row walks
+                auto lo = std::min_element(P.free_slots.begin(), P.free_slots.end());
+                q->slots.push_back(*lo);
+                *lo = P.free_slots.back();
+                P.free_slots.pop_back();
             }
-            if (q->heavy) S->heavy_lanes += need;
             S->result_bytes += bytes;
             q->counted = true;
             take.push_back(q);
@@ -346,7 +365,7 @@ int admit(agp_server_s *S)
     }
     static const int32_t zero_L = 0;
     for (int sl : cut)
-        AGP_CUDA_TRY(cudaMemcpyAsync(&S->ws->lanes[sl].L, &zero_L, sizeof(int32_t), cudaMemcpyHostToDevice, S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(&P.ws->lanes[sl].L, &zero_L, sizeof(int32_t), cudaMemcpyHostToDevice, P.stream));
     if (take.empty()) return AGP_OK;
     std::vector<CoefSpec> specs;
     std::vector<double> wts;
@@ -359,10 +378,10 @@ int admit(agp_server_s *S)
             w_off = (int)wts.size();
             wts.insert(wts.end(), q->w.begin(), q->w.end());
         }
-        int rc = alloc_result(S, q);
+        int rc = alloc_result(S, q, P.stream);
         if (rc != AGP_OK) {
             std::lock_guard<std::mutex> lk(S->m);
-            for (int sl : q->slots) S->free_slots.push_back(sl);
+            for (int sl : q->slots) P.free_slots.push_back(sl);
             S->result_bytes -= (int64_t)q->bytes;
             q->slots.clear();
             finish(S, q, rc);
@@ -370,66 +389,65 @@ int admit(agp_server_s *S)
         }
         if (q->r.source >= 0) {
             const int slot = q->slots[0];
-            specs.push_back(start_lane(S, q, slot, 0, 0, 1.0, w_off));
+            specs.push_back(start_lane(P, q, slot, 0, 0, 1.0, w_off));
             seed_lane.push_back(slot);
             seed_src.push_back(q->r.source);
             start.push_back(slot);
-            S->slot_owner[slot] = q;
+            P.slot_owner[slot] = q;
             q->lanes_left = 1;
             continue;
         }
         // feature block: column norms of the sign parts decide which lanes run
         const int cols = q->r.cols;
         const bool x_dev = q->r.flags & AGP_REQ_X_ON_DEVICE;
-        const uint16_t *X = x_dev ? q->r.X : S->d_X;
+        const uint16_t *X = x_dev ? q->r.X : P.d_X;
         const int64_t ldx = x_dev ? q->r.ldx : cols;
         const size_t xb = x_dev ? 0 : sizeof(uint16_t) * (size_t)S->g->n * cols;
-        if (xb > S->d_X_cap) {
-            cudaFree(S->d_X);
-            S->d_X = nullptr;
-            S->d_X_cap = 0;
-            if (cudaMalloc((void **)&S->d_X, xb) != cudaSuccess) {
+        if (xb > P.d_X_cap) {
+            cudaFree(P.d_X);
+            P.d_X = nullptr;
+            P.d_X_cap = 0;
+            if (cudaMalloc((void **)&P.d_X, xb) != cudaSuccess) {
                 cudaGetLastError();
                 std::lock_guard<std::mutex> lk(S->m);
-                for (int sl : q->slots) S->free_slots.push_back(sl);
+                for (int sl : q->slots) P.free_slots.push_back(sl);
                 S->result_bytes -= (int64_t)q->bytes;
                 free_result(q);
                 finish(S, q, fail(AGP_ENOMEM, "server: feature staging"));
                 continue;
             }
-            S->d_X_cap = xb;
+            P.d_X_cap = xb;
         }
         if (!x_dev) {
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_X, q->X.data(), xb, cudaMemcpyHostToDevice, S->stream));
-            X = S->d_X;
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.d_X, q->X.data(), xb, cudaMemcpyHostToDevice, P.stream));
+            X = P.d_X;
         }
-        AGP_CUDA_TRY(cudaMemsetAsync(S->d_norm, 0, sizeof(double) * 2 * cols, S->stream));
-        launch_colnorms_bf16(X, S->g->n, cols, ldx, S->d_norm, S->stream);
+        AGP_CUDA_TRY(cudaMemsetAsync(P.d_norm, 0, sizeof(double) * 2 * cols, P.stream));
+        launch_colnorms_bf16(X, S->g->n, cols, ldx, P.d_norm, P.stream);
         std::vector<double> norms(2 * cols);
-        AGP_CUDA_TRY(cudaMemcpyAsync(norms.data(), S->d_norm, sizeof(double) * 2 * cols, cudaMemcpyDeviceToHost, S->stream));
-        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(norms.data(), P.d_norm, sizeof(double) * 2 * cols, cudaMemcpyDeviceToHost, P.stream));
+        AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));
         std::vector<int32_t> lane_of, col_of, part_of;
         size_t used = 0;
         for (int c = 0; c < cols; ++c)
             for (int part = 0; part < 2; ++part) {
                 if (!(norms[2 * c + part] > 0.0)) continue;
                 const int slot = q->slots[used++];
-                specs.push_back(start_lane(S, q, slot, c, part, norms[2 * c + part], w_off));
+                specs.push_back(start_lane(P, q, slot, c, part, norms[2 * c + part], w_off));
                 lane_of.push_back(slot);
                 col_of.push_back(c);
                 part_of.push_back(part);
                 start.push_back(slot);
-                S->slot_owner[slot] = q;
+                P.slot_owner[slot] = q;
             }
         {
             std::lock_guard<std::mutex> lk(S->m);
             for (size_t k = used; k < q->slots.size(); ++k) give_back.push_back(q->slots[k]);
-            if (q->heavy) S->heavy_lanes -= (int)(q->slots.size() - used);
             q->slots.resize(used);
         }
         q->lanes_left = (int)used;
         if (used == 0) {
-            AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+            AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));
             if (q->h_out) std::memset(q->h_out, 0, q->bytes);
             std::lock_guard<std::mutex> lk(S->m);
             finish(S, q, AGP_OK);
@@ -437,116 +455,160 @@ int admit(agp_server_s *S)
         }
         // parameters and coefficients must be on the device before the dense seed
         for (size_t k = 0; k < lane_of.size(); ++k)
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->lanes + lane_of[k], S->ws->h_lanes + lane_of[k], sizeof(LaneParam),
-                                         cudaMemcpyHostToDevice, S->stream));
-        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_lane_of, lane_of.data(), sizeof(int32_t) * lane_of.size(), cudaMemcpyHostToDevice, S->stream));
-        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_col, col_of.data(), sizeof(int32_t) * col_of.size(), cudaMemcpyHostToDevice, S->stream));
-        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_part, part_of.data(), sizeof(int32_t) * part_of.size(), cudaMemcpyHostToDevice, S->stream));
-        launch_seed_dense_bf16(S->A, X, ldx, S->d_lane_of, S->d_col, S->d_part, S->d_norm, (int)lane_of.size(), S->stream);
-        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));  // d_X and the seed staging are reused
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.ws->lanes + lane_of[k], P.ws->h_lanes + lane_of[k], sizeof(LaneParam),
+                                         cudaMemcpyHostToDevice, P.stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(P.d_lane_of, lane_of.data(), sizeof(int32_t) * lane_of.size(), cudaMemcpyHostToDevice, P.stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(P.d_col, col_of.data(), sizeof(int32_t) * col_of.size(), cudaMemcpyHostToDevice, P.stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(P.d_part, part_of.data(), sizeof(int32_t) * part_of.size(), cudaMemcpyHostToDevice, P.stream));
+        launch_seed_dense_bf16(P.A, X, ldx, P.d_lane_of, P.d_col, P.d_part, P.d_norm, (int)lane_of.size(), P.stream);
+        AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));  // d_X and the seed staging are reused
     }
     if (!give_back.empty()) {
         std::lock_guard<std::mutex> lk(S->m);
-        for (int sl : give_back) S->free_slots.push_back(sl);
+        for (int sl : give_back) P.free_slots.push_back(sl);
     }
     if (!specs.empty()) {
         // lane parameters, coefficients and levels
         for (const CoefSpec &c : specs)
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->lanes + c.lane, S->ws->h_lanes + c.lane, sizeof(LaneParam),
-                                         cudaMemcpyHostToDevice, S->stream));
-        if (wts.size() > S->d_w_cap) {
-            cudaFree(S->d_w);
-            if (cudaMalloc((void **)&S->d_w, sizeof(double) * wts.size()) != cudaSuccess) {
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.ws->lanes + c.lane, P.ws->h_lanes + c.lane, sizeof(LaneParam),
+                                         cudaMemcpyHostToDevice, P.stream));
+        if (wts.size() > P.d_w_cap) {
+            cudaFree(P.d_w);
+            if (cudaMalloc((void **)&P.d_w, sizeof(double) * wts.size()) != cudaSuccess) {
                 cudaGetLastError();
-                S->d_w = nullptr;
-                S->d_w_cap = 0;
+                P.d_w = nullptr;
+                P.d_w_cap = 0;
                 return fail(AGP_ENOMEM, "server: weight staging");
             }
-            S->d_w_cap = wts.size();
+            P.d_w_cap = wts.size();
         }
-        if (!wts.empty()) AGP_CUDA_TRY(cudaMemcpyAsync(S->d_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, S->stream));
-        AGP_CUDA_TRY(cudaMemcpyAsync(S->d_spec, specs.data(), sizeof(CoefSpec) * specs.size(), cudaMemcpyHostToDevice, S->stream));
-        launch_coef(S->d_spec, S->d_w, S->ws->coef, (int)specs.size(), S->stream);
+        if (!wts.empty()) AGP_CUDA_TRY(cudaMemcpyAsync(P.d_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, P.stream));
+        AGP_CUDA_TRY(cudaMemcpyAsync(P.d_spec, specs.data(), sizeof(CoefSpec) * specs.size(), cudaMemcpyHostToDevice, P.stream));
+        launch_coef(P.d_spec, P.d_w, P.ws->coef, (int)specs.size(), P.stream);
         const int32_t zero = 0;
         for (int32_t sl : start)
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->ws->level + sl, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, S->stream));
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.ws->level + sl, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, P.stream));
         if (!seed_lane.empty()) {
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_seed_lane, seed_lane.data(), sizeof(int32_t) * seed_lane.size(), cudaMemcpyHostToDevice, S->stream));
-            AGP_CUDA_TRY(cudaMemcpyAsync(S->d_seed_src, seed_src.data(), sizeof(int32_t) * seed_src.size(), cudaMemcpyHostToDevice, S->stream));
-            launch_seed_sources(S->A, S->d_seed_lane, S->d_seed_src, (int)seed_lane.size(), S->stream);
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.d_seed_lane, seed_lane.data(), sizeof(int32_t) * seed_lane.size(), cudaMemcpyHostToDevice, P.stream));
+            AGP_CUDA_TRY(cudaMemcpyAsync(P.d_seed_src, seed_src.data(), sizeof(int32_t) * seed_src.size(), cudaMemcpyHostToDevice, P.stream));
+            launch_seed_sources(P.A, P.d_seed_lane, P.d_seed_src, (int)seed_lane.size(), P.stream);
         }
         AGP_CUDA_TRY(cudaGetLastError());
-        AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));  // host staging vectors go out of scope
-        S->active_lanes += (int)start.size();
+        AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));  // host staging vectors go out of scope
+        P.active_lanes += (int)start.size();
     }
     return AGP_OK;
 }
 
-// Lanes whose level went to -1 are finished; complete requests whose lanes are all finished.
-int retire(agp_server_s *S)
+// Lanes of pool p whose level went to -1 are finished; complete requests whose lanes are all
+// finished. Synchronises the pool's stream.
+int retire(agp_server_s *S, int p)
 {
-    AGP_CUDA_TRY(cudaMemcpyAsync(S->h_level.data(), S->ws->level, sizeof(int32_t) * S->ws->G, cudaMemcpyDeviceToHost, S->stream));
-    AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+    Pool &P = S->pool[p];
+    AGP_CUDA_TRY(cudaMemcpyAsync(P.h_level.data(), P.ws->level, sizeof(int32_t) * P.ws->G, cudaMemcpyDeviceToHost, P.stream));
+    AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));
     std::vector<Request *> ready;
-    for (int sl = 0; sl < S->ws->G; ++sl) {
-        Request *q = S->slot_owner[sl];
-        if (!q || S->h_level[sl] >= 0) continue;
-        S->slot_owner[sl] = nullptr;
-        --S->active_lanes;
+    for (int sl = 0; sl < P.ws->G; ++sl) {
+        Request *q = P.slot_owner[sl];
+        if (!q || P.h_level[sl] >= 0) continue;
+        P.slot_owner[sl] = nullptr;
+        --P.active_lanes;
         {
             std::lock_guard<std::mutex> lk(S->m);
-            S->free_slots.push_back(sl);
-            if (q->heavy) --S->heavy_lanes;
+            P.free_slots.push_back(sl);
         }
         if (--q->lanes_left == 0) ready.push_back(q);
     }
     for (Request *q : ready)
-        if (q->h_out) AGP_CUDA_TRY(cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, S->stream));
-    if (!ready.empty()) AGP_CUDA_TRY(cudaStreamSynchronize(S->stream));
+        if (q->h_out) AGP_CUDA_TRY(cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, P.stream));
+    if (!ready.empty()) AGP_CUDA_TRY(cudaStreamSynchronize(P.stream));
     std::lock_guard<std::mutex> lk(S->m);
     for (Request *q : ready) finish(S, q, q->cancelled ? AGP_ECANCELED : AGP_OK);
     return AGP_OK;
 }
 
+int launch_sweep(agp_server_s *S, int p)
+{
+    Pool &P = S->pool[p];
+    AGP_CUDA_TRY(cudaGraphLaunch(P.sweep, P.stream));
+    AGP_CUDA_TRY(cudaEventRecord(P.done, P.stream));
+    P.in_flight = true;
+    std::lock_guard<std::mutex> lk(S->m);
+    ++S->sweeps;
+    return AGP_OK;
+}
+
 void run_fifo_plain(agp_server_s *S, Request *q)
 {
-    int rc = alloc_result(S, q);
+    Pool &P = S->pool[0];
+    int rc = alloc_result(S, q, P.stream);
     if (rc == AGP_OK) {
         q->t_admit = now_us();
         // the server's own one-lane workspace and staging: the graph's buffers stay the caller's
-        ExecCtx ctx{S->ws, &S->fifo_stage, &S->fifo_stage_bytes};
+        ExecCtx ctx{P.ws, &S->fifo_stage, &S->fifo_stage_bytes};
         if (q->r.source >= 0) {
             const int64_t off[2] = {0, 1};
             rc = query_batch_ctx(S->g, &ctx, &q->r.params, 1, 1, off, &q->r.source, nullptr, q->d_out, S->g->n,
-                                 AGP_OUTPUT_ON_DEVICE | AGP_PLAIN, nullptr, S->stream);
+                                 AGP_OUTPUT_ON_DEVICE | AGP_PLAIN, nullptr, P.stream);
         } else if (q->r.flags & AGP_REQ_X_ON_DEVICE) {
             rc = feature_propagate_ctx(S->g, &ctx, &q->r.params, q->r.X, q->r.cols, q->r.ldx, q->d_out, q->r.cols,
-                                       AGP_PLAIN, S->stream);
+                                       AGP_PLAIN, P.stream);
         } else {
             const size_t xb = sizeof(uint16_t) * (size_t)S->g->n * q->r.cols;
-            if (xb > S->d_X_cap) {
-                cudaFree(S->d_X);
-                S->d_X_cap = 0;
-                if (cudaMalloc((void **)&S->d_X, xb) != cudaSuccess) {
+            if (xb > P.d_X_cap) {
+                cudaFree(P.d_X);
+                P.d_X_cap = 0;
+                if (cudaMalloc((void **)&P.d_X, xb) != cudaSuccess) {
                     cudaGetLastError();
-                    S->d_X = nullptr;
+                    P.d_X = nullptr;
                     rc = fail(AGP_ENOMEM, "server: feature staging");
                 } else {
-                    S->d_X_cap = xb;
+                    P.d_X_cap = xb;
                 }
             }
-            if (rc == AGP_OK && cudaMemcpyAsync(S->d_X, q->X.data(), xb, cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+            if (rc == AGP_OK && cudaMemcpyAsync(P.d_X, q->X.data(), xb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
                 rc = fail(AGP_ECUDA, "server: feature copy");
             if (rc == AGP_OK)
-                rc = feature_propagate_ctx(S->g, &ctx, &q->r.params, S->d_X, q->r.cols, q->r.cols, q->d_out, q->r.cols,
-                                           AGP_PLAIN, S->stream);
+                rc = feature_propagate_ctx(S->g, &ctx, &q->r.params, P.d_X, q->r.cols, q->r.cols, q->d_out, q->r.cols,
+                                           AGP_PLAIN, P.stream);
         }
-        if (rc == AGP_OK && q->h_out && cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, S->stream) != cudaSuccess)
+        if (rc == AGP_OK && q->h_out && cudaMemcpyAsync(q->h_out, q->d_out, q->bytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
             rc = fail(AGP_ECUDA, "server: result copy");
-        if (cudaStreamSynchronize(S->stream) != cudaSuccess && rc == AGP_OK) rc = fail(AGP_ECUDA, "server: sync");
+        if (cudaStreamSynchronize(P.stream) != cudaSuccess && rc == AGP_OK) rc = fail(AGP_ECUDA, "server: sync");
     }
     std::lock_guard<std::mutex> lk(S->m);
     finish(S, q, q->cancelled ? AGP_ECANCELED : rc);
+}
+
+// One step of the batched server thread: keep one heavy sweep in flight (retiring and admitting
+// between its sweeps, never waiting for it here), then admit, sweep and retire the light pool.
+// *busy: some pool has work.
+int serve_step(agp_server_s *S, bool *busy)
+{
+    Pool &Lp = S->pool[kLight], &Hp = S->pool[kHeavy];
+    *busy = false;
+    if (Hp.in_flight) {
+        const cudaError_t e = cudaEventQuery(Hp.done);
+        if (e == cudaSuccess) {
+            Hp.in_flight = false;
+            AGP_TRY(retire(S, kHeavy));
+        } else if (e != cudaErrorNotReady) {
+            return fail(AGP_ECUDA, std::string("server: heavy sweep: ") + cudaGetErrorString(e));
+        }
+    }
+    if (!Hp.in_flight) {
+        AGP_TRY(admit(S, kHeavy));
+        if (Hp.active_lanes > 0) AGP_TRY(launch_sweep(S, kHeavy));
+    }
+    *busy = Hp.in_flight;
+    AGP_TRY(admit(S, kLight));
+    if (Lp.active_lanes > 0) {
+        AGP_TRY(launch_sweep(S, kLight));
+        AGP_TRY(retire(S, kLight));  // synchronises the light stream
+        Lp.in_flight = false;
+        *busy = true;
+    }
+    return AGP_OK;
 }
 
 void server_main(agp_server_s *S)
@@ -560,30 +622,31 @@ void server_main(agp_server_s *S)
                 S->cv_work.wait(lk, [&] { return S->stop || S->queued > 0; });
                 if (S->stop) return;
                 expire_waiting(S, now_us());
-                pop_dead(S->queue);
-                if (S->queue.empty()) continue;
-                q = S->queue.front();
-                S->queue.pop_front();
+                pop_dead(S->queue[0]);
+                if (S->queue[0].empty()) continue;
+                q = S->queue[0].front();
+                S->queue[0].pop_front();
                 unref(q);
                 dequeue(S, q);
             }
             run_fifo_plain(S, q);
         }
     }
+    bool busy = true;
     while (true) {
         {
             std::unique_lock<std::mutex> lk(S->m);
             if (S->stop) return;
-            if (S->active_lanes == 0 && S->queued == 0)
+            if (!busy && S->queued == 0) {
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || S->queued > 0; });
+            } else if (S->pool[kLight].active_lanes == 0 && S->pool[kHeavy].in_flight && S->queued_pool[kLight] == 0) {
+                // only a heavy sweep runs: wake for a light arrival, or poll its event again shortly
+                S->cv_work.wait_for(lk, std::chrono::microseconds(200),
+                                    [&] { return S->stop || S->queued_pool[kLight] > 0; });
+            }
             if (S->stop) return;
         }
-        int rc = admit(S);
-        if (rc == AGP_OK && S->active_lanes > 0) {
-            if (cudaGraphLaunch(S->sweep, S->stream) != cudaSuccess) rc = fail(AGP_ECUDA, "server: sweep launch");
-            ++S->sweeps;
-            if (rc == AGP_OK) rc = retire(S);
-        }
+        const int rc = serve_step(S, &busy);
         if (rc != AGP_OK) {
             // a device error ends the server: fail everything pending and in flight
             std::lock_guard<std::mutex> lk(S->m);
@@ -594,6 +657,56 @@ void server_main(agp_server_s *S)
             return;
         }
     }
+}
+
+int create_pool(agp_server_s *S, Pool &P, int lanes, int W, int priority)
+{
+    agp_graph_s *g = S->g;
+    AGP_TRY(create_workspace(g, lanes, W, &P.ws));
+    AGP_CUDA_TRY(cudaStreamCreateWithPriority(&P.stream, cudaStreamNonBlocking, priority));
+    AGP_CUDA_TRY(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
+    // every slot may hold work: the compaction scans all of them
+    const unsigned int used = (unsigned int)P.ws->G;
+    AGP_CUDA_TRY(cudaMemcpy(&P.ws->ctrl->lanes_used, &used, sizeof(used), cudaMemcpyHostToDevice));
+    P.A = make_args(g, P.ws, 0);
+    if (S->cfg.mode != AGP_SERVE_FIFO_PLAIN) AGP_TRY(capture_levels(P.A, 1, &P.sweep));
+    auto dalloc = [&](void **p, size_t b) -> int {
+        if (cudaMalloc(p, b) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(AGP_ENOMEM, "server staging");
+        }
+        return AGP_OK;
+    };
+    const int G = P.ws->G;
+    AGP_TRY(dalloc((void **)&P.d_seed_lane, sizeof(int32_t) * G));
+    AGP_TRY(dalloc((void **)&P.d_seed_src, sizeof(int32_t) * G));
+    AGP_TRY(dalloc((void **)&P.d_spec, sizeof(CoefSpec) * G));
+    AGP_TRY(dalloc((void **)&P.d_norm, sizeof(double) * 2 * kMaxCols));
+    AGP_TRY(dalloc((void **)&P.d_col, sizeof(int32_t) * 2 * kMaxCols));
+    AGP_TRY(dalloc((void **)&P.d_part, sizeof(int32_t) * 2 * kMaxCols));
+    AGP_TRY(dalloc((void **)&P.d_lane_of, sizeof(int32_t) * 2 * kMaxCols));
+    P.slot_owner.assign(G, nullptr);
+    P.h_level.assign(G, -1);
+    for (int sl = G - 1; sl >= 0; --sl) P.free_slots.push_back(sl);
+    return AGP_OK;
+}
+
+void destroy_pool(Pool &P)
+{
+    if (P.sweep) cudaGraphExecDestroy(P.sweep);
+    free_workspace(P.ws);
+    cudaFree(P.d_seed_lane);
+    cudaFree(P.d_seed_src);
+    cudaFree(P.d_spec);
+    cudaFree(P.d_w);
+    cudaFree(P.d_X);
+    cudaFree(P.d_norm);
+    cudaFree(P.d_col);
+    cudaFree(P.d_part);
+    cudaFree(P.d_lane_of);
+    if (P.done) cudaEventDestroy(P.done);
+    if (P.stream) cudaStreamDestroy(P.stream);
+    P = Pool{};
 }
 
 }  // namespace
@@ -614,41 +727,26 @@ int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **o
     // default: room for the widest feature block (2 x 64 columns) next to 8 waves of queries
     int lanes = c.max_lanes > 0 ? c.max_lanes : std::min(lane_capacity(g), std::max(8 * wave_lanes(g), 128));
     lanes = std::max(lanes, 2);
-    if (c.mode == AGP_SERVE_FIFO_PLAIN) lanes = 1;
+    // batched slots come in groups of four lanes that share row walks (the level pipeline's layout)
+    int W = 4;
+    if (c.mode == AGP_SERVE_FIFO_PLAIN) lanes = W = 1;
+    else lanes = (lanes + 3) / 4 * 4;
     c.max_lanes = lanes;
     S->cfg = c;
-    int rc = create_workspace(g, lanes, &S->ws);
-    if (rc == AGP_OK && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) rc = fail(AGP_ECUDA, "server stream");
-    if (rc == AGP_OK) {
-        // every slot may hold work: the compaction scans all of them
-        const unsigned int used = (unsigned int)lanes;
-        if (cudaMemcpy(&S->ws->ctrl->lanes_used, &used, sizeof(used), cudaMemcpyHostToDevice) != cudaSuccess)
-            rc = fail(AGP_ECUDA, "server control block");
+    int lo = 0, hi = 0;
+    int rc = AGP_OK;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+        cudaGetLastError();
+        lo = hi = 0;
     }
-    if (rc == AGP_OK) {
-        S->A = make_args(g, S->ws, 0);
-        rc = capture_levels(S->A, 1, &S->sweep);
-    }
-    auto dalloc = [&](void **p, size_t b) {
-        if (rc == AGP_OK && cudaMalloc(p, b) != cudaSuccess) {
-            cudaGetLastError();
-            rc = fail(AGP_ENOMEM, "server staging");
-        }
-    };
-    dalloc((void **)&S->d_seed_lane, sizeof(int32_t) * lanes);
-    dalloc((void **)&S->d_seed_src, sizeof(int32_t) * lanes);
-    dalloc((void **)&S->d_spec, sizeof(CoefSpec) * lanes);
-    dalloc((void **)&S->d_norm, sizeof(double) * 2 * kMaxCols);
-    dalloc((void **)&S->d_col, sizeof(int32_t) * 2 * kMaxCols);
-    dalloc((void **)&S->d_part, sizeof(int32_t) * 2 * kMaxCols);
-    dalloc((void **)&S->d_lane_of, sizeof(int32_t) * 2 * kMaxCols);
+    S->npools = (c.mode == AGP_SERVE_FIFO_PLAIN) ? 1 : 2;
+    // the light pool's stream gets the highest priority: its short kernels are scheduled ahead of the
+    // heavy sweep's blocks as SMs free up
+    for (int p = 0; p < S->npools && rc == AGP_OK; ++p) rc = create_pool(S, S->pool[p], lanes, W, p == kLight ? hi : lo);
     if (rc != AGP_OK) {
         serve_destroy(S);
         return rc;
     }
-    S->slot_owner.assign(lanes, nullptr);
-    S->h_level.assign(lanes, -1);
-    for (int sl = lanes - 1; sl >= 0; --sl) S->free_slots.push_back(sl);
     S->th = std::thread(server_main, S);
     *out = S;
     return AGP_OK;
@@ -685,7 +783,8 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
     }
     q->t_submit = now_us();
     q->cost = estimate_cost(q->r, S->g->nnz);
-    q->heavy = q->cost > kHeavyCost;
+    const int cc = cost_class(q->cost);
+    q->pool = (S->npools == 2 && cc >= kHeavyClass) ? kHeavy : kLight;
     {
         std::lock_guard<std::mutex> lk(S->m);
         if (S->fatal != AGP_OK) {
@@ -696,8 +795,9 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
         S->all[q->ticket] = q;
         q->in_queue = true;
         ++S->queued;
-        S->queue.push_back(q);
-        S->cls[cost_class(q->cost)].push_back(q);
+        ++S->queued_pool[q->pool];
+        S->queue[q->pool].push_back(q);
+        S->cls[cc].push_back(q);
         q->refs = 2;
         if (q->r.deadline_us > 0) {
             S->with_deadline.push_back(q);
@@ -798,7 +898,7 @@ int serve_stats(agp_server_s *S, int64_t *completed, int64_t *sweeps, int32_t *l
     std::lock_guard<std::mutex> lk(S->m);
     if (completed) *completed = S->completed;
     if (sweeps) *sweeps = S->sweeps;
-    if (lanes_active) *lanes_active = S->active_lanes;
+    if (lanes_active) *lanes_active = S->pool[0].active_lanes + S->pool[1].active_lanes;
     if (queued) *queued = (int32_t)std::min<int64_t>(S->queued, INT32_MAX);
     return AGP_OK;
 }
@@ -812,7 +912,8 @@ int serve_destroy(agp_server_s *S)
     }
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
-    if (S->stream) cudaStreamSynchronize(S->stream);
+    for (Pool &P : S->pool)
+        if (P.stream) cudaStreamSynchronize(P.stream);
     {
         std::lock_guard<std::mutex> lk(S->m);
         drain_queues(S);  // released requests go with their last queue entry
@@ -823,19 +924,8 @@ int serve_destroy(agp_server_s *S)
         }
         S->all.clear();
     }
-    if (S->sweep) cudaGraphExecDestroy(S->sweep);
-    free_workspace(S->ws);
-    cudaFree(S->d_seed_lane);
-    cudaFree(S->d_seed_src);
-    cudaFree(S->d_spec);
-    cudaFree(S->d_w);
-    cudaFree(S->d_X);
-    cudaFree(S->d_norm);
-    cudaFree(S->d_col);
-    cudaFree(S->d_part);
-    cudaFree(S->d_lane_of);
+    for (Pool &P : S->pool) destroy_pool(P);
     cudaFree(S->fifo_stage);
-    if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
     return AGP_OK;
 }

@@ -73,14 +73,18 @@ def test_signed_dense_rows_fp32_and_bf16(agp, graph):
 
 
 def test_dense_eps_unbiased_mass(agp, graph):
-    """eps > 0, 200 seeds of PageRank from x = 1/n: a = 0, b = 1 is column-stochastic, so every run's
-    expected mass is sum_{i<=L} w_i (the truncated PPR mass, Lemma 4.1)."""
+    """eps > 0, 200 seeds of PageRank from x = 1/n: every run's expected total mass is that of the
+    exact propagation (Lemma 4.1). It is below sum_{i<=L} w_i on this graph: R-MAT leaves isolated
+    nodes, whose share of x is reserved once and never pushed (D^-1 := 0 there)."""
     n, g, og = graph
     N = 200
+    L, alpha = 20, 0.15
     X = torch.full((N, n), 1.0 / n, dtype=torch.float32, device="cuda")
-    out, _ = agp.query_dense(g, [agp.ppr(0.15, 20, 1e-6, seed=k) for k in range(N)], X)
+    out, _ = agp.query_dense(g, [agp.ppr(alpha, L, 1e-6, seed=k) for k in range(N)], X)
     mass = out.sum(1, dtype=torch.float64).cpu().numpy()
-    want = 1.0 - 0.85 ** 21
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    want = oracle.basic(og, 0.0, 1.0, L, w, Y, np.full(n, 1.0 / n)).sum()
+    assert want < 1.0 - (1 - alpha) ** (L + 1) - 0.01  # the isolated nodes' loss is visible
     assert abs(mass.mean() - want) <= 4.0 * mass.std(ddof=1) / np.sqrt(N) + 1e-6
     assert np.all(np.abs(mass - want) < 0.05)
 

@@ -351,6 +351,7 @@ def test_alone_equals_batched_and_plain(agp, rmat14):
     # same draws everywhere; a summation-order flip of one sampling decision (rare) leaves the two
     # results equally accurate against the exact propagation
     drifted = [(x, y, i) for x, y, i in pairs if not close(x, y)]
+    print(f"[drift] alone / batched / plain: {len(drifted)} of {len(pairs)} pairs differ beyond 1e-5")
     assert len(drifted) <= len(pairs) // 2
     if drifted:
         exact, _ = agp.query_sources(g, [agp.ppr(0.2, 20, 0.0) for _ in srcs], srcs)
