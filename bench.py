@@ -614,13 +614,16 @@ def run_serve(args, wl):
         deadline = t0 + args.serve_warmup + args.duration + args.drain
         # a request counts when it completes inside the measured window (after the warm-up), whenever
         # it arrived: under overload the oldest waiting requests are the ones that finish
+        # the window closes at warm-up + duration + drain; only requests that completed by then count
+        end_s = args.serve_warmup + args.duration + args.drain
         lat, done, done_arrived = [], 0, 0
         for (tk, kind), tr in zip(tickets, trace):
-            left = max(0.0, deadline - time.perf_counter())
-            r = srv.wait(tk, timeout_us=int(left * 1e6))
+            left = deadline - time.perf_counter()
+            r = srv.wait(tk, timeout_us=int(left * 1e6)) if left > 0 else srv.poll(tk)
             if r is None:
                 continue
-            if r.status == 0 and tr[0] + r.latency_us / 1e6 >= args.serve_warmup:
+            t_end = tr[0] + r.latency_us / 1e6
+            if r.status == 0 and args.serve_warmup <= t_end <= end_s:
                 done += 1
                 done_arrived += tr[0] >= args.serve_warmup
                 lat.append(r.latency_us / 1e3)

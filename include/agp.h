@@ -66,7 +66,8 @@ typedef struct agp_graph_s *agp_graph_t;
 
 #define AGP_ADD_SELF_LOOPS 0x1u  /* add one self-loop per node, counted once in its degree        */
 #define AGP_EDGES_ON_DEVICE 0x2u /* src/dst are device pointers (else host pointers)               */
-#define AGP_DIRECTED 0x4u        /* directed graph: see below                                      */
+#define AGP_DIRECTED 0x4u        /* directed graph, out-neighbour rows: see below                  */
+#define AGP_DIRECTED_IN 0x8u     /* directed graph, in-neighbour rows: see below                   */
 
 /*
  * Build the device CSR of an undirected graph: Section 4 "Pre-sorting adjacency list by degrees".
@@ -81,6 +82,13 @@ typedef struct agp_graph_s *agp_graph_t;
  * pushes along out-edges. Queries on a directed graph need a = 0 (AGP_EINVAL otherwise): a node
  * without out-edges would have d^-a undefined. A node without out-edges keeps what reaches it as
  * reserve and passes nothing on (D^-1 := 0).
+ * AGP_DIRECTED_IN: the untransposed adjacency of the same passage (single-target PPR, a = 1, b = 0):
+ * pi = sum_i w_i (D^-a A D^-b)^i x with (A y)(u) = sum_{v : u -> v} y(v) and D the out-degree matrix.
+ * In push form a node v passes r(v) / (d_v^b d_u^a) to every in-neighbour u (u -> v), so N_v is the
+ * in-neighbour list of v, sorted by (d_u, u), while deg[] stays the out-degree: a row's length
+ * (rowptr[v+1] - rowptr[v], the in-degree) is not its node's degree here. Any a, b is valid (every
+ * push target has an out-edge); a node without out-edges pushes nothing when b > 0 (D^-b := 0).
+ * The two directed flags exclude each other.
  *   n        number of nodes, 0 <= n < 2^31
  *   n_edges  number of input edges (>= 0)
  *   src,dst  n_edges int32 ids each, host or device memory (AGP_EDGES_ON_DEVICE); not retained
@@ -93,7 +101,8 @@ AGP_API int agp_build_graph(int64_t n, int64_t n_edges, const int32_t *src, cons
                     uint32_t flags, int device, void *stream, agp_graph_t *out);
 
 /* Sizes and device arrays of a built graph (library-owned, valid until agp_graph_destroy):
- * rowptr int64[n+1], colidx int32[nnz], deg int32[n]. Any output pointer may be NULL. */
+ * rowptr int64[n+1], colidx int32[nnz], deg int32[n] (row lengths, except with AGP_DIRECTED_IN where
+ * deg holds out-degrees). Any output pointer may be NULL. */
 AGP_API int agp_graph_info(agp_graph_t g, int64_t *n, int64_t *nnz, const int64_t **rowptr,
                    const int32_t **colidx, const int32_t **deg);
 
@@ -114,6 +123,11 @@ AGP_API int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes);
  * at a neighbour leave as one vector reduction. Results do not depend on it (a lane's random draws
  * are its own). The plain path always uses 1. agp_autotune picks it by timing. */
 AGP_API int agp_graph_set_group_width(agp_graph_t g, int32_t width);
+
+/* Columns per tile of exact feature propagation (agp_feature_propagate with eps = 0 on an undirected
+ * graph): 8, 16 or 32 (0 = automatic: the widest whose n x T FP32 residue block stays within 64 MB,
+ * half of L2, at least 8). */
+AGP_API int agp_graph_set_column_tile(agp_graph_t g, int32_t columns);
 
 /* ---- propagation parameters ---------------------------------------------------------------- */
 /* Weight sequences of Table 1. FINITE takes w_0..w_L from `w`; the others are generated with
@@ -232,6 +246,9 @@ AGP_API int agp_query_dense(agp_graph_t g, const agp_params_t *params, int32_t n
  *   Z       device, n rows x d columns of FP32, row stride ldz >= d; fully written
  *   seed    of params: column c part s uses the stream (seed, c, s)
  * d = 0 (or n = 0) returns AGP_OK without touching X or Z, which may then be NULL.
+ * eps = 0 on an undirected graph (without AGP_PLAIN) takes the exact path: Algorithm 1, Z = sum_i w_i
+ * P^i X, computed over tiles of columns (agp_graph_set_column_tile) by pulling over the symmetric rows,
+ * without sign parts or atomics; it keeps two n x T FP32 blocks with the graph.
  * Errors as agp_query_batch.
  */
 AGP_API int agp_feature_propagate(agp_graph_t g, const agp_params_t *params, const uint16_t *X,
@@ -387,6 +404,43 @@ AGP_API int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int3
  */
 AGP_API int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes,
                   const float *c, int32_t *k_out, void *stream);
+
+/*
+ * Local-clustering sweep (Section 6, local clustering with HKPR): the nodes are ordered by
+ * pi(v)/d_v, largest first, and the prefix S_i of least conductance
+ *     Phi(S_i) = cut(S_i) / min(vol(S_i), 2m - vol(S_i)),  vol(S) = sum_{v in S} d_v,
+ * is found. Readings: only nodes with pi(v) > 0 and d_v > 0 are swept; ties on the score go to the
+ * smaller id (the score is the FP64 quotient of the FP32 pi); prefixes run over i = 1..min(swept,
+ * n - 1); a prefix with min(vol, 2m - vol) = 0 is skipped; a self-loop counts once in d_v and never
+ * crosses the cut. The first prefix of least conductance wins.
+ *   g          an undirected graph (AGP_EINVAL for directed ones)
+ *   pi         device, n floats (a row of agp_query_batch output)
+ *   order      device, n int32 or NULL: the swept nodes in order, -1 after them
+ *   phi        device, n - 1 doubles or NULL: Phi(S_i) at [i - 1] for i = 1..min(swept, n - 1), +inf
+ *              where skipped, 0 after
+ *   best_size, best_phi, swept: host outputs (may be NULL): the best prefix size (0 if none
+ *              qualifies, best_phi then NaN) and the number of swept nodes
+ * Allocates device scratch for the call (O(n)) and synchronises `stream`.
+ * Errors: AGP_EINVAL, AGP_ENOMEM, AGP_ECUDA.
+ */
+AGP_API int agp_sweep(agp_graph_t g, const float *pi, int32_t *order, double *phi, int64_t *best_size,
+                      double *best_phi, int64_t *swept, void *stream);
+
+/*
+ * Sparse output: the k largest entries of each of Q result rows (serving and local-clustering
+ * consumers need the top of pi, not a dense n-vector; returning k pairs instead of n floats cuts
+ * device-to-host traffic by n / (2k)). Row q's entries are ordered by value, largest first, ties by
+ * ascending node id (-0 counts as +0); the first k of that order are written to val[q * ldo + j],
+ * idx[q * ldo + j], j < k. Exact: a radix select over the (value, id) order, one CTA per row, then a
+ * sort of the k keys.
+ *   pi       device, Q rows of ld >= n floats (an output of agp_query_batch / agp_query_dense); rows
+ *            must not hold NaN
+ *   k        1 <= k <= min(n, 2048)
+ *   val, idx device, Q rows of ldo >= k entries, caller-owned
+ * Stream-ordered, no synchronisation, no allocation. Errors: AGP_EINVAL, AGP_ECUDA.
+ */
+AGP_API int agp_topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t k, float *val, int32_t *idx,
+                     int64_t ldo, void *stream);
 
 /*
  * Level coefficients of Def. 3.1 as the level pipeline computes them on the device (FP64), for a

@@ -20,17 +20,17 @@ from . import build as _build
 
 __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
-    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "QUERY_TIMES", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "QUERY_TIMES", "topk", "sweep", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
-    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "MAX_LEVELS",
+    "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "DIRECTED_IN", "MAX_LEVELS",
 ]
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 DENSE_BF16, QUERY_TIMES = 0x40, 0x80
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
-ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED = 0x1, 0x2, 0x4
+ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED, DIRECTED_IN = 0x1, 0x2, 0x4, 0x8
 MAX_LEVELS = 64
 
 
@@ -112,6 +112,8 @@ def lib():
             L.agp_threshold.argtypes = [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _vp]
             L.agp_query_dense.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _i64, _vp, _i64, _u32,
                                           C.POINTER(Stats), _vp]
+            L.agp_sweep.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_i64), _vp]
+            L.agp_topk.argtypes = [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _i64, _vp]
             L.agp_coefficients.argtypes = [C.POINTER(Params), _vp, _vp, C.POINTER(_dbl), C.c_int, _vp]
             L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
             L.agp_graph_set_wave_lanes.argtypes = [_vp, _i32]
@@ -120,6 +122,7 @@ def lib():
             L.agp_autotune.argtypes = [_vp, C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _i32,
                                        C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_dbl), _vp]
             L.agp_graph_set_group_width.argtypes = [_vp, _i32]
+            L.agp_graph_set_column_tile.argtypes = [_vp, _i32]
             L.agp_serve_create.argtypes = [_vp, C.POINTER(ServeConfig), C.POINTER(_vp)]
             L.agp_serve_submit.argtypes = [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
             L.agp_serve_poll.argtypes = [_vp, C.c_uint64, C.POINTER(Result)]
@@ -134,7 +137,7 @@ def lib():
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
                       "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense",
-                      "agp_graph_set_group_width"):
+                      "agp_graph_set_group_width", "agp_topk", "agp_sweep", "agp_graph_set_column_tile"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -236,6 +239,10 @@ class Graph:
         """``agp_graph_set_group_width`` (0 = automatic; 1, 2 or 4)."""
         _check("agp_graph_set_group_width", lib().agp_graph_set_group_width(self.handle, int(width)))
 
+    def set_column_tile(self, columns):
+        """``agp_graph_set_column_tile`` (0 = automatic; 8, 16 or 32)."""
+        _check("agp_graph_set_column_tile", lib().agp_graph_set_column_tile(self.handle, int(columns)))
+
     def set_memory_budget(self, nbytes):
         _check("agp_graph_set_memory_budget", lib().agp_graph_set_memory_budget(self.handle, int(nbytes)))
 
@@ -264,8 +271,11 @@ class _CudaArray:
 
 def build_graph(n, src, dst, add_self_loops=False, device=0, stream=None, directed=False):
     """``agp_build_graph``: src/dst are int32 numpy arrays (host) or CUDA tensors (device).
-    directed: edges are src -> dst, rows are out-neighbour lists (AGP_DIRECTED; queries need a = 0)."""
-    flags = (ADD_SELF_LOOPS if add_self_loops else 0) | (DIRECTED if directed else 0)
+    directed=True (or "transposed"): edges are src -> dst, rows are out-neighbour lists (AGP_DIRECTED;
+    queries need a = 0); directed="untransposed": rows are in-neighbour lists, deg out-degrees
+    (AGP_DIRECTED_IN, single-target PPR)."""
+    dflag = DIRECTED_IN if directed == "untransposed" else (DIRECTED if directed else 0)
+    flags = (ADD_SELF_LOOPS if add_self_loops else 0) | dflag
     on_dev = not isinstance(src, np.ndarray)
     if on_dev:
         flags |= EDGES_ON_DEVICE
@@ -499,3 +509,29 @@ def coefficients(params, device=0, stream=None):
     _check("agp_coefficients", lib().agp_coefficients(C.byref(params), keep.ctypes.data, push.ctypes.data, C.byref(y0),
                                                        int(device), _stream(stream)))
     return keep, push, y0.value
+
+
+def topk(pi, k, stream=None):
+    """``agp_topk``: pi CUDA float32 [Q, >= n] (row stride pi.stride(0), n = pi.shape[1]); returns
+    (values [Q, k] float32, ids [Q, k] int32) on the device, largest first, ties by ascending id."""
+    import torch
+    Q, n = int(pi.shape[0]), int(pi.shape[1])
+    val = torch.empty((Q, k), dtype=torch.float32, device=pi.device)
+    idx = torch.empty((Q, k), dtype=torch.int32, device=pi.device)
+    _check("agp_topk", lib().agp_topk(pi.data_ptr(), n, int(pi.stride(0)), Q, int(k), val.data_ptr(), idx.data_ptr(),
+                                       k, _stream(stream)))
+    return val, idx
+
+
+def sweep(g, pi, stream=None):
+    """``agp_sweep`` on a CUDA float32 row pi [n]: returns (best prefix size, its conductance, the
+    swept nodes in order (CUDA int32), Phi of every prefix (CUDA float64))."""
+    import torch
+    n = g.n
+    order = torch.empty(n, dtype=torch.int32, device=pi.device)
+    phi = torch.empty(max(n - 1, 1), dtype=torch.float64, device=pi.device)
+    best, bphi, swept = _i64(), _dbl(), _i64()
+    _check("agp_sweep", lib().agp_sweep(g.handle, pi.data_ptr(), order.data_ptr(), phi.data_ptr(), C.byref(best),
+                                         C.byref(bphi), C.byref(swept), _stream(stream)))
+    k = swept.value
+    return best.value, bphi.value, order[:k], phi[:max(min(k, n - 1), 0)]

@@ -97,7 +97,8 @@ struct agp_graph_s {
     int device = 0;
     int64_t n = 0, nnz = 0;
     int32_t max_deg = 0;
-    bool directed = false;         // rows are out-neighbour lists and deg out-degrees (AGP_DIRECTED)
+    int directed = 0;              // 1: rows are out-neighbour lists, deg out-degrees (AGP_DIRECTED);
+                                   // 2: rows are in-neighbour lists, deg out-degrees (AGP_DIRECTED_IN)
     int ubits = 1;                 // bits of a node id inside a packed (lane, node) item
     int64_t *rowptr = nullptr;
     int32_t *colidx = nullptr;
@@ -117,6 +118,11 @@ struct agp_graph_s {
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     int64_t kernel_launches = 0;           // all kernels launched for this graph
     std::vector<cudaEvent_t> wave_ev;      // AGP_QUERY_TIMES: call start + one event per wave
+    int32_t *row_list[3] = {nullptr, nullptr, nullptr};  // rows by length class (exact feature tiles)
+    int64_t row_count[3] = {0, 0, 0};
+    int32_t column_tile = 0;               // columns per tile of exact feature propagation, 0 = automatic
+    void *tile_buf = nullptr;              // residue blocks of the column tiles (grown on demand)
+    size_t tile_bytes = 0;
     agp::DevGraph dev() const { return agp::DevGraph{n, nnz, rowptr, colidx, deg}; }
 };
 
@@ -128,6 +134,10 @@ int katz_beta(agp_graph_s *g, double fraction, int iters, double tol, double *be
               double *lambda1, cudaStream_t stream);
 int katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colidx, int iters, double tol,
                         double *lambda1, cudaStream_t stream);
+int sweep(agp_graph_s *g, const float *pi, int32_t *order_out, double *phi_out, int64_t *best_size, double *best_phi,
+          int64_t *swept, cudaStream_t s);
+int topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t k, float *val, int32_t *idx, int64_t ldo,
+         cudaStream_t s);
 int coefficients(const agp_params_t *p, double *keep, double *push, double *y0, int device, cudaStream_t s);
 int validate_params(const agp_params_t &p);
 int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t *nodes,
@@ -142,6 +152,10 @@ int query_batch(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
                 int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);
 int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, int32_t Q, const void *X, int64_t ldx,
                 float *pi_out, int64_t ld_out, uint32_t flags, agp_stats_t *stats, cudaStream_t stream);
+int feature_exact_tiled(agp_graph_s *g, const agp_params_t *p, const uint16_t *X, int64_t d, int64_t ldx, float *Z,
+                        int64_t ldz, cudaStream_t s);
+int column_tile(const agp_graph_s *g);
+int exponent_mode(double p);
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d,
                       int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t stream);
 

@@ -255,6 +255,8 @@ int agp_graph_destroy(agp_graph_t g)
     for (int k = 0; k < 2; ++k)
         if (g->ev_wave[k]) cudaEventDestroy(g->ev_wave[k]);
     for (cudaEvent_t e : g->wave_ev) cudaEventDestroy(e);
+    for (int c = 0; c < 3; ++c) cudaFree(g->row_list[c]);
+    cudaFree(g->tile_buf);
     cudaFree(g->rowptr);
     cudaFree(g->colidx);
     cudaFree(g->deg);
@@ -286,6 +288,15 @@ int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, in
 {
     return agp::autotune(g, params, n_params, Q, x_off, x_idx, x_val, pi_out, ld_out, flags, candidates, n_candidates,
                          best_lanes, best_width, best_ms, (cudaStream_t)stream);
+}
+
+int agp_graph_set_column_tile(agp_graph_t g, int32_t columns)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (columns != 0 && columns != 8 && columns != 16 && columns != 32)
+        return agp::fail(AGP_EINVAL, "column tile must be 0, 8, 16 or 32");
+    g->column_tile = columns;
+    return AGP_OK;
 }
 
 int agp_graph_set_group_width(agp_graph_t g, int32_t width)
@@ -360,6 +371,18 @@ int agp_katz_lambda_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col
 int agp_coefficients(const agp_params_t *params, double *keep, double *push, double *y0, int device, void *stream)
 {
     return agp::coefficients(params, keep, push, y0, device, (cudaStream_t)stream);
+}
+
+int agp_sweep(agp_graph_t g, const float *pi, int32_t *order, double *phi, int64_t *best_size, double *best_phi,
+              int64_t *swept, void *stream)
+{
+    return agp::sweep(g, pi, order, phi, best_size, best_phi, swept, (cudaStream_t)stream);
+}
+
+int agp_topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t k, float *val, int32_t *idx, int64_t ldo,
+             void *stream)
+{
+    return agp::topk(pi, n, ld, Q, k, val, idx, ldo, (cudaStream_t)stream);
 }
 
 int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes, const float *c,

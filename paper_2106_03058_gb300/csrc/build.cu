@@ -7,7 +7,10 @@
 //   2. key (u, d_v) with value v: stable, so ties on degree keep ascending v.
 // Input self-loops are dropped; with AGP_ADD_SELF_LOOPS one loop per node is added before the
 // sorts and counts once in the degree. With AGP_DIRECTED (Section 4, "Propagation on directed
-// graph") only u -> v is kept, so rows are out-neighbour lists and degrees out-degrees.
+// graph", transposed adjacency) only u -> v is kept, so rows are out-neighbour lists and degrees
+// out-degrees. With AGP_DIRECTED_IN (the untransposed adjacency of the same passage, single-target
+// PPR) only v -> u is kept: rows are in-neighbour lists, while the degrees stay out-degrees (the
+// number of rows a node appears in), so a row's length is not its node's degree.
 #include <algorithm>
 #include <vector>
 
@@ -17,7 +20,8 @@ namespace agp {
 namespace {
 
 // Two keys per input edge: (u, v) and, for an undirected graph, (v, u); a directed graph keeps
-// only u -> v (the reverse slot holds the sentinel and is dropped with the loops).
+// only u -> v (directed = 1) or only its reverse v -> u (directed = 2); a slot it does not keep
+// holds the sentinel and is dropped with the loops.
 __global__ void k_expand_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int ubits,
                                uint64_t sentinel, int directed, uint64_t *keys, unsigned int *bad)
 {
@@ -26,8 +30,8 @@ __global__ void k_expand_edges(const int32_t *src, const int32_t *dst, int64_t m
         const bool ok = u >= 0 && u < n && v >= 0 && v < n;
         if (!ok) atomicOr(bad, 1u);
         const bool keep = ok && u != v;
-        keys[2 * e] = keep ? (((uint64_t)u << ubits) | (uint64_t)v) : sentinel;
-        keys[2 * e + 1] = (keep && !directed) ? (((uint64_t)v << ubits) | (uint64_t)u) : sentinel;
+        keys[2 * e] = (keep && directed != 2) ? (((uint64_t)u << ubits) | (uint64_t)v) : sentinel;
+        keys[2 * e + 1] = (keep && directed != 1) ? (((uint64_t)v << ubits) | (uint64_t)u) : sentinel;
     }
 }
 
@@ -45,16 +49,18 @@ __global__ void k_unique_flags(const uint64_t *keys, int64_t count, uint64_t sen
     }
 }
 
+// Unique keys to the front of `uniq`; rowlen[u] counts row u. With `outdeg` (in-neighbour rows),
+// outdeg[v] counts the rows v appears in.
 __global__ void k_compact_unique(const uint64_t *keys, const uint32_t *flag, const int64_t *pos, int64_t count,
-                                 int ubits, uint64_t *uniq, int32_t *deg)
+                                 int ubits, uint64_t *uniq, int32_t *rowlen, int32_t *outdeg)
 {
     const uint64_t mask = (1ull << ubits) - 1ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[i]) continue;
         const uint64_t k = keys[i];
         uniq[pos[i]] = k;
-        atomicAdd(&deg[(int64_t)(k >> ubits)], 1);
-        (void)mask;
+        atomicAdd(&rowlen[(int64_t)(k >> ubits)], 1);
+        if (outdeg) atomicAdd(&outdeg[(int64_t)(k & mask)], 1);
     }
 }
 
@@ -119,9 +125,11 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     if (n < 0 || n >= (1ll << 31)) return fail(AGP_EINVAL, "agp_build_graph: n must be in [0, 2^31)");
     if (m < 0) return fail(AGP_EINVAL, "agp_build_graph: n_edges < 0");
     if (m > 0 && (!src || !dst)) return fail(AGP_EINVAL, "agp_build_graph: src/dst NULL");
-    if (flags & ~(AGP_ADD_SELF_LOOPS | AGP_EDGES_ON_DEVICE | AGP_DIRECTED))
+    if (flags & ~(AGP_ADD_SELF_LOOPS | AGP_EDGES_ON_DEVICE | AGP_DIRECTED | AGP_DIRECTED_IN))
         return fail(AGP_EINVAL, "agp_build_graph: unknown flag");
-    const int directed = (flags & AGP_DIRECTED) ? 1 : 0;
+    if ((flags & AGP_DIRECTED) && (flags & AGP_DIRECTED_IN))
+        return fail(AGP_EINVAL, "agp_build_graph: AGP_DIRECTED and AGP_DIRECTED_IN exclude each other");
+    const int directed = (flags & AGP_DIRECTED) ? 1 : (flags & AGP_DIRECTED_IN) ? 2 : 0;
     AGP_CUDA_TRY(cudaSetDevice(device));
 
     const bool loops = flags & AGP_ADD_SELF_LOOPS;
@@ -175,19 +183,26 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     int64_t nnz = 0;
     AGP_CUDA_TRY(cudaMemcpyAsync(&nnz, total.p, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
 
-    DevBuf rowptr, degb, colA, colB;
+    DevBuf rowptr, degb, lenb, colA, colB;
     AGP_TRY(degb.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
     AGP_TRY(rowptr.alloc(sizeof(int64_t) * (n + 1)));
     AGP_CUDA_TRY(cudaMemsetAsync(degb.p, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), stream));
+    if (directed == 2) {  // row lengths (in-degrees) apart from the degrees (out-degrees)
+        AGP_TRY(lenb.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
+        AGP_CUDA_TRY(cudaMemsetAsync(lenb.p, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), stream));
+    }
+    int32_t *rowlen = directed == 2 ? lenb.as<int32_t>() : degb.as<int32_t>();
     AGP_CUDA_TRY(cudaStreamSynchronize(stream));
     // unique keys go to the front of the spare key buffer
-    if (E > 0) k_compact_unique<<<grid, kBlock, 0, stream>>>(sorted, flagb.as<uint32_t>(), pos.as<int64_t>(), E, ubits, other, degb.as<int32_t>());
+    if (E > 0)
+        k_compact_unique<<<grid, kBlock, 0, stream>>>(sorted, flagb.as<uint32_t>(), pos.as<int64_t>(), E, ubits, other, rowlen,
+                                                      directed == 2 ? degb.as<int32_t>() : nullptr);
     AGP_CUDA_TRY(cudaGetLastError());
     flagb.reset();
     pos.reset();
 
-    // rowptr = exclusive scan of degrees
-    AGP_TRY(exclusive_scan_u32((const uint32_t *)degb.p, rowptr.as<int64_t>(), n, rowptr.as<int64_t>() + n, scratch.p, scratch_bytes, stream));
+    // rowptr = exclusive scan of row lengths
+    AGP_TRY(exclusive_scan_u32((const uint32_t *)rowlen, rowptr.as<int64_t>(), n, rowptr.as<int64_t>() + n, scratch.p, scratch_bytes, stream));
     if (n > 0) k_max_deg<<<grid, kBlock, 0, stream>>>(degb.as<int32_t>(), n, maxd.as<int32_t>());
     int32_t max_deg = 0;
     AGP_CUDA_TRY(cudaMemcpyAsync(&max_deg, maxd.p, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
@@ -211,7 +226,7 @@ int build_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, ui
     g->n = n;
     g->nnz = nnz;
     g->max_deg = max_deg;
-    g->directed = directed != 0;
+    g->directed = directed;
     g->ubits = ubits;
     g->rowptr = (int64_t *)rowptr.release();
     g->deg = (int32_t *)degb.release();

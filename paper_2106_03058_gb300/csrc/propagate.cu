@@ -579,8 +579,9 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
     const uint32_t item = __ldg(A.items + idx);
     const int grp = (int)(item >> A.ubits);
     const int32_t u = (int32_t)(item & A.umask);
-    const int32_t d = __ldg(A.g.deg + u);
+    const int32_t du = __ldg(A.g.deg + u);     // d_u of the normalisation
     const int64_t e0 = __ldg(A.g.rowptr + u);
+    const int d = (int)(__ldg(A.g.rowptr + u + 1) - e0);  // row length (d_u except on in-neighbour rows)
     float *Rg = A.R + (size_t)grp * A.ldR * W;  // r^(i+1): the compaction emptied r^(i)
     const int32_t *row = A.g.colidx + e0;
     int J = 0, nseg = 0;
@@ -600,8 +601,9 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
         const float2 cf = __ldg(A.coef + lane * kMaxLevels + lvl);
         // reserve: q^(i)(u) = (w_i / Y_i) r^(i)(u), added to pi (scale folded into cf.x)
         red_add(P.out + (int64_t)u * P.su, cf.x * rj);
-        if (lvl >= P.L || d == 0) continue;
-        const float c = apply_deg(cf.y * rj, d, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
+        // nothing to push: the last level, an empty row, or d_u = 0 with b > 0 (D^-b := 0)
+        if (lvl >= P.L || d == 0 || (du == 0 && P.b_mode != 0)) continue;
+        const float c = apply_deg(cf.y * rj, du, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
         if (!(c > 0.f)) continue;
         const int k = det_prefix(c, P, row, d, A.g.deg);
         const int tail = d - k;
@@ -796,7 +798,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         const uint32_t item = A.items[idx];
         const int grp = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
-        const int d = A.g.deg[u];
+        const int64_t e0 = A.g.rowptr[u];
+        const int d = (int)(A.g.rowptr[u + 1] - e0);  // row length
         const uint32_t flags = A.flag_item[idx];
         __syncwarp();
         if (lane_id < W) {
@@ -820,7 +823,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
             need_deg |= L.a_mode != 0;
         }
         float *Rg = A.R + (size_t)grp * A.ldR * W;
-        const int32_t *row = A.g.colidx + A.g.rowptr[u];
+        const int32_t *row = A.g.colidx + e0;
         const int c0 = (int)Rc.y * kChunk, c1 = min(J, c0 + kChunk);
         unsigned int acc[W] = {};
         for (int p0 = c0 + 4 * lane_id; p0 < c1; p0 += 128) walk4<W>(A, Rg, sL[warp], u, row, p0, min(p0 + 4, c1), need_deg, acc);
@@ -855,7 +858,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         const uint32_t item = A.items[idx];
         const int grp = (int)(item >> A.ubits);
         const int32_t u = (int32_t)(item & A.umask);
-        const int d = A.g.deg[u];
+        const int64_t e0 = A.g.rowptr[u];
+        const int d = (int)(A.g.rowptr[u + 1] - e0);  // row length
         const uint32_t flags = A.flag_item[idx];
         int s = (int)Rc.y, slot = -1, k = 0, seglen = 0;
 #pragma unroll
@@ -882,7 +886,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         float *Rs = A.R + (size_t)grp * A.ldR * W + slot;
         const float c = A.c_item[idx * W + slot];
         const int j0 = k + s * seglen, j1 = min(d, j0 + seglen);
-        const int32_t *row = A.g.colidx + A.g.rowptr[u];
+        const int32_t *row = A.g.colidx + e0;
         unsigned long long drawn = 0, accepted = 0;
         sample_range<4, W>(A, P, Rs, u, lvl, (uint32_t)s, row, j0, j1, c, drawn, accepted);
         if (A.collect && (drawn | accepted)) {
@@ -1070,7 +1074,7 @@ __global__ void k_threshold(DevGraph g, LaneParam P, int64_t count, const int32_
         const int32_t u = nodes[t];
         int k = 0;
         if (u >= 0 && u < g.n) {
-            const int d = g.deg[u];
+            const int d = (int)(g.rowptr[u + 1] - g.rowptr[u]);  // row length
             if (d > 0 && c[t] > 0.f) k = det_prefix(c[t], P, g.colidx + g.rowptr[u], d, g.deg);
         }
         k_out[t] = k;
@@ -1086,12 +1090,14 @@ int exponent_mode(double p)
     return 3;
 }
 
-// Parameters checked against the graph they run on: a directed graph (AGP_DIRECTED) needs a = 0,
-// because a node without out-edges would have d^-a undefined as a push target.
+// Parameters checked against the graph they run on: a directed graph with out-neighbour rows
+// (AGP_DIRECTED) needs a = 0, because a node without out-edges would have d^-a undefined as a push
+// target. With in-neighbour rows (AGP_DIRECTED_IN) every push target has an out-edge, and a source
+// without out-edges pushes nothing when b > 0 (D^-b := 0), so any a, b is valid.
 int validate_params_for(const agp_graph_s *g, const agp_params_t &p)
 {
     AGP_TRY(validate_params(p));
-    if (g->directed && p.a != 0.0) return fail(AGP_EINVAL, "params: a directed graph needs a = 0");
+    if (g->directed == 1 && p.a != 0.0) return fail(AGP_EINVAL, "params: a directed graph needs a = 0");
     return AGP_OK;
 }
 
@@ -2120,6 +2126,10 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     AGP_CUDA_TRY(cudaSetDevice(g->device));
     const bool plain = flags & AGP_PLAIN;
     const int64_t n = g->n;
+    // eps = 0 on an undirected graph: exact propagation (Algorithm 1) over column tiles, pulling over
+    // the symmetric rows (no atomics); the plain path and directed graphs keep the lane pipeline
+    if (params->eps == 0.0 && !plain && !g->directed && !ctx->ws)
+        return feature_exact_tiled(g, params, X, d, ldx, Z, ldz, s);
     Workspace *ws = ctx->ws;
     if (!ws) AGP_TRY(ensure_workspace(g, (int)std::min<int64_t>({2 * d, 4096, (int64_t)wave_lanes(g)}), plain, &ws));
     // column norms of the sign parts
@@ -2166,7 +2176,7 @@ int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t
 {
     if (!g) return fail(AGP_EINVAL, "graph is NULL");
     if (!(a >= 0.0 && a <= 1.0) || !(eps >= 0.0)) return fail(AGP_EINVAL, "a in [0,1], eps >= 0");
-    if (g->directed && a != 0.0) return fail(AGP_EINVAL, "a directed graph needs a = 0");
+    if (g->directed == 1 && a != 0.0) return fail(AGP_EINVAL, "a directed graph needs a = 0");
     if (count < 0 || (count > 0 && (!nodes || !c || !k_out))) return fail(AGP_EINVAL, "bad arrays");
     if (count == 0) return AGP_OK;
     AGP_CUDA_TRY(cudaSetDevice(g->device));

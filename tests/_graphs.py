@@ -110,3 +110,16 @@ def dense_directed_propagation(A, a, b, w, x, transposed=True):
             v = M @ v
         out += wi * v
     return out
+
+
+def barbell(k):
+    """Two complete graphs K_k joined by the edge (0, k): nodes 0..k-1 and k..2k-1."""
+    src, dst = [], []
+    for off in (0, k):
+        for i in range(k):
+            for j in range(i + 1, k):
+                src.append(off + i)
+                dst.append(off + j)
+    src.append(0)
+    dst.append(k)
+    return 2 * k, np.array(src, np.int32), np.array(dst, np.int32)

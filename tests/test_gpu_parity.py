@@ -566,3 +566,51 @@ def test_errors(agp, rmat14):
     # the handle is still usable afterwards
     out, _ = agp.query_sources(g, agp.ppr(0.2, 3, 0.0), [int(np.argmax(np.bincount(u)))])
     assert torch.isfinite(out).all()
+
+
+def test_directed_untransposed_single_target(agp, rmat14):
+    """Section 4, "Propagation on directed graph", untransposed adjacency (single-target PPR,
+    a = 1, b = 0, Table 1): rows are in-neighbour lists sorted by (d_out, id) while deg holds
+    out-degrees. The CSR is bit-exact against the oracle; eps = 0 matches it to 1e-5 for a = 1, b = 0
+    and for other (a, b) (a node without out-edges pushes nothing when b > 0); eps > 0 is unbiased at
+    the entries that carry mass."""
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v, directed="untransposed")
+    og = oracle.build_csr(n, u, v, directed="untransposed")
+    rp, ci, dg = (t.cpu().numpy() for t in g.csr())
+    np.testing.assert_array_equal(rp, og.rowptr)
+    np.testing.assert_array_equal(ci, og.colidx)
+    np.testing.assert_array_equal(dg, og.deg)
+    rowlen = np.diff(og.rowptr)
+    assert np.any(rowlen != og.deg)  # row lengths and degrees differ here
+    targets = np.flatnonzero(rowlen > 0)[::997][:5]
+    for kind, L, param, a, b in ((oracle.PPR, 15, 0.2, 1.0, 0.0), (oracle.TRANSITION, 4, 0.0, 0.5, 0.5),
+                                 (oracle.HKPR, 10, 3.0, 0.0, 1.0)):
+        params = agp._params(a, b, L, kind, param, eps=0.0)
+        out, _ = agp.query_sources(g, params, targets)
+        w, Y = oracle.tail_sums(kind, L, param)
+        for k, t_ in enumerate(targets):
+            x = np.zeros(n); x[t_] = 1.0
+            _assert_rel(out[k].cpu().numpy(), oracle.basic(og, a, b, L, w, Y, x))
+    # eps > 0, single-target PPR: the mean of 200 runs against the exact vector
+    t_ = int(targets[0])
+    w, Y = oracle.tail_sums(oracle.PPR, 10, 0.2)
+    x = np.zeros(n); x[t_] = 1.0
+    exact = oracle.basic(og, 1.0, 0.0, 10, w, Y, x)
+    N = 200
+    outs, _ = agp.query_sources(g, [agp._params(1.0, 0.0, 10, agp.W_PPR, 0.2, eps=1e-5, seed=k) for k in range(N)],
+                                [t_] * N)
+    runs = outs.cpu().numpy().astype(np.float64)
+    sd = runs.std(0, ddof=1) / np.sqrt(N)
+    live = sd > 0
+    assert live.sum() >= 100
+    z = (runs.mean(0)[live] - exact[live]) / sd[live]
+    assert np.mean(np.abs(z) > 2.576) <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / live.sum()) and np.abs(z).max() < 6.0
+    # the two directed layouts exclude each other
+    import ctypes
+    h = ctypes.c_void_p()
+    uu, vv = np.ascontiguousarray(u[:10]), np.ascontiguousarray(v[:10])
+    rc = agp.lib().agp_build_graph(n, 10, uu.ctypes.data, vv.ctypes.data, agp.DIRECTED | agp.DIRECTED_IN, 0, None,
+                                   ctypes.byref(h))
+    assert rc == 1 and not h.value
+    g.destroy()

@@ -1,0 +1,65 @@
+"""Parity at the scale of the batched benchmark: a Chung-Lu graph (exponent 2.1) with 4.2M nodes,
+so node ids need 23 bits inside a packed (group, node) item, queried in multi-wave batches of 16
+lanes (two waves in flight) with lane groups of four and of one. Exact (eps = 0) Katz and L-step
+transition queries are compared entry by entry with the FP64 oracle (Algorithm 1) to relative 1e-5.
+The edge count is reduced to 20M so that the oracle's exact runs take seconds on the host.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import graphs as SG
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def agp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_03058_gb300 as agp
+    agp.lib()
+    return agp
+
+
+def test_exact_parity_at_scale(agp):
+    from concurrent.futures import ThreadPoolExecutor
+    n, m = 4_200_000, 20_000_000
+    u, v = SG.chung_lu_edges(n, m, 2.1, 20210603 + 9)
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    assert n > (1 << 22)
+    beta, lam = agp.katz_beta(g, 0.85, iters=500, tol=1e-10)
+    deg = og.deg
+    rng = np.random.default_rng(5)
+    live = np.flatnonzero(deg > 0)
+    Q = 40
+    srcs = rng.choice(live, Q, replace=False).astype(np.int32)
+    srcs[0] = int(np.argmax(deg))  # a hub source: long rows, warp walks
+    checked = [0, 7, 21, 39]       # across the three waves
+    tables = {"katz": (0.0, 0.0, 20) + oracle.tail_sums(oracle.KATZ, 20, beta),
+              "transition": (0.0, 1.0, 4) + oracle.tail_sums(oracle.TRANSITION, 4)}
+
+    def exact(item):
+        kind, s_ = item
+        a, b, L, w, Y = tables[kind]
+        x = np.zeros(n)
+        x[s_] = 1.0
+        return oracle.basic(og, a, b, L, w, Y, x)
+
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        want = dict(zip([(k, int(srcs[q])) for k in tables for q in checked],
+                        ex.map(exact, [(k, int(srcs[q])) for k in tables for q in checked])))
+    for width in (4, 1):
+        g.set_wave_lanes(16)
+        g.set_group_width(width)
+        for kind, params in (("katz", agp.katz(beta, 20, 0.0)), ("transition", agp.transition(4, 0.0))):
+            out, _ = agp.query_sources(g, params, srcs)
+            for q in checked:
+                w_ = want[(kind, int(srcs[q]))]
+                got = out[q].cpu().numpy().astype(np.float64)
+                err = np.abs(got - w_)
+                bad = err > 1e-5 * np.abs(w_) + 1e-30
+                assert not bad.any(), (kind, width, q, int(bad.sum()), float(np.max(err / np.maximum(np.abs(w_), 1e-300))))
+    g.destroy()
