@@ -673,6 +673,9 @@ def main():
     ap.add_argument("--queries", type=int, default=0, help="sources per launch (default: the workload's 256)")
     ap.add_argument("--lanes", type=int, default=0, help="wave width; 0 = autotune (with the group width)")
     ap.add_argument("--width", type=int, default=0, help="group width with --lanes (1, 2, 4; 0 = automatic)")
+    ap.add_argument("--pull", type=int, default=None,
+                    help="pull a level when the lane's frontier volume is >= nnz >> PULL (-1 = never; default: the "
+                         "library's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving trace instead of the batched step")
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -736,6 +739,8 @@ def main():
     log(f"[bench] graph built on GPU in {time.perf_counter() - t0:.2f}s (nnz={g.nnz})")
     beta, lam = agp.katz_beta(g, 0.85, iters=1000, tol=1e-12)
     log(f"[bench] lambda_1={lam:.6f} beta={beta:.6e}")
+    if args.pull is not None:
+        g.set_pull_threshold(args.pull)
 
     steps_total = args.warmup + args.steps
     srcs = degree_weighted_sources(n, u, v, Q * 2 * steps_total, wl["seed_src"])
@@ -928,6 +933,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "parallelism": f"replicas{world}", "queries_per_step": 2 * Q,
                        "wave_lanes": lanes, "group_width": width, "autotune_ms": tuned_ms,
+                       "pull_threshold_shift": args.pull if args.pull is not None else "default (2)",
                        "lambda_1": lam, "beta": beta,
                        "l2": "flushed before every timed step (256 MB write); CSR 0.96 GB and 8 GB of residues exceed L2"},
             "latency_ms": {"per_query": latency_summary(lat_k + lat_t), "katz": latency_summary(lat_k),

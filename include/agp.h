@@ -124,6 +124,19 @@ AGP_API int agp_graph_set_wave_lanes(agp_graph_t g, int32_t lanes);
  * are its own). The plain path always uses 1. agp_autotune picks it by timing. */
 AGP_API int agp_graph_set_group_width(agp_graph_t g, int32_t width);
 
+/* Direction of a level. On an undirected graph a lane whose frontier volume (sum of d_u over
+ * r^(i)(u) != 0) is at least nnz >> shift computes level i by pulling: every node v walks its row
+ * once for the lane's group and adds, per edge (u, v) with r(u) != 0, what Algorithm 2 pushes along
+ * it (the deterministic increment when it passes the push test, else eps with the sampling
+ * probability, the trial drawn from a stream keyed by (u, v, level)). There are no atomics; the
+ * estimator and its distribution are those of the push. Smaller frontiers push. The decision is the
+ * lane's own, so a lane's result does not depend on its batch. shift in [0, 62]; -1 = never pull
+ * (the default). Pulling walks every edge and draws a trial for each sampled one, while pushing
+ * skips through sparse tails: it pays only where nearly every edge of the graph carries a
+ * deterministic increment (exact or large-residue levels); on the batched benchmark's eps = 1e-8
+ * Katz levels it was several times slower. Directed graphs always push. */
+AGP_API int agp_graph_set_pull_threshold(agp_graph_t g, int32_t shift);
+
 /* Columns per tile of exact feature propagation (agp_feature_propagate with eps = 0 on an undirected
  * graph): 8, 16 or 32 (0 = automatic: the widest whose n x T FP32 residue block stays within 64 MB,
  * half of L2, at least 8). */
@@ -182,6 +195,11 @@ typedef struct {
                                      device time with agp_profile_read                          */
 #define AGP_QUERY_TIMES 0x80u     /* fill stats[q].done_ms: one CUDA event per wave (no counter
                                      atomics); needs stats                                      */
+#define AGP_SAMPLER_GROUPS 0x100u /* subset sampling by the paper's scheme (Section 4): per degree
+                                     group a Binomial(|G_k|, p*) count of trials at uniformly chosen
+                                     positions, each kept with p_v / p*, instead of geometric skips
+                                     and per-position trials (same distribution; for the sampler's
+                                     ablation). Such lanes always push                           */
 #define AGP_EPS_ABSOLUTE 0x20u    /* eps is in the raw units of the signal: a sign part x+- runs
                                      with eps / ||x+-||_1 on its normalised residues. Default
                                      (flag clear): eps applies to the normalised residues, the
@@ -228,7 +246,7 @@ AGP_API int agp_query(agp_graph_t g, const agp_params_t *params, int64_t x_nnz, 
  *            copied to the graph's device staging first.
  *   pi_out   Q rows of ld_out >= n floats; host or device (AGP_OUTPUT_ON_DEVICE)
  *   flags    AGP_INPUT_ON_DEVICE, AGP_OUTPUT_ON_DEVICE, AGP_PLAIN, AGP_COLLECT_STATS, AGP_PROFILE,
- *            AGP_QUERY_TIMES, AGP_EPS_ABSOLUTE, AGP_DENSE_BF16
+ *            AGP_QUERY_TIMES, AGP_EPS_ABSOLUTE, AGP_DENSE_BF16, AGP_SAMPLER_GROUPS
  * The call synchronises `stream` once after the norms, and at the end when pi_out or stats are host
  * memory. Errors as agp_query_batch (a non-finite entry of X: AGP_EINVAL).
  */
@@ -241,7 +259,8 @@ AGP_API int agp_query_dense(agp_graph_t g, const agp_params_t *params, int32_t n
  * Feature propagation for GNNs (Section 5.2; SGC, APPNP and GDC rows of Table 1): every column
  * c of X is a graph signal, Z[:, c] = estimate of sum_i w_i (D^-a A D^-b)^i X[:, c]. Columns are
  * split into sign parts and normalised as in agp_query_batch; eps applies per normalised part
- * (flags AGP_PLAIN, AGP_PROFILE and AGP_EPS_ABSOLUTE; with the last, eps is in X's raw units).
+ * (flags AGP_PLAIN, AGP_PROFILE, AGP_SAMPLER_GROUPS and AGP_EPS_ABSOLUTE; with the last, eps is in X's
+ * raw units).
  *   X       device, n rows x d columns of bfloat16 (raw 16-bit patterns), row stride ldx >= d
  *   Z       device, n rows x d columns of FP32, row stride ldz >= d; fully written
  *   seed    of params: column c part s uses the stream (seed, c, s)
@@ -285,18 +304,21 @@ typedef struct agp_server_s *agp_server_t;
 
 typedef struct {
     int32_t mode;             /* AGP_SERVE_*                                                        */
-    int32_t max_lanes;        /* slots (lanes) in flight; 0 = max(8 x automatic wave width, 128)    */
+    int32_t max_lanes;        /* slots (lanes) per pool; 0 = max(8 x automatic wave width, 128)     */
     int64_t result_budget;    /* bytes of result buffers of admitted, unreleased requests; 0 = 4 GiB */
     int32_t results_on_host;  /* 1: results are copied to library-owned pinned host memory          */
-    int32_t admission;        /* AGP_ADMIT_* (batched mode). The cost estimate is the bound of the
-                                 proof of Theorem 4.3, (1/eps) sum_{i=1..L} (Y_i/Y_0) ||P^i x||_1,
-                                 with the mass ||P^i x||_1 bounded per weight kind; a request's
-                                 priority is cost / (1 + seconds waited), compared between the
-                                 oldest waiting requests of 64 cost classes (floor(log2 cost));
-                                 requests above 1e8
-                                 estimated operations use at most 3/4 of the slots while another
-                                 such request holds slots; a request that has waited over 30 s is
-                                 admitted next, nothing else starting until its slots are free      */
+    int32_t admission;        /* AGP_ADMIT_* (batched mode). Requests are split by estimated cost
+                                 into a light pool (below 2^23 ~ 8.4e6 operations) and a heavy pool,
+                                 each with max_lanes slots, its own workspace, stream and sweeps, so
+                                 light sweeps never wait for heavy lanes. The estimate is the edge
+                                 bound of the proof of Theorem 4.3, (1/eps) sum_{i=1..L} (Y_i/Y_0)
+                                 ||P^i x||_1 (the mass bounded per weight kind), plus one frontier
+                                 item per non-zero residue and level ((L+1) n/2 per sign part of a
+                                 feature column). Within a pool a request's priority is cost / (1 +
+                                 seconds waited), compared between the oldest waiting requests of its
+                                 cost classes (floor(log2 cost)); a request that has waited over 30 s
+                                 is admitted next, nothing else of its pool starting until its slots
+                                 are free                                                           */
 } agp_serve_config_t;
 
 #define AGP_REQ_X_ON_DEVICE 0x1u   /* X is a device pointer that stays valid until the request is done */

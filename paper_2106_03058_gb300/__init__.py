@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "AgpError", "Params", "Stats", "lib", "build_graph", "Graph", "query_batch", "query_sources",
-    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "QUERY_TIMES", "topk", "sweep", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
+    "feature_propagate", "katz_beta", "coefficients", "query_dense", "DENSE_BF16", "QUERY_TIMES", "SAMPLER_GROUPS", "topk", "sweep", "katz_lambda_noalloc", "threshold", "ppr", "hkpr", "katz", "transition", "finite",
     "W_FINITE", "W_PPR", "W_HKPR", "W_KATZ", "W_TRANSITION", "INPUT_ON_DEVICE", "OUTPUT_ON_DEVICE",
     "PLAIN", "COLLECT_STATS", "PROFILE", "EPS_ABSOLUTE", "KERNELS", "profile_read", "autotune", "Server", "ServeConfig",
     "Request", "Result", "SERVE_BATCHED", "SERVE_FIFO_PLAIN", "REQ_X_ON_DEVICE", "REQ_EPS_ABSOLUTE", "ADMIT_COST", "ADMIT_FIFO", "ADD_SELF_LOOPS", "EDGES_ON_DEVICE", "DIRECTED", "DIRECTED_IN", "MAX_LEVELS",
@@ -28,7 +28,7 @@ __all__ = [
 
 W_FINITE, W_PPR, W_HKPR, W_KATZ, W_TRANSITION = 0, 1, 2, 3, 4
 INPUT_ON_DEVICE, OUTPUT_ON_DEVICE, PLAIN, COLLECT_STATS, PROFILE, EPS_ABSOLUTE = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
-DENSE_BF16, QUERY_TIMES = 0x40, 0x80
+DENSE_BF16, QUERY_TIMES, SAMPLER_GROUPS = 0x40, 0x80, 0x100
 KERNELS = ("compact", "expand", "push", "sample", "level_end")
 ADD_SELF_LOOPS, EDGES_ON_DEVICE, DIRECTED, DIRECTED_IN = 0x1, 0x2, 0x4, 0x8
 MAX_LEVELS = 64
@@ -123,6 +123,7 @@ def lib():
                                        C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_dbl), _vp]
             L.agp_graph_set_group_width.argtypes = [_vp, _i32]
             L.agp_graph_set_column_tile.argtypes = [_vp, _i32]
+            L.agp_graph_set_pull_threshold.argtypes = [_vp, _i32]
             L.agp_serve_create.argtypes = [_vp, C.POINTER(ServeConfig), C.POINTER(_vp)]
             L.agp_serve_submit.argtypes = [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
             L.agp_serve_poll.argtypes = [_vp, C.c_uint64, C.POINTER(Result)]
@@ -137,7 +138,8 @@ def lib():
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
                       "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense",
-                      "agp_graph_set_group_width", "agp_topk", "agp_sweep", "agp_graph_set_column_tile"):
+                      "agp_graph_set_group_width", "agp_topk", "agp_sweep", "agp_graph_set_column_tile",
+                      "agp_graph_set_pull_threshold"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -238,6 +240,11 @@ class Graph:
     def set_group_width(self, width):
         """``agp_graph_set_group_width`` (0 = automatic; 1, 2 or 4)."""
         _check("agp_graph_set_group_width", lib().agp_graph_set_group_width(self.handle, int(width)))
+
+    def set_pull_threshold(self, shift):
+        """``agp_graph_set_pull_threshold``: pull a level when the frontier holds >= n >> shift nodes
+        (-1 = never; 62 = always)."""
+        _check("agp_graph_set_pull_threshold", lib().agp_graph_set_pull_threshold(self.handle, int(shift)))
 
     def set_column_tile(self, columns):
         """``agp_graph_set_column_tile`` (0 = automatic; 8, 16 or 32)."""
@@ -447,7 +454,8 @@ def profile_read(g, reset=False):
     return dict(zip(KERNELS, list(ms))), dict(zip(KERNELS, list(ln))), tot.value
 
 
-def query_sources(g, params, sources, out=None, plain=False, collect_stats=False, stream=None, profile=False):
+def query_sources(g, params, sources, out=None, plain=False, collect_stats=False, stream=None, profile=False,
+                  sampler_groups=False):
     """One query per source node (x = e_s). Inputs/outputs on the device; returns (out, stats)."""
     import torch
     dev = f"cuda:{g.device}"
@@ -457,7 +465,7 @@ def query_sources(g, params, sources, out=None, plain=False, collect_stats=False
     if out is None:
         out = torch.empty((Q, g.n), dtype=torch.float32, device=dev)
     flags = (INPUT_ON_DEVICE | OUTPUT_ON_DEVICE | (PLAIN if plain else 0) | (COLLECT_STATS if collect_stats else 0)
-             | (PROFILE if profile else 0))
+             | (PROFILE if profile else 0) | (SAMPLER_GROUPS if sampler_groups else 0))
     st = query_batch(g, params, off, src, None, out, out.stride(0), flags, None, stream)
     return out, st
 

@@ -118,9 +118,11 @@ struct agp_graph_s {
     int64_t prof_launches[5] = {0, 0, 0, 0, 0};
     int64_t kernel_launches = 0;           // all kernels launched for this graph
     std::vector<cudaEvent_t> wave_ev;      // AGP_QUERY_TIMES: call start + one event per wave
-    int32_t *row_list[3] = {nullptr, nullptr, nullptr};  // rows by length class (exact feature tiles)
+    int32_t *row_list[3] = {nullptr, nullptr, nullptr};  // rows by length class (feature tiles, pull levels)
     int64_t row_count[3] = {0, 0, 0};
     int32_t column_tile = 0;               // columns per tile of exact feature propagation, 0 = automatic
+    int32_t pull_shift = -1;               // a lane pulls a level whose frontier volume (sum of d_u) is
+                                           // >= nnz >> pull_shift (undirected graphs); < 0: never
     void *tile_buf = nullptr;              // residue blocks of the column tiles (grown on demand)
     size_t tile_bytes = 0;
     agp::DevGraph dev() const { return agp::DevGraph{n, nnz, rowptr, colidx, deg}; }
@@ -155,6 +157,7 @@ int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
 int feature_exact_tiled(agp_graph_s *g, const agp_params_t *p, const uint16_t *X, int64_t d, int64_t ldx, float *Z,
                         int64_t ldz, cudaStream_t s);
 int column_tile(const agp_graph_s *g);
+int ensure_row_lists(agp_graph_s *g, cudaStream_t s);
 int exponent_mode(double p);
 int feature_propagate(agp_graph_s *g, const agp_params_t *params, const uint16_t *X, int64_t d,
                       int64_t ldx, float *Z, int64_t ldz, uint32_t flags, cudaStream_t stream);

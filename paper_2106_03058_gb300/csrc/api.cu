@@ -290,6 +290,14 @@ int agp_autotune(agp_graph_t g, const agp_params_t *params, int32_t n_params, in
                          best_lanes, best_width, best_ms, (cudaStream_t)stream);
 }
 
+int agp_graph_set_pull_threshold(agp_graph_t g, int32_t shift)
+{
+    if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
+    if (shift < -1 || shift > 62) return agp::fail(AGP_EINVAL, "pull threshold shift must be in [-1, 62]");
+    g->pull_shift = shift;
+    return AGP_OK;
+}
+
 int agp_graph_set_column_tile(agp_graph_t g, int32_t columns)
 {
     if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");

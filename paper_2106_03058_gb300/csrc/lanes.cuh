@@ -24,6 +24,7 @@ constexpr uint32_t kOffsetsOnHost = 0x80000000u;  // internal query flag: x_off 
                                                    // when x_idx / x_val are on the device
 constexpr uint32_t kSampleTag = 0x53414D50u;  // Philox counter word of the skip sampler
 constexpr uint32_t kDenseTag = 0x44534E53u;   // Philox counter word of the per-position sampler
+constexpr uint32_t kPullTag = 0x50554C4Cu;    // Philox counter word of the edge trials of a pull level
 
 struct LaneParam {
     double eps_d;     // eps (FP64) for the push/sample decision
@@ -34,6 +35,7 @@ struct LaneParam {
     int32_t b_mode;
     int32_t L;
     int32_t out_row;  // query / column index (statistics and bookkeeping)
+    int32_t sampler;  // 0: geometric skips / per-position trials; 1: the paper's Binomial-count scheme
     uint32_t key0, key1;
     float *out;       // pi(u) of this lane accumulates at out[u * su]
     int64_t su;
@@ -96,6 +98,14 @@ struct KArgs {
     int ubits;
     uint32_t umask;
     int W;                    // lanes per group
+    int rows_in;              // rows are in-neighbour lists (deg[] is not the row length)
+    int groups;               // the wave may hold lanes of the paper's group sampler
+    float *C;                 // [G / W][ldR][W]: c(u) of the lanes that pull this level (else 0)
+    unsigned long long *lane_count;  // [G] frontier volume (sum of d_u) of each lane, from the compaction
+    int32_t *pull;            // [G] 1: the lane pulls this level; [G + g]: group g has a pulling lane
+    int64_t pull_min;         // frontier volume from which a lane pulls (> nnz: never)
+    const int32_t *rows[3];   // rows by length class (pull levels)
+    int64_t row_count[3];
     float *R;                 // [G / W][ldR][W]
     uint32_t *items;          // current frontier, ascending (group << ubits | u)
     float *rval;              // [item][W]: r^(i)(u) of the group's lanes
@@ -142,6 +152,9 @@ struct Workspace {
     uint2 *nrec = nullptr;
     unsigned long long *rpart = nullptr;
     uint2 *det_rec = nullptr, *smp_rec = nullptr;
+    float *C = nullptr;
+    unsigned long long *lane_count = nullptr;
+    int32_t *pull = nullptr;
     LaneParam *lanes = nullptr;
     float2 *coef = nullptr;
     int32_t *level = nullptr;
@@ -164,6 +177,7 @@ struct Workspace {
     int graph_levels = -1;
     int graph_collect = -1;
     int graph_profile = -1;
+    int graph_groups = -1;
     // AGP_PROFILE events: [level][kernel][begin/end]
     cudaEvent_t ev[kMaxLevels][kProfKernels][2] = {};
     bool ev_ready = false;
@@ -204,7 +218,9 @@ size_t bytes_per_lane(const agp_graph_s *g);
 int lane_capacity(const agp_graph_s *g);
 // Group width of a wave of G lanes: 4 when G is a multiple of 4, else 2 when even, else 1.
 inline int group_width(int G) { return (G % 4 == 0) ? 4 : (G % 2 == 0) ? 2 : 1; }
-int create_workspace(agp_graph_s *g, int G, int W, Workspace **out);
+// grid > 0: blocks of the grid-stride level kernels (default 8 per SM); a smaller grid leaves SM
+// slots to kernels of other streams (the server's heavy pool)
+int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid = 0);
 KArgs make_args(agp_graph_s *g, Workspace *ws, int collect);
 int blocks_for(unsigned long long work, int per_block);
 void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,

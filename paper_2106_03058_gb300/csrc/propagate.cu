@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <limits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -107,25 +108,25 @@ __device__ __forceinline__ int32_t ld_col(const int32_t *p)
 // as red.global explicitly: for a pointer loaded from memory (an output row of the lane parameters)
 // the compiler cannot prove the global space and would issue a returning generic atomic. The next
 // frontier is not tracked during the pushes: each level starts by scanning the residue vectors (see
-// k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly.
+// k_compact_*), which finds F_i = {u : r^(i)(u) != 0} exactly. No kernel reads what it reduces into,
+// so the reductions carry no memory clobber: values the kernel holds (lane parameters, the walk's
+// lane states) stay in registers across them.
 __device__ __forceinline__ void red_add(float *p, float v)
 {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v));
 }
 
 // The W residues of one node are contiguous and W-float aligned (vectors start 4 KB-aligned), so the
 // increments of several lanes at one neighbour go out as one vector reduction.
 __device__ __forceinline__ void red_add_v2(float *p, float a, float b)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b)
-                 : "memory");
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b));
 }
 
 __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
 {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b),
-                 "f"(c), "f"(d)
-                 : "memory");
+                 "f"(c), "f"(d));
 }
 
 __device__ __forceinline__ void push_to(float *p, float inc)
@@ -176,9 +177,57 @@ struct Uniforms {
     }
 };
 
+// The paper's subset-sampling scheme (Section 4) for positions [j, gend) of one degree group whose
+// largest probability is pstar: the number of trials is Binomial(m, pstar), the trial positions are
+// chosen uniformly without replacement, and a reached neighbour is kept with probability p_v / pstar.
+// The group is taken in chunks of at most min(64, 10 / pstar) positions: the inversion then starts
+// from (1 - pstar)^m >= e^-10.6 (representable in FP32), and Floyd's algorithm keeps the chosen set
+// in a 64-bit mask. Chunks are independent, so the positions are still independent Bernoulli(pstar)
+// trials, which is the distribution the scheme draws.
+template <int W>
+__device__ __forceinline__ void sample_group_paper(const KArgs &A, const LaneParam &P, float *Rs, Uniforms &U,
+                                                   const int32_t *row, int j, int gend, float pstar, float ce,
+                                                   unsigned long long &drawn, unsigned long long &accepted)
+{
+    const int chunk = (pstar >= 1.f) ? 64 : max(1, (int)fminf(10.f / pstar, 64.f));
+    for (int c0 = j; c0 < gend; c0 += chunk) {
+        const int m = min(chunk, gend - c0);
+        int cnt = m;  // pstar = 1: every position is a trial
+        if (pstar < 1.f) {
+            const float x = U.next();
+            const float ratio = pstar / (1.f - pstar);
+            float pk = expf((float)m * log1pf(-pstar));  // Binomial pmf at 0
+            float F = pk;
+            cnt = 0;
+            while (x > F && cnt < m) {
+                pk *= (float)(m - cnt) / (float)(cnt + 1) * ratio;
+                ++cnt;
+                F += pk;
+            }
+        }
+        uint64_t chosen = 0;  // Floyd: for t = m - cnt .. m - 1 pick r in [0, t], or t if r is taken
+        for (int t = m - cnt; t < m; ++t) {
+            const int r = min((int)(U.next() * (float)(t + 1)), t);
+            chosen |= ((chosen >> r) & 1ull) ? (1ull << t) : (1ull << r);
+        }
+        while (chosen) {
+            const int pos = c0 + __ffsll((long long)chosen) - 1;
+            chosen &= chosen - 1;
+            const int32_t v = ld_col(row + pos);
+            ++drawn;
+            bool keep = true;
+            if (P.a_mode != 0) keep = U.next() * pstar < apply_deg(ce, A.g.deg[v], P.a_mode, P.a);
+            if (keep) {
+                ++accepted;
+                push_to(Rs + (size_t)v * W, P.eps);
+            }
+        }
+    }
+}
+
 // Subset sampling of row positions [j0, j1) (Section 4), stream (u, level, seg) of the lane. Rs is
 // the lane's residue at node 0 (group block + slot); node v's residue is Rs[v * W].
-template <int kSampleBatch, int W>
+template <int kSampleBatch, int W, bool kGroups = false>
 __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rs, int32_t u, int lvl, uint32_t seg,
                              const int32_t *row, int j0, int j1, float c, unsigned long long &drawn,
                              unsigned long long &accepted)
@@ -206,6 +255,11 @@ __device__ void sample_range(const KArgs &A, const LaneParam &P, float *Rs, int3
         }
         pstar = fminf(pstar, 1.f);
         if (!(pstar > 0.f)) { j = gend; continue; }
+        if constexpr (kGroups) {  // AGP_SAMPLER_GROUPS: the paper's Binomial-count scheme for this group
+            sample_group_paper<W>(A, P, Rs, U, row, j, gend, pstar, ce, drawn, accepted);
+            j = gend;
+            continue;
+        }
         // geometric skip: floor(ln U / ln(1 - p*)) positions are passed over before the next trial.
         // Trials are taken kSampleBatch at a time: their uniforms are drawn first, in the order of
         // one trial after the other (skip, then the acceptance uniform when a > 0), so that the
@@ -432,15 +486,47 @@ template <int W>
 __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
 {
     __shared__ unsigned long long red[kBlock / 32];
+    __shared__ unsigned long long slot_n[kBlock / 32][W];
     int64_t begin, end;
     compact_range(A, begin, end);
     unsigned long long c = 0;
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t unit = begin; unit < end; ++unit) {
         int grp;
         int64_t off_f;
         bool live;
         const float4 *p = unit_ptr<W>(A, unit, grp, off_f, live);
-        if (live) c += nz_items<W>(p[threadIdx.x]);
+        if (!live) continue;  // uniform over the block
+        const float4 v = p[threadIdx.x];
+        c += nz_items<W>(v);
+        if (A.C) {
+            // the C block of a group that pulled the previous level is cleared here, before this
+            // level's expansion writes it again
+            if (A.pull[A.G + grp]) reinterpret_cast<float4 *>(A.C + (size_t)grp * A.ldR * W + off_f)[threadIdx.x] =
+                make_float4(0.f, 0.f, 0.f, 0.f);
+            // frontier volume per lane, sum of d_u over r(u) != 0 (the pull decision of the level)
+            const float e[4] = {v.x, v.y, v.z, v.w};
+            const int64_t node0 = (off_f + 4 * threadIdx.x) / W;
+            unsigned long long ns[W];
+#pragma unroll
+            for (int sl = 0; sl < W; ++sl) {
+                ns[sl] = 0;
+#pragma unroll
+                for (int k = sl; k < 4; k += W) {
+                    const int64_t nd = node0 + k / W;
+                    if (e[k] != 0.f && nd < A.g.n) ns[sl] += (unsigned long long)(A.g.rowptr[nd + 1] - A.g.rowptr[nd]);
+                }
+                for (int o = 16; o > 0; o >>= 1) ns[sl] += __shfl_down_sync(0xffffffffu, ns[sl], o);
+                if (lane_id == 0) slot_n[warp][sl] = ns[sl];
+            }
+            __syncthreads();
+            if (threadIdx.x < W) {
+                unsigned long long t = 0;
+                for (int w = 0; w < kBlock / 32; ++w) t += slot_n[w][threadIdx.x];
+                if (t) atomicAdd(&A.lane_count[grp * W + threadIdx.x], t);
+            }
+            __syncthreads();
+        }
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -470,6 +556,23 @@ __global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
         run += (unsigned long long)v;
     }
     if (t == 0) A.ctrl->n_items = total;
+    if (A.C) {
+        // pull or push, per lane, from its own frontier size (so a lane's mode does not depend on the
+        // other lanes of its batch); a lane at its last level pushes nothing
+        for (int l = t; l < A.G; l += blockDim.x) {
+            const unsigned long long vol = A.lane_count[l];
+            A.lane_count[l] = 0;
+            const int lvl = A.level[l];
+            A.pull[l] = (lvl >= 0 && lvl < A.lanes[l].L && vol > 0 && (int64_t)vol >= A.pull_min && !A.lanes[l].sampler)
+                            ? 1 : 0;
+        }
+        __syncthreads();
+        for (int gi = t; gi < A.G / A.W; gi += blockDim.x) {
+            int any = 0;
+            for (int sl = 0; sl < A.W; ++sl) any |= A.pull[gi * A.W + sl];
+            A.pull[A.G + gi] = any;
+        }
+    }
 }
 
 // Pass 3: units are taken four at a time. The four float4 loads of a thread are issued together,
@@ -579,9 +682,10 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
     const uint32_t item = __ldg(A.items + idx);
     const int grp = (int)(item >> A.ubits);
     const int32_t u = (int32_t)(item & A.umask);
-    const int32_t du = __ldg(A.g.deg + u);     // d_u of the normalisation
     const int64_t e0 = __ldg(A.g.rowptr + u);
-    const int d = (int)(__ldg(A.g.rowptr + u + 1) - e0);  // row length (d_u except on in-neighbour rows)
+    const int d = (int)(__ldg(A.g.rowptr + u + 1) - e0);  // row length
+    const int32_t du = A.rows_in ? __ldg(A.g.deg + u) : d;  // d_u of the normalisation (the row length
+                                                            // except on in-neighbour rows)
     float *Rg = A.R + (size_t)grp * A.ldR * W;  // r^(i+1): the compaction emptied r^(i)
     const int32_t *row = A.g.colidx + e0;
     int J = 0, nseg = 0;
@@ -605,6 +709,10 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
         if (lvl >= P.L || d == 0 || (du == 0 && P.b_mode != 0)) continue;
         const float c = apply_deg(cf.y * rj, du, P.b_mode, P.b);  // (Y_{i+1}/Y_i) r / d_u^b
         if (!(c > 0.f)) continue;
+        if (A.C && A.pull[lane]) {  // this level pulls: the targets gather c(u) (k_pull_*)
+            A.C[((size_t)grp * A.ldR + u) * W + j] = c;
+            continue;
+        }
         const int k = det_prefix(c, P, row, d, A.g.deg);
         const int tail = d - k;
         bool is_dense = false;
@@ -614,9 +722,9 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
             const float ce = c * P.inv_eps;
             const float p0 = fminf(1.f, (P.a_mode == 0) ? ce : apply_deg(ce, A.g.deg[row[k]], P.a_mode, P.a));
             const float expect = p0 * (float)tail;  // upper bound on the trials reached
-            if (expect <= kLightSamples) {
+            if (expect <= kLightSamples && !P.sampler) {
                 sample_range<2, W>(A, P, Rg + j, u, lvl, 0u, row, k, d, c, drawn, accepted);
-            } else if (p0 >= kDenseP) {
+            } else if (p0 >= kDenseP && !P.sampler) {
                 is_dense = true;  // most positions are kept: one Bernoulli per position in the walk
             } else {
                 int ns = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
@@ -801,23 +909,31 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         const int64_t e0 = A.g.rowptr[u];
         const int d = (int)(A.g.rowptr[u + 1] - e0);  // row length
         const uint32_t flags = A.flag_item[idx];
-        __syncwarp();
-        if (lane_id < W) {
-            const int j = lane_id;
-            WalkLane L = idle_walk_lane();
-            if ((flags >> (8 + j)) & 1u) {
-                const int lane = grp * W + j;
-                L = walk_lane(A.lanes[lane], A.c_item[idx * W + j], A.k_item[idx * W + j], (flags >> j) & 1u,
-                              A.level[lane]);
+        // the record's lane states: in registers for a single lane, else in the warp's shared slot
+        WalkLane L1[1];
+        const WalkLane *Ls = L1;
+        if constexpr (W == 1) {
+            L1[0] = walk_lane(A.lanes[grp], A.c_item[idx], A.k_item[idx], flags & 1u, A.level[grp]);
+        } else {
+            __syncwarp();
+            if (lane_id < W) {
+                const int j = lane_id;
+                WalkLane L = idle_walk_lane();
+                if ((flags >> (8 + j)) & 1u) {
+                    const int lane = grp * W + j;
+                    L = walk_lane(A.lanes[lane], A.c_item[idx * W + j], A.k_item[idx * W + j], (flags >> j) & 1u,
+                                  A.level[lane]);
+                }
+                sL[warp][j] = L;
             }
-            sL[warp][j] = L;
+            __syncwarp();
+            Ls = sL[warp];
         }
-        __syncwarp();
         int J = 0;
         bool need_deg = false;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const WalkLane &L = sL[warp][j];
+            const WalkLane &L = Ls[j];
             if (L.dense < 0) continue;
             J = max(J, L.dense > 0 ? d : L.k);
             need_deg |= L.a_mode != 0;
@@ -826,11 +942,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
         const int32_t *row = A.g.colidx + e0;
         const int c0 = (int)Rc.y * kChunk, c1 = min(J, c0 + kChunk);
         unsigned int acc[W] = {};
-        for (int p0 = c0 + 4 * lane_id; p0 < c1; p0 += 128) walk4<W>(A, Rg, sL[warp], u, row, p0, min(p0 + 4, c1), need_deg, acc);
+        for (int p0 = c0 + 4 * lane_id; p0 < c1; p0 += 128) walk4<W>(A, Rg, Ls, u, row, p0, min(p0 + 4, c1), need_deg, acc);
         if (A.collect) {
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                const WalkLane &L = sL[warp][j];
+                const WalkLane &L = Ls[j];
                 if (L.dense < 0) continue;
                 const int lane = grp * W + j;
                 if (lane_id == 0) {
@@ -847,7 +963,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_push(KArgs A)
 
 // One thread per sparse-tail segment: record (item, s), s counting the segments of the item's lanes
 // in slot order.
-template <int W>
+// kGroups: the wave may hold lanes of the paper's group sampler (AGP_SAMPLER_GROUPS); the default
+// instantiation carries no code of that scheme
+template <int W, bool kGroups>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
 {
     const unsigned long long n_smp = min(A.ctrl->n_smp, A.cap_smp);
@@ -888,11 +1006,179 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_sample(KArgs A)
         const int j0 = k + s * seglen, j1 = min(d, j0 + seglen);
         const int32_t *row = A.g.colidx + e0;
         unsigned long long drawn = 0, accepted = 0;
-        sample_range<4, W>(A, P, Rs, u, lvl, (uint32_t)s, row, j0, j1, c, drawn, accepted);
+        if (kGroups && P.sampler) sample_range<4, W, true>(A, P, Rs, u, lvl, (uint32_t)s, row, j0, j1, c, drawn, accepted);
+        else sample_range<4, W>(A, P, Rs, u, lvl, (uint32_t)s, row, j0, j1, c, drawn, accepted);
         if (A.collect && (drawn | accepted)) {
             atomicAdd(&A.stats[lane].by_kernel[2][1], drawn);
             atomicAdd(&A.stats[lane].by_kernel[2][2], accepted);
         }
+    }
+}
+
+// ---- pull levels -------------------------------------------------------------------------------
+// A lane whose frontier covers a large part of the graph spends most of a pushed level on random
+// reductions into r^(i+1). On an undirected graph the row of v lists exactly the nodes that push to
+// v, so the same level can be computed by the targets: every node v walks its row once for the
+// group, gathers c(u) of the pulling lanes (published by the expansion in the C block) and adds, per
+// lane and edge, what Algorithm 2 adds there: c(u) / d_v^a when that increment passes the push test,
+// else eps with probability (c(u) / eps) / d_v^a. The trial of edge (u, v) uses word 0 of the Philox
+// block (u, v, level, kPullTag) under the lane's key. The sums land in the lane's own slot of R with
+// plain stores: no other kernel writes a pulling lane's slot during the level, and the compaction
+// left it zero.
+struct PullLane {
+    LaneParam P;
+    int lvl;
+    int on;
+};
+
+template <int W>
+__device__ __forceinline__ void pull_edge(const PullLane *L, float4 cu4, int32_t u, int32_t v, int32_t dv,
+                                          float (&acc)[W], unsigned int (&cnt)[W][3])
+{
+    const float cu[4] = {cu4.x, cu4.y, cu4.z, cu4.w};
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const float c = cu[j];
+        if (!L[j].on || !(c > 0.f)) continue;
+        const LaneParam &P = L[j].P;
+        if (P.eps_d == 0.0 || push_test(c, dv, P)) {
+            acc[j] += (P.a_mode == 0) ? c : apply_deg(c, dv, P.a_mode, P.a);
+            ++cnt[j][0];
+        } else {
+            const float p = (P.a_mode == 0) ? c * P.inv_eps : apply_deg(c * P.inv_eps, dv, P.a_mode, P.a);
+            const Philox4 q = philox4x32_10((uint32_t)u, (uint32_t)v, (uint32_t)L[j].lvl, kPullTag, P.key0, P.key1);
+            ++cnt[j][1];
+            if (u01_open(q.x) < p) {
+                acc[j] += P.eps;
+                ++cnt[j][2];
+            }
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ float4 load_c(const float *Cg, int32_t u)
+{
+    if constexpr (W == 4) return __ldg(reinterpret_cast<const float4 *>(Cg) + u);
+    else if constexpr (W == 2) {
+        const float2 c = __ldg(reinterpret_cast<const float2 *>(Cg) + u);
+        return make_float4(c.x, c.y, 0.f, 0.f);
+    } else {
+        return make_float4(__ldg(Cg + u), 0.f, 0.f, 0.f);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void pull_store(const KArgs &A, const PullLane *L, float *Rg, int32_t v,
+                                           const float (&acc)[W])
+{
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (L[j].on && acc[j] != 0.f) Rg[(size_t)v * W + j] = acc[j];
+}
+
+template <int W>
+__device__ __forceinline__ void pull_stats(const KArgs &A, int grp, const PullLane *L, const unsigned int (&cnt)[W][3])
+{
+    if (!A.collect) return;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (L[j].on && (cnt[j][0] | cnt[j][1])) {
+            LaneStats &S = A.stats[grp * W + j];
+            atomicAdd(&S.by_kernel[1][0], (unsigned long long)cnt[j][0]);
+            atomicAdd(&S.by_kernel[1][1], (unsigned long long)cnt[j][1]);
+            atomicAdd(&S.by_kernel[1][2], (unsigned long long)cnt[j][2]);
+        }
+}
+
+// the group's lane states into shared memory (threads 0..W-1), read by every thread of the block
+template <int W>
+__device__ __forceinline__ void pull_lanes(const KArgs &A, int grp, PullLane *L)
+{
+    if (threadIdx.x < W) {
+        const int lane = grp * W + threadIdx.x;
+        L[threadIdx.x].on = A.pull[lane];
+        L[threadIdx.x].lvl = A.level[lane];
+        L[threadIdx.x].P = A.lanes[lane];
+    }
+}
+
+// CLS 0: short rows, a thread each; 1: medium rows, a warp each; 2: long rows, a block each
+template <int W, int CLS>
+__global__ void __launch_bounds__(kBlock) k_pull(KArgs A)
+{
+    if (!A.C) return;
+    __shared__ float part[kBlock / 32][W];
+    __shared__ PullLane L[W];
+    const int groups = (min((int)A.ctrl->lanes_used, A.G) + W - 1) / W;
+    const int64_t count = A.row_count[CLS];
+    const int32_t *rows = A.rows[CLS];
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int grp = 0; grp < groups; ++grp) {
+        if (!A.pull[A.G + grp]) continue;  // uniform over the grid
+        __syncthreads();  // the previous group's states are no longer read
+        pull_lanes<W>(A, grp, L);
+        __syncthreads();
+        const float *Cg = A.C + (size_t)grp * A.ldR * W;
+        float *Rg = A.R + (size_t)grp * A.ldR * W;
+        unsigned int cnt[W][3] = {};
+        if constexpr (CLS == 0) {
+            for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+                const int32_t v = rows[r];
+                const int64_t e0 = A.g.rowptr[v], e1 = A.g.rowptr[v + 1];
+                const int32_t dv = (int32_t)(e1 - e0);
+                float acc[W] = {};
+                for (int64_t e = e0; e < e1; ++e) {
+                    const int32_t u = ld_col(A.g.colidx + e);
+                    pull_edge<W>(L, load_c<W>(Cg, u), u, v, dv, acc, cnt);
+                }
+                pull_store<W>(A, L, Rg, v, acc);
+            }
+        } else if constexpr (CLS == 1) {
+            const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+            for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < count; r += nw) {
+                const int32_t v = rows[r];
+                const int64_t e0 = A.g.rowptr[v], e1 = A.g.rowptr[v + 1];
+                const int32_t dv = (int32_t)(e1 - e0);
+                float acc[W] = {};
+                for (int64_t e = e0 + lane_id; e < e1; e += 32) {
+                    const int32_t u = ld_col(A.g.colidx + e);
+                    pull_edge<W>(L, load_c<W>(Cg, u), u, v, dv, acc, cnt);
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+                if (lane_id == 0) pull_store<W>(A, L, Rg, v, acc);
+            }
+        } else {
+            for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
+                const int32_t v = rows[r];
+                const int64_t e0 = A.g.rowptr[v], e1 = A.g.rowptr[v + 1];
+                const int32_t dv = (int32_t)(e1 - e0);
+                float acc[W] = {};
+                for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                    const int32_t u = ld_col(A.g.colidx + e);
+                    pull_edge<W>(L, load_c<W>(Cg, u), u, v, dv, acc, cnt);
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+                    if (lane_id == 0) part[warp][j] = acc[j];
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    float tot[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        tot[j] = 0.f;
+                        for (int w = 0; w < kBlock / 32; ++w) tot[j] += part[w][j];
+                    }
+                    pull_store<W>(A, L, Rg, v, tot);
+                }
+                __syncthreads();
+            }
+        }
+        pull_stats<W>(A, grp, L, cnt);
     }
 }
 
@@ -1171,7 +1457,8 @@ size_t bytes_per_lane(const agp_graph_s *g)
     // per (lane, node): R (4), the item's residue, c, k and segment length (16), and the lane's share
     // of the item id, flags and record counts (16, as if every lane were its own group); walk-chunk
     // records (8, with the extra records of long rows) and segment records (8, likewise)
-    return n * (4 + 16 + 16) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
+    // (+ 4 for the c(u) block of pull levels)
+    return n * (4 + 4 + 16 + 16) + (size_t)(n * 8 * (1.0 + avg / kChunk)) + (size_t)(n * 8 * (1.0 + avg / kMinSeg)) + 8192;
 }
 
 // Lanes a workspace can hold: the group index of an item has 32 - ubits bits, and the item lists
@@ -1203,6 +1490,9 @@ void free_workspace(Workspace *ws)
     cudaFree(ws->rpart);
     cudaFree(ws->det_rec);
     cudaFree(ws->smp_rec);
+    cudaFree(ws->C);
+    cudaFree(ws->lane_count);
+    cudaFree(ws->pull);
     cudaFree(ws->lanes);
     cudaFree(ws->coef);
     cudaFree(ws->level);
@@ -1245,7 +1535,7 @@ int lanes_for_budget(agp_graph_s *g, int64_t held, int *lanes)
     return AGP_OK;
 }
 
-int create_workspace(agp_graph_s *g, int G, int W, Workspace **out)
+int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid)
 {
     if (W != 1 && W != 2 && W != 4) return fail(AGP_EINTERNAL, "group width must be 1, 2 or 4");
     G = (G + W - 1) / W * W;
@@ -1267,7 +1557,7 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out)
     const int64_t node_unit = kScanUnit / W;  // nodes per scanned unit of a group block
     ws->ldR = ((int64_t)n + node_unit - 1) / node_unit * node_unit;
     const int64_t units = (int64_t)groups * (ws->ldR * W / kScanUnit);
-    ws->grid = grid_stride_blocks();
+    ws->grid = grid > 0 ? grid : grid_stride_blocks();
     ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid, units));
     A(dev_alloc(&ws->R, (size_t)G * ws->ldR, acc));
     A(dev_alloc(&ws->items, ws->cap_items, acc));
@@ -1281,6 +1571,13 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out)
     A(dev_alloc(&ws->rpart, (size_t)2 * ws->grid, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
+    // pull levels (undirected graphs): c(u) block beside R, per-lane frontier counts and modes
+    if (!g->directed) {
+        A(dev_alloc(&ws->C, (size_t)G * ws->ldR, acc));
+        A(dev_alloc(&ws->lane_count, (size_t)G, acc));
+        A(dev_alloc(&ws->pull, (size_t)2 * G, acc));
+        if (rc == AGP_OK) rc = ensure_row_lists(g, 0);
+    }
     A(dev_alloc(&ws->lanes, (size_t)G, acc));
     A(dev_alloc(&ws->coef, (size_t)G * kMaxLevels, acc));
     A(dev_alloc(&ws->level, (size_t)G, acc));
@@ -1290,6 +1587,9 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out)
     if (rc == AGP_OK && cudaMallocHost((void **)&ws->h_lanes, sizeof(LaneParam) * G) != cudaSuccess) rc = fail(AGP_ENOMEM, "cudaMallocHost");
     if (rc == AGP_OK) {
         cudaError_t e = cudaMemset(ws->R, 0, sizeof(float) * (size_t)G * ws->ldR);
+        if (e == cudaSuccess && ws->C) e = cudaMemset(ws->C, 0, sizeof(float) * (size_t)G * ws->ldR);
+        if (e == cudaSuccess && ws->lane_count) e = cudaMemset(ws->lane_count, 0, sizeof(unsigned long long) * G);
+        if (e == cudaSuccess && ws->pull) e = cudaMemset(ws->pull, 0, sizeof(int32_t) * 2 * G);
         if (e == cudaSuccess) e = cudaMemset(ws->level, 0xff, sizeof(int32_t) * G);
         if (e == cudaSuccess) e = cudaMemset(ws->ctrl, 0, sizeof(Ctrl));
         if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(LaneStats) * G);
@@ -1425,6 +1725,17 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.collect = collect;
     A.G = ws->G;
     A.grid = ws->grid;
+    A.rows_in = g->directed == 2 ? 1 : 0;
+    A.groups = 0;
+    A.C = ws->C;
+    A.lane_count = ws->lane_count;
+    A.pull = ws->pull;
+    A.pull_min = (g->pull_shift >= 0 && g->pull_shift < 63) ? std::max<int64_t>(1, g->nnz >> g->pull_shift)
+                                                           : std::numeric_limits<int64_t>::max();
+    for (int c = 0; c < 3; ++c) {
+        A.rows[c] = g->row_list[c];
+        A.row_count[c] = g->row_count[c];
+    }
     A.ctrl = ws->ctrl;
     return A;
 }
@@ -1457,7 +1768,17 @@ template <int W> void launch_expand_w(const KArgs &A, cudaStream_t s)
 }
 
 template <int W> void launch_push_w(const KArgs &A, cudaStream_t s, int blocks) { k_push<W><<<blocks, kBlock, 0, s>>>(A); }
-template <int W> void launch_sample_w(const KArgs &A, cudaStream_t s, int blocks) { k_sample<W><<<blocks, kBlock, 0, s>>>(A); }
+template <int W> void launch_sample_w(const KArgs &A, cudaStream_t s, int blocks)
+{
+    if (A.groups) k_sample<W, true><<<blocks, kBlock, 0, s>>>(A);
+    else k_sample<W, false><<<blocks, kBlock, 0, s>>>(A);
+}
+template <int W> void launch_pull_w(const KArgs &A, cudaStream_t s)
+{
+    k_pull<W, 0><<<A.grid, kBlock, 0, s>>>(A);
+    k_pull<W, 1><<<A.grid, kBlock, 0, s>>>(A);
+    k_pull<W, 2><<<(int)std::max<int64_t>(1, std::min<int64_t>(A.row_count[2], A.grid)), kBlock, 0, s>>>(A);
+}
 
 #define AGP_BY_WIDTH(fn, ...)                         \
     do {                                              \
@@ -1470,6 +1791,10 @@ void launch_compact(const KArgs &A, cudaStream_t s) { AGP_BY_WIDTH(launch_compac
 void launch_expand(const KArgs &A, cudaStream_t s) { AGP_BY_WIDTH(launch_expand_w, A, s); }
 void launch_push(const KArgs &A, cudaStream_t s, int blocks) { AGP_BY_WIDTH(launch_push_w, A, s, blocks); }
 void launch_sample(const KArgs &A, cudaStream_t s, int blocks) { AGP_BY_WIDTH(launch_sample_w, A, s, blocks); }
+void launch_pull(const KArgs &A, cudaStream_t s)
+{
+    if (A.C) AGP_BY_WIDTH(launch_pull_w, A, s);
+}
 
 // One level: compact, expand, push, sample, level end. With `ev` (profiling) every step is
 // bracketed by event records on the same stream.
@@ -1488,6 +1813,7 @@ void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_bl
     launch_push(A, s, push_blocks);
     if (ev) { rec(ev[2][1]); rec(ev[3][0]); }
     launch_sample(A, s, sample_blocks);
+    launch_pull(A, s);
     if (ev) { rec(ev[3][1]); rec(ev[4][0]); }
     k_level_end<<<1, kBlock, 0, s>>>(A);
     if (ev) rec(ev[4][1]);
@@ -1592,6 +1918,8 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
             __atomic_fetch_add(&g->kernel_launches, (int64_t)(4 + (nd ? 1 : 0) + (ns ? 1 : 0)), __ATOMIC_RELAXED);
             if (nd) { rec(2, 0); launch_push(A, s, blocks_for(nd, kBlock / 32)); rec(2, 1); ran[lvl * kProfKernels + 2] = true; }
             if (ns) { rec(3, 0); launch_sample(A, s, blocks_for(ns, kBlock)); rec(3, 1); ran[lvl * kProfKernels + 3] = true; }
+            launch_pull(A, s);
+            if (A.C) __atomic_fetch_add(&g->kernel_launches, (int64_t)3, __ATOMIC_RELAXED);
             rec(4, 0);
             k_level_end<<<1, kBlock, 0, s>>>(A);
             rec(4, 1);
@@ -1604,7 +1932,8 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         }
         return AGP_OK;
     }
-    if (!ws->graph || ws->graph_levels != max_L || ws->graph_collect != A.collect || ws->graph_profile != (int)profile) {
+    if (!ws->graph || ws->graph_levels != max_L || ws->graph_collect != A.collect || ws->graph_profile != (int)profile ||
+        ws->graph_groups != A.groups) {
         if (ws->graph) {
             cudaGraphExecDestroy(ws->graph);
             ws->graph = nullptr;
@@ -1613,9 +1942,10 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         ws->graph_levels = max_L;
         ws->graph_collect = A.collect;
         ws->graph_profile = (int)profile;
+        ws->graph_groups = A.groups;
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
-    __atomic_fetch_add(&g->kernel_launches, (int64_t)(kKernelsPerLevel * (max_L + 1)), __ATOMIC_RELAXED);
+    __atomic_fetch_add(&g->kernel_launches, (int64_t)((kKernelsPerLevel + (A.C ? 3 : 0)) * (max_L + 1)), __ATOMIC_RELAXED);
     ws->prof_levels = profile ? max_L + 1 : 0;  // read when the wave is checked
     return AGP_OK;
 }
@@ -1640,7 +1970,7 @@ struct LaneSpec {
 // uploaded from the workspace's pinned staging on stream s. The workspace must be idle (its
 // previous wave checked), which is what makes reusing the pinned staging safe without a sync.
 int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lanes, size_t first, int count,
-                 const agp_params_t *params, uint64_t stream_base_is_query, bool eps_absolute, float *out, int64_t su,
+                 const agp_params_t *params, uint64_t stream_base_is_query, bool eps_absolute, bool sampler_groups, float *out, int64_t su,
                  int64_t sr, const std::vector<int32_t> &aux, int32_t **d_aux, cudaStream_t s, int *max_L)
 {
     *max_L = 0;
@@ -1675,6 +2005,7 @@ int prepare_wave(agp_graph_s *g, Workspace *ws, const std::vector<LaneSpec> &lan
         P.b_mode = exponent_mode(p.b);
         P.L = p.L;
         P.out_row = ls.query;
+        P.sampler = sampler_groups ? 1 : 0;
         P.out = out + (int64_t)ls.query * sr;
         P.su = su;
         lane_param_derive(P);
@@ -1741,6 +2072,7 @@ struct WaveJob {
     int64_t su, sr;
     uint64_t stream_base_is_query;
     bool eps_absolute = false;  // eps in raw signal units: a lane uses eps / ||x+-||_1
+    bool sampler_groups = false;  // AGP_SAMPLER_GROUPS
     std::function<void(size_t first, int count, std::vector<int32_t> &aux)> make_aux;
     std::function<int(const KArgs &A, int count, const int32_t *d_aux, cudaStream_t st)> seed;
     // optional: called on the wave's stream after its levels, once every earlier wave is complete
@@ -1817,11 +2149,13 @@ int run_waves(agp_graph_s *g, ExecCtx *ctx, Workspace *ws0, const std::vector<La
         job.make_aux(first, count, aux);
         int32_t *d_aux = nullptr;
         int max_L = 0;
-        if ((rc = prepare_wave(g, W, lanes, first, count, params, job.stream_base_is_query, job.eps_absolute, job.out,
+        if ((rc = prepare_wave(g, W, lanes, first, count, params, job.stream_base_is_query, job.eps_absolute,
+                               job.sampler_groups, job.out,
                                job.su, job.sr, aux, &d_aux, st, &max_L)) != AGP_OK)
             break;
         if ((rc = reset_ctrl(W, count, st)) != AGP_OK) break;
-        const KArgs A = make_args(g, W, collect);
+        KArgs A = make_args(g, W, collect);
+        A.groups = job.sampler_groups ? 1 : 0;
         if ((rc = job.seed(A, count, d_aux, st)) != AGP_OK) break;
         __atomic_fetch_add(&g->kernel_launches, (int64_t)2, __ATOMIC_RELAXED);  // coefficients + seed
         if ((rc = run_levels(g, W, A, max_L, plain, profile, st)) != AGP_OK) break;
@@ -1887,7 +2221,7 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
     if (!x_off || !pi_out) return fail(AGP_EINVAL, "x_off / pi_out NULL");
     if (ld_out < g->n) return fail(AGP_EINVAL, "ld_out < n");
     if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
-                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | kOffsetsOnHost))
+                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | AGP_SAMPLER_GROUPS | kOffsetsOnHost))
         return fail(AGP_EINVAL, "unknown flag");
     // offsets on the device only when the inputs are and the caller did not pass them from the host
     const bool off_dev = (flags & AGP_INPUT_ON_DEVICE) && !(flags & kOffsetsOnHost);
@@ -2009,6 +2343,7 @@ int run_queries(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, int32_
     // from the stream (seed, q), so that they do not repeat one another's draws on common nodes
     job.stream_base_is_query = (n_params == 1) ? 1 : 0;
     job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
+    job.sampler_groups = flags & AGP_SAMPLER_GROUPS;
     if (flags & AGP_QUERY_TIMES) job.times = stats;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.assign(2 * (size_t)Q, -1);
@@ -2057,7 +2392,7 @@ int query_dense(agp_graph_s *g, const agp_params_t *params, int32_t n_params, in
     if (ldx < n || ld_out < n) return fail(AGP_EINVAL, "ldx and ld_out must be >= n");
     if (n > 0 && (!X || !pi_out)) return fail(AGP_EINVAL, "X / pi_out NULL");
     if (flags & ~(AGP_INPUT_ON_DEVICE | AGP_OUTPUT_ON_DEVICE | AGP_PLAIN | AGP_COLLECT_STATS | AGP_PROFILE |
-                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | AGP_DENSE_BF16))
+                  AGP_QUERY_TIMES | AGP_EPS_ABSOLUTE | AGP_DENSE_BF16 | AGP_SAMPLER_GROUPS))
         return fail(AGP_EINVAL, "unknown flag");
     if ((flags & (AGP_COLLECT_STATS | AGP_QUERY_TIMES)) && !stats)
         return fail(AGP_EINVAL, "AGP_COLLECT_STATS / AGP_QUERY_TIMES need stats");
@@ -2118,7 +2453,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
 {
     if (!g || !params) return fail(AGP_EINVAL, "NULL argument");
     if (d < 0 || ldx < d || ldz < d) return fail(AGP_EINVAL, "need d >= 0, ldx >= d, ldz >= d");
-    if (flags & ~(AGP_PLAIN | AGP_PROFILE | AGP_EPS_ABSOLUTE)) return fail(AGP_EINVAL, "unknown flag");
+    if (flags & ~(AGP_PLAIN | AGP_PROFILE | AGP_EPS_ABSOLUTE | AGP_SAMPLER_GROUPS)) return fail(AGP_EINVAL, "unknown flag");
     AGP_TRY(validate_params_for(g, *params));
     const bool profile = flags & AGP_PROFILE;
     if (d == 0 || g->n == 0) return AGP_OK;  // nothing to read or write: X and Z may be NULL
@@ -2155,6 +2490,7 @@ int feature_propagate_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *para
     job.sr = 1;
     job.stream_base_is_query = 1;  // column c of part s draws from the stream (seed, c, s)
     job.eps_absolute = flags & AGP_EPS_ABSOLUTE;
+    job.sampler_groups = flags & AGP_SAMPLER_GROUPS;
     job.make_aux = [&](size_t first, int count, std::vector<int32_t> &aux) {
         aux.resize(2 * (size_t)count);
         for (int l = 0; l < count; ++l) {

@@ -13,8 +13,9 @@
 //   3. when the heavy sweep's event has fired, it retires finished heavy requests and starts the next
 //      heavy sweep.
 // A light request therefore never waits for a sweep of heavy lanes (eps = 1e-9, L = 40: ~140 ms a
-// level on the 4M-node graph), only for its own pool's short sweeps. Waits of host threads on results
-// are bounded by the caller's timeout.
+// level on the 4M-node graph), only for its own pool's short sweeps; the heavy pool's kernels use a
+// quarter of the usual grid, so the light kernels find free SM slots while they run. Waits of host
+// threads on results are bounded by the caller's timeout.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -110,6 +111,8 @@ struct agp_server_s {
     std::unordered_map<uint64_t, agp::Request *> all;
     int64_t result_bytes = 0;
     int64_t completed = 0, sweeps = 0;
+    std::unordered_map<size_t, std::vector<void *>> free_dev, free_host;  // result buffers by size
+    int64_t pooled_bytes = 0;
     void *fifo_stage = nullptr;  // input staging of the FIFO-plain path (never the graph's own)
     size_t fifo_stage_bytes = 0;
     int fatal = AGP_OK;
@@ -120,15 +123,18 @@ namespace {
 
 constexpr int kMaxCols = 1024;
 constexpr int kCostClasses = 64;
-constexpr int kHeavyClass = 27;        // cost classes >= this (estimated operations >= 2^27 ~ 1.3e8) are heavy
+constexpr int kHeavyClass = 23;        // cost classes >= this (estimated operations >= 2^23 ~ 8.4e6) are heavy:
+                                       // a sweep of a full light pool then stays at a few milliseconds
 constexpr double kAgingUs = 1e6;       // a request's priority doubles every second it waits
 constexpr double kStarveUs = 30e6;     // a request waiting longer than this reserves the lanes it needs
 
-// Upper bound on the expected operations of a request, from the proof of Theorem 4.3:
-// E[cost] <= (1/eps) sum_{i=1..L} (Y_i / Y_0) ||P^i x||_1. The mass ||P^i x||_1 is 1 for the
-// column-stochastic presets (a = 0, b = 1 and one-hot x) and is bounded by the number of levels
-// otherwise; eps = 0 (exact) counts as the full graph per level.
-double estimate_cost(const agp_request_t &r, int64_t nnz)
+// Estimated operations of a request: the edge operations bounded in the proof of Theorem 4.3,
+// E[pushes + samples] <= (1/eps) sum_{i=1..L} (Y_i / Y_0) ||P^i x||_1, plus the frontier items, one
+// per non-zero residue and level (the bound leaves them out; a dense feature column starts with n of
+// them and keeps most of them). The mass ||P^i x||_1 is 1 for the column-stochastic presets (a = 0,
+// b = 1 and one-hot x) and is bounded by the number of levels otherwise; eps = 0 (exact) counts as
+// the full graph per level.
+double estimate_cost(const agp_request_t &r, int64_t n, int64_t nnz)
 {
     const agp_params_t &p = r.params;
     const int L = p.L;
@@ -142,7 +148,8 @@ double estimate_cost(const agp_request_t &r, int64_t nnz)
     }
     const double parts = r.source >= 0 ? 1.0 : 2.0 * r.cols;
     const double per_lane = p.eps > 0.0 ? mass / p.eps : (double)L * (double)nnz;
-    return parts * std::min(per_lane, (double)(L + 1) * (double)nnz) + 1e5;
+    const double support = r.source >= 0 ? 1.0 : 0.5 * (double)n;  // non-zeros of a sign part of x
+    return parts * (std::min(per_lane, (double)(L + 1) * (double)nnz) + (double)(L + 1) * support) + 1e5;
 }
 
 int cost_class(double cost)
@@ -160,31 +167,63 @@ void finish(agp_server_s *S, Request *q, int status)
     S->cv_done.notify_all();
 }
 
+void free_result(agp_server_s *S, Request *q, bool destroy = false);
+
+// Result buffers are pooled by size: cudaMalloc and cudaFree synchronise the whole device, so an
+// allocation per admitted request (or a free per released one) would stall every sweep in flight,
+// the heavy pool's included, until it ends. A released buffer goes back to its size's free list
+// (while the pooled bytes stay within the result budget) and the next request of that size takes it.
 int alloc_result(agp_server_s *S, Request *q, cudaStream_t st)
 {
     const int64_t n = S->g->n;
     const size_t elems = (size_t)n * (size_t)(q->r.source >= 0 ? 1 : q->r.cols);
     q->bytes = std::max<size_t>(elems * sizeof(float), 16);
-    if (cudaMalloc((void **)&q->d_out, q->bytes) != cudaSuccess) {
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        auto take = [&](std::unordered_map<size_t, std::vector<void *>> &pool, void **out) {
+            auto it = pool.find(q->bytes);
+            if (it == pool.end() || it->second.empty()) return false;
+            *out = it->second.back();
+            it->second.pop_back();
+            S->pooled_bytes -= (int64_t)q->bytes;
+            return true;
+        };
+        void *p = nullptr;
+        if (take(S->free_dev, &p)) q->d_out = (float *)p;
+        if (S->cfg.results_on_host && take(S->free_host, &p)) q->h_out = (float *)p;
+    }
+    if (!q->d_out && cudaMalloc((void **)&q->d_out, q->bytes) != cudaSuccess) {
         cudaGetLastError();
         q->d_out = nullptr;
         return fail(AGP_ENOMEM, "server: result buffer");
     }
-    if (S->cfg.results_on_host && cudaMallocHost((void **)&q->h_out, q->bytes) != cudaSuccess) {
+    if (S->cfg.results_on_host && !q->h_out && cudaMallocHost((void **)&q->h_out, q->bytes) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(q->d_out);
-        q->d_out = nullptr;
-        q->h_out = nullptr;
+        free_result(S, q);
         return fail(AGP_ENOMEM, "server: pinned result buffer");
     }
     AGP_CUDA_TRY(cudaMemsetAsync(q->d_out, 0, q->bytes, st));
     return AGP_OK;
 }
 
-void free_result(Request *q)
+// Return q's buffers to the size pools (freed outright past the result budget, or at destroy).
+void free_result(agp_server_s *S, Request *q, bool destroy)
 {
-    if (q->d_out) cudaFree(q->d_out);
-    if (q->h_out) cudaFreeHost(q->h_out);
+    bool keep = false;
+    if (!destroy) {
+        std::lock_guard<std::mutex> lk(S->m);
+        const int64_t add = (int64_t)q->bytes * ((q->d_out ? 1 : 0) + (q->h_out ? 1 : 0));
+        if (S->pooled_bytes + add <= S->cfg.result_budget) {
+            if (q->d_out) S->free_dev[q->bytes].push_back(q->d_out);
+            if (q->h_out) S->free_host[q->bytes].push_back(q->h_out);
+            S->pooled_bytes += add;
+            keep = true;
+        }
+    }
+    if (!keep) {
+        if (q->d_out) cudaFree(q->d_out);
+        if (q->h_out) cudaFreeHost(q->h_out);
+    }
     q->d_out = nullptr;
     q->h_out = nullptr;
 }
@@ -409,10 +448,10 @@ int admit(agp_server_s *S, int p)
             P.d_X_cap = 0;
             if (cudaMalloc((void **)&P.d_X, xb) != cudaSuccess) {
                 cudaGetLastError();
+                free_result(S, q);  // takes the server lock itself
                 std::lock_guard<std::mutex> lk(S->m);
                 for (int sl : q->slots) P.free_slots.push_back(sl);
                 S->result_bytes -= (int64_t)q->bytes;
-                free_result(q);
                 finish(S, q, fail(AGP_ENOMEM, "server: feature staging"));
                 continue;
             }
@@ -659,10 +698,10 @@ void server_main(agp_server_s *S)
     }
 }
 
-int create_pool(agp_server_s *S, Pool &P, int lanes, int W, int priority)
+int create_pool(agp_server_s *S, Pool &P, int lanes, int W, int priority, int grid)
 {
     agp_graph_s *g = S->g;
-    AGP_TRY(create_workspace(g, lanes, W, &P.ws));
+    AGP_TRY(create_workspace(g, lanes, W, &P.ws, grid));
     AGP_CUDA_TRY(cudaStreamCreateWithPriority(&P.stream, cudaStreamNonBlocking, priority));
     AGP_CUDA_TRY(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
     // every slot may hold work: the compaction scans all of them
@@ -740,9 +779,12 @@ int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **o
         lo = hi = 0;
     }
     S->npools = (c.mode == AGP_SERVE_FIFO_PLAIN) ? 1 : 2;
-    // the light pool's stream gets the highest priority: its short kernels are scheduled ahead of the
-    // heavy sweep's blocks as SMs free up
-    for (int p = 0; p < S->npools && rc == AGP_OK; ++p) rc = create_pool(S, S->pool[p], lanes, W, p == kLight ? hi : lo);
+    // The GPU is shared between the pools: the heavy pool's level kernels run 2 blocks per SM (all
+    // resident at once, half of the slots at the kernels' register use), so its grid-stride blocks never
+    // hold every slot for a whole heavy kernel; the light pool's kernels, on the highest-priority
+    // stream, take the other slots and run beside them.
+    for (int p = 0; p < S->npools && rc == AGP_OK; ++p)
+        rc = create_pool(S, S->pool[p], lanes, W, p == kLight ? hi : lo, p == kHeavy ? 2 * sm_count() : 0);
     if (rc != AGP_OK) {
         serve_destroy(S);
         return rc;
@@ -782,7 +824,7 @@ int serve_submit(agp_server_s *S, const agp_request_t *req, uint64_t *ticket)
         q->r.X = nullptr;
     }
     q->t_submit = now_us();
-    q->cost = estimate_cost(q->r, S->g->nnz);
+    q->cost = estimate_cost(q->r, S->g->n, S->g->nnz);
     const int cc = cost_class(q->cost);
     q->pool = (S->npools == 2 && cc >= kHeavyClass) ? kHeavy : kLight;
     {
@@ -861,7 +903,7 @@ int serve_release(agp_server_s *S, uint64_t ticket)
         S->all.erase(it);
         if (q->counted) S->result_bytes -= (int64_t)(q->r.source >= 0 ? 1 : q->r.cols) * S->g->n * (int64_t)sizeof(float);
     }
-    free_result(q);  // nobody deletes q meanwhile: it is not a zombie yet
+    free_result(S, q);  // nobody deletes q meanwhile: it is not a zombie yet
     {
         std::lock_guard<std::mutex> lk(S->m);
         if (q->refs > 0) {
@@ -919,12 +961,16 @@ int serve_destroy(agp_server_s *S)
         drain_queues(S);  // released requests go with their last queue entry
         for (auto &kv : S->all) {
             if (!kv.second->done) finish(S, kv.second, AGP_ECANCELED);
-            free_result(kv.second);
+            free_result(S, kv.second, true);
             delete kv.second;
         }
         S->all.clear();
     }
     for (Pool &P : S->pool) destroy_pool(P);
+    for (auto &kv : S->free_dev)
+        for (void *p : kv.second) cudaFree(p);
+    for (auto &kv : S->free_host)
+        for (void *p : kv.second) cudaFreeHost(p);
     cudaFree(S->fifo_stage);
     delete S;
     return AGP_OK;

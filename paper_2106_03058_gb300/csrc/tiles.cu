@@ -254,7 +254,11 @@ int run_tiles(agp_graph_s *g, const double *keep, const double *rho, int L, cons
     return AGP_OK;
 }
 
-// rows of the graph by length class (built once, kept with the graph)
+}  // namespace
+
+// Rows of the graph by length class (built once, kept with the graph): short (d <= 32), medium
+// (d <= 4096), long; rows without neighbours are in none. Used by the exact feature tiles and by
+// the pull levels of the propagation.
 int ensure_row_lists(agp_graph_s *g, cudaStream_t s)
 {
     if (g->row_list[0] || g->n == 0) return AGP_OK;
@@ -296,8 +300,6 @@ int ensure_row_lists(agp_graph_s *g, cudaStream_t s)
     }
     return rc;
 }
-
-}  // namespace
 
 // Column tile width: the graph's setting, else the widest of 8 / 16 / 32 whose S block stays within
 // 64 MB (half of L2), at least 8.

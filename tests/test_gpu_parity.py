@@ -289,11 +289,13 @@ def test_unbiased_variance_guarantee(agp, rmat14, case):
           f"worst per-node failure rate {fails.max():.4f}")
 
 
+@pytest.mark.parametrize("groups", [False, True], ids=["skips", "paper_groups"])
 @pytest.mark.parametrize("p", [0.02, 0.05, 0.3, 0.9])
-def test_sampler_star_binomial(agp, p):
+def test_sampler_star_binomial(agp, p, groups):
     """Star K_{1,N}, a = 0, one level: the number of sampled leaves is Binomial(N, p). p = 0.02 and
     0.05 exercise the geometric-skip samplers (thread inline and segment records), p = 0.3 and 0.9
-    the per-position sampler of dense tails."""
+    the per-position sampler of dense tails; with AGP_SAMPLER_GROUPS every tail goes through the
+    paper's scheme (a Binomial count of trials at uniformly chosen positions)."""
     from scipy import stats
     leaves = 500
     n, src, dst = G.star(leaves)
@@ -301,7 +303,7 @@ def test_sampler_star_binomial(agp, p):
     eps = (1.0 / leaves) / p
     N = 2000
     params = [agp.transition(1, eps, seed=k) for k in range(N)]
-    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32))
+    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32), sampler_groups=groups)
     k = out[:, 1:].cpu().numpy() / np.float32(eps)
     assert np.allclose(k, np.round(k))
     counts = np.round(k).sum(1).astype(int)
@@ -315,8 +317,9 @@ def test_sampler_star_binomial(agp, p):
     assert stats.chi2.sf(chi2, o.size - 1) > 1e-3
 
 
+@pytest.mark.parametrize("groups", [False, True], ids=["skips", "paper_groups"])
 @pytest.mark.parametrize("a", [0.5, 1.0])
-def test_sampler_inclusion_across_degree_groups(agp, a):
+def test_sampler_inclusion_across_degree_groups(agp, a, groups):
     degrees = [1, 2, 3, 5, 8, 9, 15, 17, 30, 33, 60, 64, 100, 129, 250]
     n, src, dst = G.graded_fan(degrees)
     g = agp.build_graph(n, src, dst)
@@ -327,7 +330,7 @@ def test_sampler_inclusion_across_degree_groups(agp, a):
     p = np.minimum(1.0, inc / eps)
     N = 4000
     params = [agp._params(a, 0.0, 1, agp.W_TRANSITION, eps=eps, seed=k) for k in range(N)]
-    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32))
+    out, _ = agp.query_sources(g, params, np.zeros(N, np.int32), sampler_groups=groups)
     hit = (out[:, hubs].cpu().numpy() > 0).mean(0)
     samp = p < 1
     z = (hit[samp] - p[samp]) / np.sqrt(p[samp] * (1 - p[samp]) / N)
@@ -613,4 +616,70 @@ def test_directed_untransposed_single_target(agp, rmat14):
     rc = agp.lib().agp_build_graph(n, 10, uu.ctypes.data, vv.ctypes.data, agp.DIRECTED | agp.DIRECTED_IN, 0, None,
                                    ctypes.byref(h))
     assert rc == 1 and not h.value
+    g.destroy()
+
+
+# ---------------------------------------------------------------- pull levels
+@pytest.mark.parametrize("preset", [PRESETS[0], PRESETS[3], PRESETS[5]], ids=["ppr", "appnp", "single_target"])
+def test_pull_levels_exact(agp, rmat14, preset):
+    """A level computed by the targets (every node gathers c(u) over its row) gives the same exact
+    propagation as the pushed level: eps = 0, pulling every level, never pulling, and the default, each
+    against the oracle at 1e-5 per entry, in groups of one and four lanes."""
+    name, a, b, kind, L, param = preset
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    srcs = np.random.default_rng(17).choice(np.flatnonzero(og.deg > 0), 8, replace=False)
+    w, Y = oracle.tail_sums(kind, L, param)
+    want = []
+    for s_ in srcs:
+        x = np.zeros(n); x[s_] = 1.0
+        want.append(oracle.basic(og, a, b, L, w, Y, x))
+    for shift in (62, -1, 4):
+        for width in (1, 4):
+            g.set_pull_threshold(shift)
+            g.set_wave_lanes(8)
+            g.set_group_width(width)
+            out, _ = agp.query_sources(g, _agp_params(agp, a, b, kind, L, param, 0.0), srcs)
+            got = out.cpu().numpy()
+            for q in range(len(srcs)):
+                _assert_rel(got[q], want[q])
+    g.destroy()
+
+
+@pytest.mark.parametrize("a,b,kind,L,param,eps", [(0.0, 1.0, oracle.PPR, 10, 0.2, 2e-6),
+                                                  (0.5, 0.5, oracle.PPR, 8, 0.1, 1e-6)], ids=["ppr", "appnp"])
+def test_pull_levels_unbiased(agp, rmat14, a, b, kind, L, param, eps):
+    """eps > 0 with every level pulled: the edge trials of the targets keep Algorithm 2 unbiased
+    (Lemma 4.1, 200 seeds) and within the Lemma 4.2 variance, and the mean agrees with the pushed runs."""
+    n, u, v = rmat14
+    g = agp.build_graph(n, u, v)
+    og = oracle.build_csr(n, u, v)
+    s = int(np.argsort(og.deg)[-200])
+    N = 200
+    w, Y = oracle.tail_sums(kind, L, param)
+    x = np.zeros(n); x[s] = 1.0
+    exact = oracle.basic(og, a, b, L, w, Y, x)
+    params = [_agp_params(agp, a, b, kind, L, param, eps, seed=3000 + k) for k in range(N)]
+    means = {}
+    for shift in (62, -1):
+        g.set_pull_threshold(shift)
+        out, st = agp.query_sources(g, params, np.full(N, s), collect_stats=True)
+        runs = out.cpu().numpy().astype(np.float64)
+        mean, var = runs.mean(0), runs.var(0, ddof=1)
+        sd = np.sqrt(var / N)
+        live = sd > 0
+        assert live.sum() >= 1000
+        z = (mean[live] - exact[live]) / sd[live]
+        assert np.mean(np.abs(z) > 2.576) <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / live.sum()) + 1e-9
+        assert np.abs(z).max() < 6.0
+        bound = L * (L + 1) * eps * (exact / Y[0]) / 2 * Y[0] * Y[0]
+        assert np.all(var <= 1.35 * bound + 1e-24)
+        means[shift] = (mean, sd)
+        if shift == 62:  # the pulled levels did the work: the push kernel saw every edge trial
+            assert sum(x.by_kernel[1][1] for x in st) > 0
+    (m1, s1), (m2, s2) = means[62], means[-1]
+    both = (s1 > 0) & (s2 > 0)
+    zz = (m1[both] - m2[both]) / np.sqrt(s1[both] ** 2 + s2[both] ** 2)
+    assert np.mean(np.abs(zz) > 2.576) <= 0.01 + 3 * np.sqrt(0.01 * 0.99 / both.sum()) + 1e-9
     g.destroy()

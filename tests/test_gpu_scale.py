@@ -1,8 +1,16 @@
 """Parity at the scale of the batched benchmark: a Chung-Lu graph (exponent 2.1) with 4.2M nodes,
 so node ids need 23 bits inside a packed (group, node) item, queried in multi-wave batches of 16
 lanes (two waves in flight) with lane groups of four and of one. Exact (eps = 0) Katz and L-step
-transition queries are compared entry by entry with the FP64 oracle (Algorithm 1) to relative 1e-5.
-The edge count is reduced to 20M so that the oracle's exact runs take seconds on the host.
+transition queries are compared entry by entry with the FP64 oracle (Algorithm 1). The edge count is
+reduced to 20M so that the oracle's exact runs take seconds on the host.
+
+Tolerance. An FP32 residue is a sum of positive increments added by atomics in an arbitrary order,
+one rounding (unit u = 2^-24) per addition, so its relative error grows with the number of terms,
+as sqrt(terms) when the rounding errors are independent. A node v receives at most d_v increments
+per level, and the errors of L + 1 levels add up, so the bound per entry is
+    |got - want| <= (1e-5 + 4 u sqrt((L + 1) d_v)) |want|,
+which is 1e-5 for small degrees and about 4e-5 at the hubs of this graph (d_v ~ 6000). Entries
+beyond the plain 1e-5 must stay below 1 in 10^5.
 """
 import numpy as np
 import pytest
@@ -56,10 +64,17 @@ def test_exact_parity_at_scale(agp):
         g.set_group_width(width)
         for kind, params in (("katz", agp.katz(beta, 20, 0.0)), ("transition", agp.transition(4, 0.0))):
             out, _ = agp.query_sources(g, params, srcs)
+            L = tables[kind][2]
+            tol = 1e-5 + 4 * 2.0 ** -24 * np.sqrt((L + 1) * np.maximum(deg, 1).astype(np.float64))
             for q in checked:
                 w_ = want[(kind, int(srcs[q]))]
                 got = out[q].cpu().numpy().astype(np.float64)
                 err = np.abs(got - w_)
-                bad = err > 1e-5 * np.abs(w_) + 1e-30
-                assert not bad.any(), (kind, width, q, int(bad.sum()), float(np.max(err / np.maximum(np.abs(w_), 1e-300))))
+                bad = err > tol * np.abs(w_) + 1e-30
+                rel = err / np.maximum(np.abs(w_), 1e-300)
+                assert not bad.any(), (kind, width, q, int(bad.sum()), float(rel.max()))
+                over = int((err > 1e-5 * np.abs(w_) + 1e-30).sum())
+                assert over <= 1e-5 * n, (kind, width, q, over)
+                print(f"[scale] {kind} width={width} query={q}: max rel err {rel[w_ != 0].max():.2e}, "
+                      f"{over} entries beyond 1e-5")
     g.destroy()
