@@ -355,7 +355,8 @@ def test_alone_equals_batched_and_plain(agp, rmat14):
     # results equally accurate against the exact propagation
     drifted = [(x, y, i) for x, y, i in pairs if not close(x, y)]
     print(f"[drift] alone / batched / plain: {len(drifted)} of {len(pairs)} pairs differ beyond 1e-5")
-    assert len(drifted) <= len(pairs) // 2
+    # bound: at most 5% of the pairs (measured on GB300: none)
+    assert len(drifted) <= max(1, len(pairs) // 20)
     if drifted:
         exact, _ = agp.query_sources(g, [agp.ppr(0.2, 20, 0.0) for _ in srcs], srcs)
         exact = exact.cpu().numpy()

@@ -87,7 +87,7 @@ def test_mix_equals_alone(agp, graph):
         exact, _ = agp.query_sources(g, _exact(agp, p), [s])
         assert equally_accurate(got, want, exact[0].cpu().numpy())
     print(f"[drift] served mix vs alone: {drifted} of {len(reqs)} requests differ beyond 1e-5")
-    assert drifted <= len(reqs) // 2  # most requests are identical up to summation order
+    assert drifted <= max(1, len(reqs) // 20)  # at most 5% (measured on GB300: none)
 
 
 def test_mix_exact_matches_oracle(agp, graph):
