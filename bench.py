@@ -459,6 +459,7 @@ def run_large(args):
         deg_expected += torch.bincount(u[s0:s0 + (1 << 28)].long(), minlength=n)
         deg_expected += torch.bincount(v[s0:s0 + (1 << 28)].long(), minlength=n)
     log(f"[large] generated in {t_gen:.1f}s; building the CSR")
+    u_h, v_h = u.cpu().numpy(), v.cpu().numpy()  # the edge list on the host, for the oracle check
     t0 = time.perf_counter()
     g = agp.build_graph(n, u, v)
     t_build = time.perf_counter() - t0
@@ -535,15 +536,63 @@ def run_large(args):
                                          "deterministic_pushes": float(work[:, 0].sum()),
                                          "sampler_trials": float(work[:, 1].sum()),
                                          "samples_accepted": float(work[:, 2].sum())}}
+    oracle_check = None if args.no_accuracy else large_oracle_check(agp, g, n, u_h, v_h, srcs[:4].numpy())
+    del u_h, v_h
     line = {"metric": "queries/s", "value": 2 * Q / ((res["ppr"]["ms_per_launch"] + res["hkpr"]["ms_per_launch"]) / 1e3),
             "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"chung-lu-2.0 n={n} m={m} ppr(0.2)+hkpr(5), L=30, eps=1e-8, {Q} uniform sources per launch",
                        "generate_s": t_gen, "build_s": t_build, "wave_lanes": lanes, "group_width": width,
                        "autotune_ms": tuned_ms},
-            "checks": checks, "models": res,
+            "checks": checks, "models": res, "oracle_check": oracle_check,
             "note": "a = 0, b = 1 keeps mass: E[sum pi] = sum_{i<=L} w_i for every source with degree >= 1"}
     print(json.dumps(line), flush=True)
     g.destroy()
+
+
+def large_oracle_check(agp, g, n, u_h, v_h, srcs):
+    """Exact PPR (alpha = 0.2, L = 2, eps = 0) of a few sources on the full graph against the FP64
+    oracle, entry by entry. With L = 2, a = 0 and b = 1, pi depends only on x, the degrees of the
+    source and of its neighbours, and the rows of those nodes: the oracle runs on the subgraph of
+    every edge incident to a source or a neighbour of one (the generator's edges are distinct and
+    loop-free, so each such node keeps its full degree there), built by the oracle's own CSR builder
+    from the host edge list. Every entry outside that subgraph must be exactly zero."""
+    import torch
+    import oracle
+    L, alpha = 2, 0.2
+    t0 = time.perf_counter()
+    pi_gpu, _ = agp.query_sources(g, [agp.ppr(alpha, L, 0.0) for _ in srcs], srcs)
+    pi_gpu = pi_gpu.cpu().numpy()
+    # the nodes whose rows matter: the sources and their neighbours
+    mark = np.zeros(n, bool)
+    mark[srcs] = True
+    hit = mark[u_h] | mark[v_h]
+    mark[u_h[hit]] = True
+    mark[v_h[hit]] = True
+    sel = mark[u_h] | mark[v_h]
+    su, sv = u_h[sel], v_h[sel]
+    nodes = np.unique(np.concatenate([su, sv]))
+    local = np.full(n, -1, np.int64)
+    local[nodes] = np.arange(nodes.size)
+    og = oracle.build_csr(int(nodes.size), local[su].astype(np.int32), local[sv].astype(np.int32))
+    w, Y = oracle.tail_sums(oracle.PPR, L, alpha)
+    t_sub = time.perf_counter() - t0
+    per = []
+    for q, s_ in enumerate(srcs):
+        x = np.zeros(og.n)
+        x[local[s_]] = 1.0
+        want_local = oracle.basic(og, 0.0, 1.0, L, w, Y, x)
+        want = np.zeros(n)
+        want[nodes] = want_local
+        got = pi_gpu[q].astype(np.float64)
+        nz = want != 0
+        rel = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+        per.append({"source": int(s_), "degree": int(og.deg[local[s_]]), "support": int(nz.sum()),
+                    "max_rel_err": float(rel.max()) if rel.size else 0.0,
+                    "entries_beyond_1e-5": int((rel > 1e-5).sum()),
+                    "nonzero_outside_support": int((got[~nz] != 0).sum())})
+    return {"what": f"exact PPR alpha={alpha} L={L} (eps = 0) vs the FP64 oracle, every entry",
+            "subgraph_edges": int(su.size), "subgraph_nodes": int(nodes.size),
+            "seconds": time.perf_counter() - t0, "subgraph_s": t_sub, "per_source": per}
 
 
 # ------------------------------------------------------------------------------- serving
@@ -599,7 +648,34 @@ def run_serve(args, wl):
         return agp._params(0.5, 0.5, L, agp.W_PPR, 0.1, eps=eps, seed=seed)
 
     def replay(mode, admission=agp.ADMIT_COST):
+        """Submit the trace in real time while a consumer thread takes results in completion order
+        (agp_serve_next) and releases each at once, as a serving client does."""
+        import threading
         srv = agp.Server(g, mode=mode, max_lanes=args.lanes if args.lanes > 0 else 0, admission=admission)
+        arrival = {}
+        lock = threading.Lock()
+        stop = threading.Event()
+        finished = []  # (arrival s, latency s, status)
+
+        def consume():
+            while True:
+                r = srv.next(timeout_us=20_000)
+                if r is None:
+                    if stop.is_set():
+                        return
+                    continue
+                tk, res = r
+                while True:  # the submitting thread records the arrival right after submit returns
+                    with lock:
+                        ta = arrival.get(tk)
+                    if ta is not None:
+                        break
+                    time.sleep(1e-4)
+                finished.append((ta, res.latency_us / 1e6, res.status))
+                srv.release(tk)
+
+        th = threading.Thread(target=consume, daemon=True)
+        th.start()
         tickets = []
         log(f"[serve] mode {mode}: replaying {len(trace)} requests over {args.serve_warmup + args.duration}s")
         t0 = time.perf_counter()
@@ -609,29 +685,28 @@ def run_serve(args, wl):
                 time.sleep(dt)
             p = params_of(kind, eps, L, seed)
             tk = srv.submit(p, X=X[:, :cols]) if kind == "features" else srv.submit(p, source=src)
-            tickets.append((tk, kind))
+            with lock:
+                arrival[tk] = ta
+            tickets.append(tk)
         submitted_by = time.perf_counter() - t0
-        deadline = t0 + args.serve_warmup + args.duration + args.drain
-        # a request counts when it completes inside the measured window (after the warm-up), whenever
-        # it arrived: under overload the oldest waiting requests are the ones that finish
-        # the window closes at warm-up + duration + drain; only requests that completed by then count
+        # the window closes at warm-up + duration + drain; a request counts when it completes inside
+        # the measured window (after the warm-up), whenever it arrived: under overload the oldest
+        # waiting requests are the ones that finish
         end_s = args.serve_warmup + args.duration + args.drain
+        time.sleep(max(0.0, t0 + end_s - time.perf_counter()))
+        stop.set()
+        th.join()
         lat, done, done_arrived = [], 0, 0
-        for (tk, kind), tr in zip(tickets, trace):
-            left = deadline - time.perf_counter()
-            r = srv.wait(tk, timeout_us=int(left * 1e6)) if left > 0 else srv.poll(tk)
-            if r is None:
-                continue
-            t_end = tr[0] + r.latency_us / 1e6
-            if r.status == 0 and args.serve_warmup <= t_end <= end_s:
+        for ta, latency, status in finished:
+            t_end = ta + latency
+            if status == 0 and args.serve_warmup <= t_end <= end_s:
                 done += 1
-                done_arrived += tr[0] >= args.serve_warmup
-                lat.append(r.latency_us / 1e3)
-            srv.release(tk)
-        elapsed = min(time.perf_counter(), deadline) - t0 - args.serve_warmup
+                done_arrived += ta >= args.serve_warmup
+                lat.append(latency * 1e3)
+        elapsed = end_s - args.serve_warmup
         st = srv.stats()
         log(f"[serve] mode {mode}: {done} done in {elapsed:.1f}s, stats {st}; stopping the server")
-        for tk, _ in tickets:  # requests still queued are dropped, the running ones end their sweep
+        for tk in tickets:  # requests still queued are dropped, the running ones end their sweep
             try:
                 srv.cancel(tk)
             except Exception:
@@ -654,7 +729,8 @@ def run_serve(args, wl):
                        "warmup_s": args.serve_warmup, "drain_s": args.drain, "lambda_1": lam},
             "batched": batched, "batched_fifo_admission": batched_fifo, "fifo_plain": fifo,
             "note": "completed = requests finishing inside the measured window (after the warm-up); latency "
-                    "percentiles over those; offered = arrivals inside the window"}
+                    "percentiles over those; offered = arrivals inside the window; a consumer thread takes "
+                    "results in completion order (agp_serve_next) and releases each at once"}
     print(json.dumps(line), flush=True)
     g.destroy()
 
@@ -933,7 +1009,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "parallelism": f"replicas{world}", "queries_per_step": 2 * Q,
                        "wave_lanes": lanes, "group_width": width, "autotune_ms": tuned_ms,
-                       "pull_threshold_shift": args.pull if args.pull is not None else "default (2)",
+                       "pull_threshold_shift": args.pull if args.pull is not None else "default (-1: pull levels off)",
                        "lambda_1": lam, "beta": beta,
                        "l2": "flushed before every timed step (256 MB write); CSR 0.96 GB and 8 GB of residues exceed L2"},
             "latency_ms": {"per_query": latency_summary(lat_k + lat_t), "katz": latency_summary(lat_k),

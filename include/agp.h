@@ -310,7 +310,10 @@ typedef struct {
     int32_t admission;        /* AGP_ADMIT_* (batched mode). Requests are split by estimated cost
                                  into a light pool (below 2^23 ~ 8.4e6 operations) and a heavy pool,
                                  each with max_lanes slots, its own workspace, stream and sweeps, so
-                                 light sweeps never wait for heavy lanes. The estimate is the edge
+                                 light sweeps never wait for heavy lanes. Heavy sweeps yield: one
+                                 starts only while the light pool is idle, or once a heavy request
+                                 has waited over 30 s (then its sweeps run beside the light ones
+                                 until it is done). The estimate is the edge
                                  bound of the proof of Theorem 4.3, (1/eps) sum_{i=1..L} (Y_i/Y_0)
                                  ||P^i x||_1 (the mass bounded per weight kind), plus one frontier
                                  item per non-zero residue and level ((L+1) n/2 per sign part of a
@@ -355,6 +358,12 @@ AGP_API int agp_serve_submit(agp_server_t s, const agp_request_t *req, uint64_t 
 AGP_API int agp_serve_poll(agp_server_t s, uint64_t ticket, agp_result_t *out);
 /* Wait up to timeout_us (< 0: no limit) for a result; AGP_ETIMEDOUT if it is still pending. */
 AGP_API int agp_serve_wait(agp_server_t s, uint64_t ticket, int64_t timeout_us, agp_result_t *out);
+/* Wait up to timeout_us (< 0: no limit) for the next request to finish, in completion order:
+ * *ticket and *out are filled (AGP_OK), or AGP_ETIMEDOUT when none finished in time. Every finished
+ * request is reported once; one released before it is reported is skipped. A client that takes its
+ * results this way can release each as it arrives, which keeps the result budget free for
+ * admissions. */
+AGP_API int agp_serve_next(agp_server_t s, int64_t timeout_us, uint64_t *ticket, agp_result_t *out);
 /* Free the result buffer of a finished request (pending requests: AGP_EINVAL). */
 AGP_API int agp_serve_release(agp_server_t s, uint64_t ticket);
 /* Cancel: a queued request finishes at once, an admitted one at the next sweep, with AGP_ECANCELED. */

@@ -128,11 +128,13 @@ def lib():
             L.agp_serve_submit.argtypes = [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
             L.agp_serve_poll.argtypes = [_vp, C.c_uint64, C.POINTER(Result)]
             L.agp_serve_wait.argtypes = [_vp, C.c_uint64, _i64, C.POINTER(Result)]
+            L.agp_serve_next.argtypes = [_vp, _i64, C.POINTER(C.c_uint64), C.POINTER(Result)]
             L.agp_serve_release.argtypes = [_vp, C.c_uint64]
             L.agp_serve_cancel.argtypes = [_vp, C.c_uint64]
             L.agp_serve_stats.argtypes = [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32)]
             L.agp_serve_destroy.argtypes = [_vp]
-            for f in ("agp_serve_create", "agp_serve_submit", "agp_serve_poll", "agp_serve_wait", "agp_serve_release",
+            for f in ("agp_serve_create", "agp_serve_submit", "agp_serve_poll", "agp_serve_wait", "agp_serve_next",
+                      "agp_serve_release",
                       "agp_serve_cancel", "agp_serve_stats", "agp_serve_destroy"):
                 getattr(L, f).restype = C.c_int
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
@@ -399,6 +401,15 @@ class Server:
             return None
         _check("agp_serve_wait", rc)
         return r
+
+    def next(self, timeout_us=-1):
+        """The next finished request in completion order: (ticket, Result), or None on timeout."""
+        r, t = Result(), C.c_uint64()
+        rc = lib().agp_serve_next(self.handle, int(timeout_us), C.byref(t), C.byref(r))
+        if rc == 6:  # AGP_ETIMEDOUT
+            return None
+        _check("agp_serve_next", rc)
+        return int(t.value), r
 
     def result_array(self, r):
         """Copy a finished result into a torch tensor ([n] or [n, cols], on its device or the host)."""

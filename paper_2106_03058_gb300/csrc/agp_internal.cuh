@@ -167,6 +167,7 @@ int serve_create(agp_graph_s *g, const agp_serve_config_t *cfg, agp_server_s **o
 int serve_submit(agp_server_s *s, const agp_request_t *req, uint64_t *ticket);
 int serve_poll(agp_server_s *s, uint64_t ticket, agp_result_t *out);
 int serve_wait(agp_server_s *s, uint64_t ticket, int64_t timeout_us, agp_result_t *out);
+int serve_next(agp_server_s *s, int64_t timeout_us, uint64_t *ticket, agp_result_t *out);
 int serve_release(agp_server_s *s, uint64_t ticket);
 int serve_cancel(agp_server_s *s, uint64_t ticket);
 int serve_stats(agp_server_s *s, int64_t *completed, int64_t *sweeps, int32_t *lanes_active, int32_t *queued);

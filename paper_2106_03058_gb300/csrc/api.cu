@@ -294,6 +294,10 @@ int agp_graph_set_pull_threshold(agp_graph_t g, int32_t shift)
 {
     if (!g) return agp::fail(AGP_EINVAL, "graph is NULL");
     if (shift < -1 || shift > 62) return agp::fail(AGP_EINVAL, "pull threshold shift must be in [-1, 62]");
+    // workspaces made while pulling was off have no c(u) blocks: they are rebuilt at the next call
+    const bool need_c = shift >= 0 && !g->directed;
+    if (need_c && ((g->ws && !g->ws->C) || (g->ws2 && !g->ws2->C) || (g->ws_plain && !g->ws_plain->C)))
+        agp::drop_workspace(g);
     g->pull_shift = shift;
     return AGP_OK;
 }
@@ -408,6 +412,10 @@ int agp_serve_poll(agp_server_t s, uint64_t ticket, agp_result_t *out) { return 
 int agp_serve_wait(agp_server_t s, uint64_t ticket, int64_t timeout_us, agp_result_t *out)
 {
     return agp::serve_wait(s, ticket, timeout_us, out);
+}
+int agp_serve_next(agp_server_t s, int64_t timeout_us, uint64_t *ticket, agp_result_t *out)
+{
+    return agp::serve_next(s, timeout_us, ticket, out);
 }
 int agp_serve_release(agp_server_t s, uint64_t ticket) { return agp::serve_release(s, ticket); }
 int agp_serve_cancel(agp_server_t s, uint64_t ticket) { return agp::serve_cancel(s, ticket); }

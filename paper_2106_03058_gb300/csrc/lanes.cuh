@@ -81,6 +81,7 @@ struct Ctrl {
     unsigned long long n_det, n_smp;  // walk-chunk and segment records of the current level
     unsigned int error;          // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 16: bad level
     unsigned int lanes_used;     // lanes [0, lanes_used) hold work; the compaction scans only those
+    unsigned int scan_mode;      // compaction of the next level: 0 one pass (sparse frontier), 1 two passes
 };
 
 constexpr int kProfKernels = 5;  // compact, expand, push, sample, level end
@@ -178,6 +179,7 @@ struct Workspace {
     int graph_collect = -1;
     int graph_profile = -1;
     int graph_groups = -1;
+    int64_t graph_pull = -2;   // pull threshold the graph was captured with (-1: pull off)
     // AGP_PROFILE events: [level][kernel][begin/end]
     cudaEvent_t ev[kMaxLevels][kProfKernels][2] = {};
     bool ev_ready = false;
@@ -221,6 +223,7 @@ inline int group_width(int G) { return (G % 4 == 0) ? 4 : (G % 2 == 0) ? 2 : 1; 
 // grid > 0: blocks of the grid-stride level kernels (default 8 per SM); a smaller grid leaves SM
 // slots to kernels of other streams (the server's heavy pool)
 int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid = 0);
+void drop_workspace(agp_graph_s *g);
 KArgs make_args(agp_graph_s *g, Workspace *ws, int collect);
 int blocks_for(unsigned long long work, int per_block);
 void launch_level(const KArgs &A, cudaStream_t s, int expand_blocks, int push_blocks, int sample_blocks,

@@ -482,9 +482,17 @@ __device__ __forceinline__ unsigned long long block_scan_1024(unsigned long long
     return (warp > 0 ? sm[warp - 1] : 0ull) + x - v;
 }
 
+template <int W, bool kLocal>
+__device__ __forceinline__ void compact_emit_body(const KArgs &A);
+__device__ __forceinline__ bool compact_one_pass(const KArgs &A);
+
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
 {
+    if (compact_one_pass(A)) {
+        compact_emit_body<W, true>(A);
+        return;
+    }
     __shared__ unsigned long long red[kBlock / 32];
     __shared__ unsigned long long slot_n[kBlock / 32][W];
     int64_t begin, end;
@@ -555,7 +563,10 @@ __global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
         A.part[b] = (int64_t)run;
         run += (unsigned long long)v;
     }
-    if (t == 0) A.ctrl->n_items = total;
+    if (t == 0) {
+        A.ctrl->n_items = total;
+        A.part[nb] = (int64_t)total;
+    }
     if (A.C) {
         // pull or push, per lane, from its own frontier size (so a lane's mode does not depend on the
         // other lanes of its batch); a lane at its last level pushes nothing
@@ -579,15 +590,25 @@ __global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
 // and one block scan of the four per-thread counts (packed in 16-bit fields of a 64-bit word: a
 // unit holds at most 1024 items, so no field carries into the next) places every item. The warp
 // totals are double-buffered, so a batch needs a single __syncthreads.
+//
+// kLocal (the one-pass form, for sparse frontiers): the same pass runs first, without a count pass,
+// and writes the items of block b to its own stretch of a staging list, slot begin_b * (1024 / W)
+// onwards (a block's units hold at most that many items), and its count to part[b]; after the scan
+// of the counts, k_compact_emit moves each block's items to their place (compact_gather). The
+// residues are read once instead of twice, and the items are moved once more: 4 + 24 rho bytes per
+// (lane, node) at frontier density rho (W = 1) against 8 + 8 rho, the better choice below rho = 1/4.
+// The staging list is the c_item / k_item storage, which the expansion of the level rewrites.
 constexpr int kEmitBatch = 4;
-template <int W>
-__global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
+template <int W, bool kLocal>
+__device__ __forceinline__ void compact_emit_body(const KArgs &A)
 {
     __shared__ unsigned long long wsum[2][kBlock / 32];
     int64_t begin, end;
     compact_range(A, begin, end);
     const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long run = (unsigned long long)A.part[blockIdx.x];
+    uint32_t *items = kLocal ? reinterpret_cast<uint32_t *>(A.k_item) + begin * (kScanUnit / W) : A.items;
+    float *rval = kLocal ? A.c_item + begin * (kScanUnit / W) * W : A.rval;
+    unsigned long long run = kLocal ? 0ull : (unsigned long long)A.part[blockIdx.x];
     int parity = 0;
     for (int64_t u0 = begin; u0 < end; u0 += kEmitBatch, parity ^= 1) {
         float4 v[kEmitBatch];
@@ -643,12 +664,13 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
 #pragma unroll
                 for (int s = 0; s < W; ++s) any |= e[k * W + s] != 0.f;
                 if (!any) continue;
-                if (off < A.cap_items) {
-                    A.items[off] = hi | (node0 + (uint32_t)k);
-                    if constexpr (W == 4) reinterpret_cast<float4 *>(A.rval)[off] = v[j];
+                // the staging stretch of a block holds all of its units' nodes: no overflow there
+                if (kLocal || off < A.cap_items) {
+                    items[off] = hi | (node0 + (uint32_t)k);
+                    if constexpr (W == 4) reinterpret_cast<float4 *>(rval)[off] = v[j];
                     else if constexpr (W == 2)
-                        reinterpret_cast<float2 *>(A.rval)[off] = make_float2(e[2 * k], e[2 * k + 1]);
-                    else A.rval[off] = e[k];
+                        reinterpret_cast<float2 *>(rval)[off] = make_float2(e[2 * k], e[2 * k + 1]);
+                    else rval[off] = e[k];
                 } else {
                     atomicOr(&A.ctrl->error, 1u);
                 }
@@ -666,6 +688,38 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
         }
         run = unit_base;
     }
+    if (kLocal && threadIdx.x == 0) A.part[blockIdx.x] = (int64_t)run;
+}
+
+// The one-pass form's last step: block b copies its staged items (count part[b + 1] - part[b]
+// after the scan) to items[part[b] ...), in order.
+template <int W>
+__device__ __forceinline__ void compact_gather(const KArgs &A)
+{
+    int64_t begin, end;
+    compact_range(A, begin, end);
+    const unsigned long long n_items = min(A.ctrl->n_items, A.cap_items);
+    const unsigned long long o0 = (unsigned long long)A.part[blockIdx.x];
+    const unsigned long long o1 = min((unsigned long long)A.part[blockIdx.x + 1], n_items);
+    const uint32_t *src_i = reinterpret_cast<const uint32_t *>(A.k_item) + begin * (kScanUnit / W);
+    const float *src_r = A.c_item + begin * (kScanUnit / W) * W;
+    for (unsigned long long i = threadIdx.x; o0 + i < o1; i += kBlock) {
+        A.items[o0 + i] = src_i[i];
+        if constexpr (W == 4) reinterpret_cast<float4 *>(A.rval)[o0 + i] = reinterpret_cast<const float4 *>(src_r)[i];
+        else if constexpr (W == 2) reinterpret_cast<float2 *>(A.rval)[o0 + i] = reinterpret_cast<const float2 *>(src_r)[i];
+        else A.rval[o0 + i] = src_r[i];
+    }
+}
+
+// The level's compaction form, decided at the end of the previous level (k_level_end) from its
+// frontier density; pull levels keep the two-pass form (their count pass also sums volumes).
+__device__ __forceinline__ bool compact_one_pass(const KArgs &A) { return !A.C && A.ctrl->scan_mode == 0; }
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
+{
+    if (compact_one_pass(A)) compact_gather<W>(A);
+    else compact_emit_body<W, false>(A);
 }
 
 // Record counts of one frontier item: x = walk chunks (kChunk positions of the row walk that covers
@@ -674,8 +728,16 @@ __global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
 // here, alone. Written for every item; k_rec_* turn them into record lists without a shared counter.
 // flag_item bits: j = lane j's tail is dense, 8 + j = lane j is in the walk, 16 + j = lane j has
 // segments; c_item / k_item / seg_item are written for the lanes named there.
+// A short deterministic prefix left to the warp (group width 1): the row, its length and the
+// lane's increment parameters. len = 0: none.
+struct InlinePush {
+    int64_t e0;
+    float c, a;
+    int len, a_mode, grp;
+};
+
 template <int W>
-__device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long idx)
+__device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long idx, InlinePush &ip)
 {
     Ctrl *ctrl = A.ctrl;
     // every array read here is written only by earlier kernels: read-only path
@@ -739,8 +801,18 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
         bool in_walk = false;
         if (wlen > 0) {
             if (!is_dense && wlen <= kInlineDet) {
-                unsigned int acc = 0;
-                walk_lane_inline<W>(A, Rg + j, walk_lane(P, c, k, false, lvl), u, row, wlen, acc);
+                if constexpr (W == 1) {
+                    // pushed by the whole warp after the items (warp_inline_push)
+                    ip.e0 = e0;
+                    ip.c = c;
+                    ip.a = P.a;
+                    ip.len = wlen;
+                    ip.a_mode = P.a_mode;
+                    ip.grp = grp;
+                } else {
+                    unsigned int acc = 0;
+                    walk_lane_inline<W>(A, Rg + j, walk_lane(P, c, k, false, lvl), u, row, wlen, acc);
+                }
                 if (A.collect) atomicAdd(&A.stats[lane].by_kernel[0][0], (unsigned long long)k);
             } else {
                 in_walk = true;
@@ -764,6 +836,59 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
     return nrec;
 }
 
+// The short deterministic prefixes of a warp's 32 items (group width 1), pushed by the whole warp:
+// the prefixes are laid end to end and every lane takes four consecutive outputs of each round of
+// 128, so a round's neighbour loads are mostly coalesced and no lane waits for the longest prefix.
+// Output p belongs to the first lane whose inclusive prefix-length sum exceeds p (a five-step search
+// over the lanes' sums). The increments are those of the lane's own walk, c / d_v^a.
+__device__ __forceinline__ void warp_inline_push(const KArgs &A, const InlinePush &ip)
+{
+    const int lane_id = threadIdx.x & 31;
+    unsigned int incl = (unsigned int)ip.len;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane_id >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned int excl = incl - (unsigned int)ip.len;
+    for (unsigned int p0 = 0; p0 < total; p0 += 128) {
+        int owner[4];
+        unsigned int pos[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const unsigned int p = p0 + 4 * lane_id + t;
+            int lo = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const unsigned int v = __shfl_sync(0xffffffffu, incl, lo + s - 1);
+                if (v <= p) lo += s;
+            }
+            owner[t] = lo;
+            pos[t] = p - __shfl_sync(0xffffffffu, excl, lo);
+        }
+        int32_t v[4];
+        float c[4], a[4];
+        int am[4];
+        float *Rg[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t e0 = __shfl_sync(0xffffffffu, ip.e0, owner[t]);
+            c[t] = __shfl_sync(0xffffffffu, ip.c, owner[t]);
+            a[t] = __shfl_sync(0xffffffffu, ip.a, owner[t]);
+            am[t] = __shfl_sync(0xffffffffu, ip.a_mode, owner[t]);
+            const int grp = __shfl_sync(0xffffffffu, ip.grp, owner[t]);
+            Rg[t] = A.R + (size_t)grp * A.ldR;
+            v[t] = (p0 + 4 * lane_id + t < total) ? ld_col(A.g.colidx + e0 + pos[t]) : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (v[t] < 0) continue;
+            const float inc = (am[t] == 0) ? c[t] : apply_deg(c[t], A.g.deg[v[t]], am[t], a[t]);
+            push_to(Rg[t] + v[t], inc);
+        }
+    }
+}
+
 // Items are split into contiguous block ranges, a multiple of kBlock long (k_rec_emit walks the
 // same ranges). Returns [begin, end) of this block.
 __device__ __forceinline__ void item_range(const KArgs &A, unsigned long long &begin, unsigned long long &end)
@@ -783,11 +908,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
     // per-thread record totals (32-bit: a thread's items have far fewer than 2^32 records; the
     // block sums are 64-bit)
     unsigned int tot[2] = {0u, 0u};
-    for (unsigned long long idx = begin + threadIdx.x; idx < end; idx += kBlock) {
-        const uint2 nr = expand_item<W>(A, idx);
-        A.nrec[idx] = nr;
-        tot[0] += nr.x;
-        tot[1] += nr.y;
+    // warp-uniform trip count: the whole warp takes part in the inline pushes of every round
+    for (unsigned long long base = begin; base < end; base += kBlock) {
+        const unsigned long long idx = base + threadIdx.x;
+        InlinePush ip{0, 0.f, 0.f, 0, 0, 0};
+        if (idx < end) {
+            const uint2 nr = expand_item<W>(A, idx, ip);
+            A.nrec[idx] = nr;
+            tot[0] += nr.x;
+            tot[1] += nr.y;
+        }
+        if constexpr (W == 1) warp_inline_push(A, ip);
     }
     // block totals of the two record kinds, for k_rec_scan
     unsigned long long wt[2];
@@ -865,7 +996,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
             if (lane_id == 31) wsum[parity][t][warp] = x[t];
         }
         __syncthreads();
-        unsigned long long off[2], total[2];
+        const uint32_t idx0 = (uint32_t)(tile + (threadIdx.x & ~31u));  // item of the warp's lane 0
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             unsigned long long before = 0, all = 0;
@@ -874,19 +1005,30 @@ __global__ void __launch_bounds__(kBlock) k_rec_emit(KArgs A)
                 if (w < warp) before += v;
                 all += v;
             }
-            off[t] = base[t] + before + x[t] - cnt[t];
-            total[t] = all;
-        }
-        for (unsigned int r = 0; r < cnt[0]; ++r) {
-            if (off[0] + r < A.cap_det) A.det_rec[off[0] + r] = make_uint2((uint32_t)idx, r);
-            else atomicOr(&A.ctrl->error, 2u);
-        }
-        for (unsigned int r = 0; r < cnt[1]; ++r) {
-            if (off[1] + r < A.cap_smp) A.smp_rec[off[1] + r] = make_uint2((uint32_t)idx, r);
-            else atomicOr(&A.ctrl->error, 4u);
-        }
+            // the warp's records are written by consecutive lanes (a hub item has hundreds): output p
+            // of the warp belongs to the first lane whose inclusive count exceeds p, found by a
+            // five-step search over the lanes' counts
+            const unsigned int wtotal = __shfl_sync(0xffffffffu, x[t], 31);
+            const unsigned int excl = x[t] - cnt[t];
+            uint2 *rec = t == 0 ? A.det_rec : A.smp_rec;
+            const unsigned long long cap = t == 0 ? A.cap_det : A.cap_smp;
+            const unsigned long long wbase = base[t] + before;
+            for (unsigned int p0 = 0; p0 < wtotal; p0 += 32) {
+                const unsigned int p = p0 + lane_id;
+                int lo = 0;
 #pragma unroll
-        for (int t = 0; t < 2; ++t) base[t] += total[t];
+                for (int s = 16; s > 0; s >>= 1) {
+                    const unsigned int v = __shfl_sync(0xffffffffu, x[t], lo + s - 1);
+                    if (v <= p) lo += s;
+                }
+                const unsigned int r = p - __shfl_sync(0xffffffffu, excl, lo);
+                if (p < wtotal) {
+                    if (wbase + p < cap) rec[wbase + p] = make_uint2(idx0 + (uint32_t)lo, r);
+                    else atomicOr(&A.ctrl->error, t == 0 ? 2u : 4u);
+                }
+            }
+            base[t] += all;
+        }
     }
 }
 
@@ -1193,6 +1335,11 @@ __global__ void k_level_end(KArgs A)
     if (threadIdx.x == 0) {
         ctrl->n_det = 0;
         ctrl->n_smp = 0;
+        // the next level's compaction form, predicted from this level's frontier density: one pass
+        // below 1/16 of the scanned (group, node) pairs (break-even is 1/4; a frontier can grow
+        // several-fold in one level)
+        const unsigned long long groups = (min((int)ctrl->lanes_used, A.G) + A.W - 1) / A.W;
+        ctrl->scan_mode = (ctrl->n_items * 16ull < groups * (unsigned long long)A.ldR) ? 0u : 1u;
     }
 }
 
@@ -1274,6 +1421,7 @@ __global__ void k_colnorms_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t
 __global__ void k_seed_dense_bf16(KArgs A, const uint16_t *X, int64_t ldx, const int32_t *lane_of, const int32_t *col_of,
                                   const int32_t *part_of, const double *norms, int nl)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->scan_mode = 1u;  // dense seeds: two-pass compaction
     const int64_t total = A.g.n * nl;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(t % nl);
@@ -1340,6 +1488,7 @@ __global__ void k_rownorm_sum(const double *part, int chunks, int Q, double *nor
 template <typename T>
 __global__ void k_seed_dense_rows(KArgs A, const T *X, int64_t ldx, int Q, const int32_t *lane_of, const double *norms)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->scan_mode = 1u;  // dense seeds: two-pass compaction
     const int64_t n = A.g.n, total = (int64_t)Q * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(t / n);
@@ -1546,7 +1695,11 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid)
     ws->n = g->n;
     const unsigned long long n = (unsigned long long)std::max<int64_t>(g->n, 1);
     const unsigned long long groups = (unsigned long long)(G / W), nnz = (unsigned long long)g->nnz;
-    ws->cap_items = groups * n;
+    const int64_t node_unit = kScanUnit / W;  // nodes per scanned unit of a group block
+    ws->ldR = ((int64_t)n + node_unit - 1) / node_unit * node_unit;
+    // one item per (group, node); the one-pass compaction stages a block's items at its units'
+    // node offsets, so the item storage covers every node slot of the blocks (ldR per group)
+    ws->cap_items = groups * (unsigned long long)ws->ldR;
     // a row is walked at most once per group and level: ceil(d_u / kChunk) <= 1 + d_u / kChunk chunks
     ws->cap_det = ws->cap_items + groups * nnz / kChunk + 1;
     // segments of a lane's tail: at most 1 + d_u / kMinSeg per (lane, node)
@@ -1554,8 +1707,6 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid)
     size_t acc = 0;
     int rc = AGP_OK;
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
-    const int64_t node_unit = kScanUnit / W;  // nodes per scanned unit of a group block
-    ws->ldR = ((int64_t)n + node_unit - 1) / node_unit * node_unit;
     const int64_t units = (int64_t)groups * (ws->ldR * W / kScanUnit);
     ws->grid = grid > 0 ? grid : grid_stride_blocks();
     ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid, units));
@@ -1571,8 +1722,9 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid)
     A(dev_alloc(&ws->rpart, (size_t)2 * ws->grid, acc));
     A(dev_alloc(&ws->det_rec, ws->cap_det, acc));
     A(dev_alloc(&ws->smp_rec, ws->cap_smp, acc));
-    // pull levels (undirected graphs): c(u) block beside R, per-lane frontier counts and modes
-    if (!g->directed) {
+    // pull levels (undirected graphs, when enabled): c(u) block beside R, per-lane frontier counts
+    // and modes
+    if (!g->directed && g->pull_shift >= 0) {
         A(dev_alloc(&ws->C, (size_t)G * ws->ldR, acc));
         A(dev_alloc(&ws->lane_count, (size_t)G, acc));
         A(dev_alloc(&ws->pull, (size_t)2 * G, acc));
@@ -1727,11 +1879,12 @@ KArgs make_args(agp_graph_s *g, Workspace *ws, int collect)
     A.grid = ws->grid;
     A.rows_in = g->directed == 2 ? 1 : 0;
     A.groups = 0;
-    A.C = ws->C;
-    A.lane_count = ws->lane_count;
-    A.pull = ws->pull;
-    A.pull_min = (g->pull_shift >= 0 && g->pull_shift < 63) ? std::max<int64_t>(1, g->nnz >> g->pull_shift)
-                                                           : std::numeric_limits<int64_t>::max();
+    // pull levels off (the default): no frontier volumes, pull decisions or pull launches at all
+    const bool pull_on = ws->C && g->pull_shift >= 0 && g->pull_shift < 63;
+    A.C = pull_on ? ws->C : nullptr;
+    A.lane_count = pull_on ? ws->lane_count : nullptr;
+    A.pull = pull_on ? ws->pull : nullptr;
+    A.pull_min = pull_on ? std::max<int64_t>(1, g->nnz >> g->pull_shift) : std::numeric_limits<int64_t>::max();
     for (int c = 0; c < 3; ++c) {
         A.rows[c] = g->row_list[c];
         A.row_count[c] = g->row_count[c];
@@ -1932,8 +2085,9 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         }
         return AGP_OK;
     }
+    const int64_t pull_key = A.C ? A.pull_min : -1;
     if (!ws->graph || ws->graph_levels != max_L || ws->graph_collect != A.collect || ws->graph_profile != (int)profile ||
-        ws->graph_groups != A.groups) {
+        ws->graph_groups != A.groups || ws->graph_pull != pull_key) {
         if (ws->graph) {
             cudaGraphExecDestroy(ws->graph);
             ws->graph = nullptr;
@@ -1943,6 +2097,7 @@ int run_levels(agp_graph_s *g, Workspace *ws, const KArgs &A, int max_L, bool pl
         ws->graph_collect = A.collect;
         ws->graph_profile = (int)profile;
         ws->graph_groups = A.groups;
+        ws->graph_pull = pull_key;
     }
     AGP_CUDA_TRY(cudaGraphLaunch(ws->graph, s));
     __atomic_fetch_add(&g->kernel_launches, (int64_t)((kKernelsPerLevel + (A.C ? 3 : 0)) * (max_L + 1)), __ATOMIC_RELAXED);

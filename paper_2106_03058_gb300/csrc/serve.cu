@@ -109,7 +109,8 @@ struct agp_server_s {
     int64_t queued = 0;                          // waiting requests
     int64_t queued_pool[2] = {0, 0};
     std::unordered_map<uint64_t, agp::Request *> all;
-    int64_t result_bytes = 0;
+    int64_t result_bytes[2] = {0, 0};  // result bytes of admitted, unreleased requests, per pool
+    std::deque<uint64_t> done_q;     // tickets of finished requests, in completion order (agp_serve_next)
     int64_t completed = 0, sweeps = 0;
     std::unordered_map<size_t, std::vector<void *>> free_dev, free_host;  // result buffers by size
     int64_t pooled_bytes = 0;
@@ -164,6 +165,7 @@ void finish(agp_server_s *S, Request *q, int status)
     q->done = true;
     q->t_done = now_us();
     ++S->completed;
+    S->done_q.push_back(q->ticket);
     S->cv_done.notify_all();
 }
 
@@ -383,7 +385,10 @@ int admit(agp_server_s *S, int p)
             }
             const int need = need_of(q);
             const int64_t bytes = (int64_t)S->g->n * (q->r.source >= 0 ? 1 : q->r.cols) * (int64_t)sizeof(float);
-            if (S->result_bytes + bytes > S->cfg.result_budget && S->result_bytes > 0) break;
+            // each pool has half of the result budget, so that requests of one pool that hold their
+            // results (waiting to run, or unreleased) never keep the other from admitting
+            const int64_t budget = S->npools == 2 ? S->cfg.result_budget / 2 : S->cfg.result_budget;
+            if (S->result_bytes[p] + bytes > budget && S->result_bytes[p] > 0) break;
             from->pop_front();
             unref(q);  // still owned by S->all: not released while it waits
             dequeue(S, q);
@@ -397,7 +402,7 @@ int admit(agp_server_s *S, int p)
                 *lo = P.free_slots.back();
                 P.free_slots.pop_back();
             }
-            S->result_bytes += bytes;
+            S->result_bytes[p] += bytes;
             q->counted = true;
             take.push_back(q);
         }
@@ -421,7 +426,7 @@ int admit(agp_server_s *S, int p)
         if (rc != AGP_OK) {
             std::lock_guard<std::mutex> lk(S->m);
             for (int sl : q->slots) P.free_slots.push_back(sl);
-            S->result_bytes -= (int64_t)q->bytes;
+            S->result_bytes[p] -= (int64_t)q->bytes;
             q->slots.clear();
             finish(S, q, rc);
             continue;
@@ -451,7 +456,7 @@ int admit(agp_server_s *S, int p)
                 free_result(S, q);  // takes the server lock itself
                 std::lock_guard<std::mutex> lk(S->m);
                 for (int sl : q->slots) P.free_slots.push_back(sl);
-                S->result_bytes -= (int64_t)q->bytes;
+                S->result_bytes[p] -= (int64_t)q->bytes;
                 finish(S, q, fail(AGP_ENOMEM, "server: feature staging"));
                 continue;
             }
@@ -619,9 +624,27 @@ void run_fifo_plain(agp_server_s *S, Request *q)
     finish(S, q, q->cancelled ? AGP_ECANCELED : rc);
 }
 
-// One step of the batched server thread: keep one heavy sweep in flight (retiring and admitting
-// between its sweeps, never waiting for it here), then admit, sweep and retire the light pool.
-// *busy: some pool has work.
+// The heavy pool yields to the light one. Its kernels share the SMs, the L2 and HBM with the light
+// sweeps, and one dense level of a wide feature block keeps them busy for a large fraction of a
+// second, which slows every light request in flight by as much. So a heavy sweep starts only while
+// the light pool has no lanes in flight (after its admissions), or once a heavy request (waiting or
+// in flight) has waited past kStarveUs, from which point its sweeps run beside the light ones until
+// it is done.
+bool heavy_may_run(agp_server_s *S)
+{
+    Pool &Lp = S->pool[kLight], &Hp = S->pool[kHeavy];
+    if (Lp.active_lanes == 0) return true;
+    std::lock_guard<std::mutex> lk(S->m);
+    const double t = now_us();
+    for (const Request *q : Hp.slot_owner)
+        if (q && t - q->t_submit > kStarveUs) return true;
+    pop_dead(S->queue[kHeavy]);
+    return !S->queue[kHeavy].empty() && t - S->queue[kHeavy].front()->t_submit > kStarveUs;
+}
+
+// One step of the batched server thread: admit to the light pool; keep a heavy sweep in flight
+// while the heavy pool may run (retiring and admitting between its sweeps, never waiting for it
+// here); then sweep and retire the light pool. *busy: some pool has work.
 int serve_step(agp_server_s *S, bool *busy)
 {
     Pool &Lp = S->pool[kLight], &Hp = S->pool[kHeavy];
@@ -635,12 +658,12 @@ int serve_step(agp_server_s *S, bool *busy)
             return fail(AGP_ECUDA, std::string("server: heavy sweep: ") + cudaGetErrorString(e));
         }
     }
-    if (!Hp.in_flight) {
+    AGP_TRY(admit(S, kLight));
+    if (!Hp.in_flight && heavy_may_run(S)) {
         AGP_TRY(admit(S, kHeavy));
         if (Hp.active_lanes > 0) AGP_TRY(launch_sweep(S, kHeavy));
     }
     *busy = Hp.in_flight;
-    AGP_TRY(admit(S, kLight));
     if (Lp.active_lanes > 0) {
         AGP_TRY(launch_sweep(S, kLight));
         AGP_TRY(retire(S, kLight));  // synchronises the light stream
@@ -890,6 +913,30 @@ int serve_wait(agp_server_s *S, uint64_t ticket, int64_t timeout_us, agp_result_
     return AGP_OK;
 }
 
+int serve_next(agp_server_s *S, int64_t timeout_us, uint64_t *ticket, agp_result_t *out)
+{
+    if (!S || !ticket || !out) return fail(AGP_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->m);
+    const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max<int64_t>(0, timeout_us));
+    while (true) {
+        // requests released before they were reported are skipped
+        while (!S->done_q.empty()) {
+            const uint64_t t = S->done_q.front();
+            S->done_q.pop_front();
+            auto it = S->all.find(t);
+            if (it == S->all.end() || it->second->released) continue;
+            *ticket = t;
+            fill_result(S, it->second, out);
+            return AGP_OK;
+        }
+        if (timeout_us < 0) {
+            S->cv_done.wait(lk);
+        } else if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && S->done_q.empty()) {
+            return AGP_ETIMEDOUT;
+        }
+    }
+}
+
 int serve_release(agp_server_s *S, uint64_t ticket)
 {
     if (!S) return fail(AGP_EINVAL, "NULL argument");
@@ -901,7 +948,8 @@ int serve_release(agp_server_s *S, uint64_t ticket)
         if (!it->second->done) return fail(AGP_EINVAL, "request still pending");
         q = it->second;
         S->all.erase(it);
-        if (q->counted) S->result_bytes -= (int64_t)(q->r.source >= 0 ? 1 : q->r.cols) * S->g->n * (int64_t)sizeof(float);
+        if (q->counted)
+            S->result_bytes[q->pool] -= (int64_t)(q->r.source >= 0 ? 1 : q->r.cols) * S->g->n * (int64_t)sizeof(float);
     }
     free_result(S, q);  // nobody deletes q meanwhile: it is not a zombie yet
     {

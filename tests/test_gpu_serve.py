@@ -177,3 +177,34 @@ def test_fifo_plain_mode_matches(agp, graph):
             srv.release(t)
             alone, _ = agp.query_sources(g, p, [s])
             assert same_draws(got, alone[0].cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", ["batched", "fifo_plain"])
+def test_completion_order_next(agp, graph, mode):
+    """agp_serve_next reports every finished request once, in completion order, and skips one that
+    was released before it was reported; its results equal those of agp_serve_wait."""
+    n, g, og, _, _ = graph
+    reqs = _mixed_requests(agp, og, 24, 3)
+    m = agp.SERVE_BATCHED if mode == "batched" else agp.SERVE_FIFO_PLAIN
+    with agp.Server(g, mode=m, max_lanes=8) as srv:
+        tickets = [srv.submit(p, source=s) for p, s in reqs]
+        # take the first one by its ticket and release it before next() can report it
+        first = srv.wait(tickets[0], timeout_us=120_000_000)
+        assert first is not None and first.status == 0
+        want0 = srv.result_array(first).cpu().numpy().copy()
+        srv.release(tickets[0])
+        seen, lat = [], []
+        while len(seen) < len(tickets) - 1:
+            r = srv.next(timeout_us=120_000_000)
+            assert r is not None
+            tk, res = r
+            assert res.status == 0 and tk != tickets[0] and tk not in seen
+            seen.append(tk)
+            lat.append(res.latency_us)
+            got = srv.result_array(res).cpu().numpy()
+            again = srv.poll(tk)
+            assert again is not None and np.array_equal(srv.result_array(again).cpu().numpy(), got)
+            srv.release(tk)
+        assert sorted(seen) == sorted(tickets[1:])
+        assert srv.next(timeout_us=1000) is None  # nothing left to report
+    assert np.isfinite(want0).all() and want0.sum() > 0
