@@ -258,6 +258,29 @@ def run_reference(args, wl, rank):
 
 
 # ------------------------------------------------------------------------------- accuracy
+def row_accuracy(og, kind, a, b, L, w, Y, eps, s_, row):
+    """One GPU result row against the exact FP64 propagation of x = e_s (the oracle's Algorithm 1)."""
+    import oracle
+    x = np.zeros(og.n)
+    x[s_] = 1.0
+    exact = oracle.basic(og, a, b, L, w, Y, x)
+    res = {"kind": kind, "source": int(s_), "eps": float(eps), "L": int(L)}
+    rel = np.abs(row.astype(np.float64) - exact) / np.maximum(exact, 1e-300)
+    for name, delta in (("paper", eps * L * (L + 1) / 2 * Y[0]), ("chebyshev", 5000 * L * (L + 1) * eps * Y[0])):
+        big = exact >= delta
+        res[f"delta_{name}"] = float(delta)
+        res[f"nodes_{name}"] = int(big.sum())
+        res[f"frac_ok_{name}"] = float(np.mean(rel[big] <= 0.1)) if big.any() else None
+    res["rel_l1"] = float(np.abs(row - exact).sum() / np.abs(exact).sum())
+    # the smallest delta at which >= 99% of the nodes with pi >= delta have relative error <= 0.1
+    order = np.argsort(-exact)
+    order = order[exact[order] > 0]
+    ok = np.cumsum(rel[order] <= 0.1) / np.arange(1, order.size + 1)
+    good = np.flatnonzero(ok >= 0.99)
+    res["delta_99"] = float(exact[order[good[-1]]]) if good.size else None
+    return res
+
+
 def accuracy_vs_oracle(og, checks, eps, beta, L_katz, threads):
     """Relative error of GPU results against the exact FP64 propagation (the oracle's Algorithm 1).
     checks: list of (kind, source, gpu_row). Reported per query: the fraction of nodes with
@@ -273,24 +296,7 @@ def accuracy_vs_oracle(og, checks, eps, beta, L_katz, threads):
     def one(item):
         kind, s_, row = item
         a, b, L, w, Y = tables[kind]
-        x = np.zeros(n)
-        x[s_] = 1.0
-        exact = oracle.basic(og, a, b, L, w, Y, x)
-        res = {"kind": kind, "source": int(s_)}
-        rel = np.abs(row.astype(np.float64) - exact) / np.maximum(exact, 1e-300)
-        for name, delta in (("paper", eps * L * (L + 1) / 2 * Y[0]), ("chebyshev", 5000 * L * (L + 1) * eps * Y[0])):
-            big = exact >= delta
-            res[f"delta_{name}"] = float(delta)
-            res[f"nodes_{name}"] = int(big.sum())
-            res[f"frac_ok_{name}"] = float(np.mean(rel[big] <= 0.1)) if big.any() else None
-        res["rel_l1"] = float(np.abs(row - exact).sum() / np.abs(exact).sum())
-        # the smallest delta at which >= 99% of the nodes with pi >= delta have relative error <= 0.1
-        order = np.argsort(-exact)
-        order = order[exact[order] > 0]
-        ok = np.cumsum(rel[order] <= 0.1) / np.arange(1, order.size + 1)
-        good = np.flatnonzero(ok >= 0.99)
-        res["delta_99"] = float(exact[order[good[-1]]]) if good.size else None
-        return res
+        return row_accuracy(og, kind, a, b, L, w, Y, eps, s_, row)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=max(1, min(threads, len(checks)))) as ex:
@@ -493,11 +499,16 @@ def run_large(args):
     w_ppr = 1.0 - 0.8 ** 31
     w_hk = float(sum(math.exp(-5.0 + i * math.log(5.0) - math.lgamma(i + 1.0)) for i in range(31)))
     flags = agp.INPUT_ON_DEVICE | agp.OUTPUT_ON_DEVICE
-    # wave width by timing on the first 32 PPR queries
+    # wave width by timing on the first 32 PPR queries (or as given)
     qs = min(Q, 32)
-    lanes, width, tuned_ms = agp.autotune(g, [agp.ppr(0.2, 30, 1e-8, seed=S + q) for q in range(qs)], off[:qs + 1],
-                                   d_srcs[:qs], None, out, n, candidates=[1, 2, 4, 8, 16])
-    log(f"[large] autotuned wave width {lanes} lanes, group width {width}")
+    if args.lanes > 0:
+        g.set_wave_lanes(args.lanes)
+        g.set_group_width(args.width)
+        lanes, width, tuned_ms = args.lanes, args.width, None
+    else:
+        lanes, width, tuned_ms = agp.autotune(g, [agp.ppr(0.2, 30, 1e-8, seed=S + q) for q in range(qs)],
+                                              off[:qs + 1], d_srcs[:qs], None, out, n, candidates=[1, 2, 4, 8, 16])
+        log(f"[large] autotuned wave width {lanes} lanes, group width {width}")
     res = {}
     for name, mk, mass in (("ppr", lambda sd: agp.ppr(0.2, 30, 1e-8, seed=sd), w_ppr),
                            ("hkpr", lambda sd: agp.hkpr(5.0, 30, 1e-8, seed=sd), w_hk)):
@@ -647,7 +658,7 @@ def run_serve(args, wl):
             return agp.transition(L, eps, seed=seed)
         return agp._params(0.5, 0.5, L, agp.W_PPR, 0.1, eps=eps, seed=seed)
 
-    def replay(mode, admission=agp.ADMIT_COST):
+    def replay(mode, admission=agp.ADMIT_COST, check=False):
         """Submit the trace in real time while a consumer thread takes results in completion order
         (agp_serve_next) and releases each at once, as a serving client does."""
         import threading
@@ -656,6 +667,7 @@ def run_serve(args, wl):
         lock = threading.Lock()
         stop = threading.Event()
         finished = []  # (arrival s, latency s, status)
+        kept = []      # (trace index, result row) of a few single-source results, for the oracle check
 
         def consume():
             while True:
@@ -671,7 +683,12 @@ def run_serve(args, wl):
                     if ta is not None:
                         break
                     time.sleep(1e-4)
+                ta, i_tr = ta
                 finished.append((ta, res.latency_us / 1e6, res.status))
+                tr = trace[i_tr]
+                if (check and res.status == 0 and len(kept) < 8 and tr[1] != "features" and tr[3] <= 12
+                        and ta >= args.serve_warmup):
+                    kept.append((i_tr, srv.result_array(res).cpu().numpy().copy()))
                 srv.release(tk)
 
         th = threading.Thread(target=consume, daemon=True)
@@ -679,14 +696,14 @@ def run_serve(args, wl):
         tickets = []
         log(f"[serve] mode {mode}: replaying {len(trace)} requests over {args.serve_warmup + args.duration}s")
         t0 = time.perf_counter()
-        for (ta, kind, eps, L, src, cols, seed) in trace:
+        for i_tr, (ta, kind, eps, L, src, cols, seed) in enumerate(trace):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
             p = params_of(kind, eps, L, seed)
             tk = srv.submit(p, X=X[:, :cols]) if kind == "features" else srv.submit(p, source=src)
             with lock:
-                arrival[tk] = ta
+                arrival[tk] = (ta, i_tr)
             tickets.append(tk)
         submitted_by = time.perf_counter() - t0
         # the window closes at warm-up + duration + drain; a request counts when it completes inside
@@ -715,12 +732,53 @@ def run_serve(args, wl):
         log(f"[serve] mode {mode}: stopped after {time.perf_counter() - t0:.1f}s")
         lat = np.array(lat) if lat else np.array([np.nan])
         offered = sum(1 for tr in trace if tr[0] >= args.serve_warmup)
-        return {"offered": offered, "completed": done, "completed_arrived_in_window": done_arrived,
-                "queries_per_s": done / elapsed,
-                "p50_ms": float(np.nanpercentile(lat, 50)), "p99_ms": float(np.nanpercentile(lat, 99)),
-                "elapsed_s": elapsed, "submit_s": submitted_by, "sweeps": st["sweeps"]}
+        out = {"offered": offered, "completed": done, "completed_arrived_in_window": done_arrived,
+               "queries_per_s": done / elapsed,
+               "p50_ms": float(np.nanpercentile(lat, 50)), "p99_ms": float(np.nanpercentile(lat, 99)),
+               "elapsed_s": elapsed, "submit_s": submitted_by, "sweeps": st["sweeps"]}
+        if check:
+            out["accuracy"] = serve_accuracy(kept)
+        return out
 
-    batched = replay(agp.SERVE_BATCHED)
+    og_cache = []
+
+    def serve_accuracy(kept):
+        """Served single-source results (L <= 12, arrived in the window) against the exact FP64
+        propagation: the same measures as the batched step's accuracy."""
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        if not kept:
+            return None
+        if not og_cache:
+            og_cache.append(oracle.build_csr(n, u, v))
+        og = og_cache[0]
+        weights = {"ppr": (oracle.PPR, 0.2), "katz": (oracle.KATZ, beta), "hkpr": (oracle.HKPR, 5.0),
+                   "transition": (oracle.TRANSITION, 0.0)}
+
+        def one(item):
+            i_tr, row = item
+            _, kind, eps, L, src, _, _ = trace[i_tr]
+            wk, prm = weights[kind]
+            w, Y = oracle.tail_sums(wk, L, prm)
+            return row_accuracy(og, kind, 0.0, 1.0 if kind != "katz" else 0.0, L, w, Y, eps, src, row)
+
+        t0_ = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=max(1, min(host_cores(), len(kept)))) as ex:
+            per = list(ex.map(one, kept))
+        summ = {}
+        for name in ("paper", "chebyshev"):
+            vals = [r[f"frac_ok_{name}"] for r in per if r[f"frac_ok_{name}"] is not None]
+            summ[f"frac_ok_at_delta_{name}"] = {"min": float(min(vals)) if vals else None,
+                                               "mean": float(np.mean(vals)) if vals else None, "queries": len(vals)}
+        summ["rel_l1_max"] = float(max(r["rel_l1"] for r in per))
+        d99 = [r["delta_99"] for r in per if r["delta_99"] is not None]
+        summ["delta_99"] = {"max": float(max(d99)) if d99 else None, "median": float(np.median(d99)) if d99 else None}
+        summ["queries_checked"] = len(per)
+        summ["oracle_s"] = time.perf_counter() - t0_
+        summ["per_query"] = per
+        return summ
+
+    batched = replay(agp.SERVE_BATCHED, check=not args.no_accuracy)
     batched_fifo = replay(agp.SERVE_BATCHED, agp.ADMIT_FIFO)
     fifo = replay(agp.SERVE_FIFO_PLAIN) if not args.no_fifo else None
     line = {"metric": "served queries/s (continuous batching)", "value": batched["queries_per_s"], "unit": "queries/s",

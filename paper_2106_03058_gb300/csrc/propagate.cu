@@ -789,7 +789,7 @@ __device__ __forceinline__ uint2 expand_item(const KArgs &A, unsigned long long 
             } else if (p0 >= kDenseP && !P.sampler) {
                 is_dense = true;  // most positions are kept: one Bernoulli per position in the walk
             } else {
-                int ns = (int)fminf(ceilf(expect / kLightSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
+                int ns = (int)fminf(ceilf(expect / kSegSamples), (float)((tail + kMinSeg - 1) / kMinSeg));
                 ns = max(ns, 1);
                 seglen = (tail + ns - 1) / ns;
                 nseg += (tail + seglen - 1) / seglen;
