@@ -45,13 +45,13 @@ HBM_FALLBACK_GBS = 6800.0
 #   accepted sample:        residue atomic RMW 8
 B_ITEM, B_DET, B_TRIAL, B_ACC, B_DEG, B_COMPACT_ITEM, B_SCAN = 28, 12, 4, 8, 4, 12, 8
 
-# DRAM traffic of k_push per L2 reduction, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over lts__t_sectors_srcunit_tex_op_red.sum, all 52 k_push launches of a step
-# of 8 Katz + 8 transition sources at four lanes per wave, warm L2). It scales a launch of the bench
-# step by its reductions, for a four-lane wave only. None while it is not measured for the current
-# split of tails between the samplers: it was 11.0 B with dense per-position sampling from p >= 1/8,
-# and per-position sampling now starts at p >= 1/4, which changes the kernel's mix of work.
-PUSH_DRAM_BYTES_PER_RED, PUSH_TRAFFIC_LANES = None, 4
+# DRAM traffic of k_push per L2 reduction, from one ncu capture with warm caches
+# (dram__bytes_read.sum + dram__bytes_write.sum over lts__t_sectors_srcunit_tex_op_red.sum, three
+# k_push launches of a step of 64 Katz + 64 transition sources at four lanes per wave; see
+# profiles/launch_list_katz_transition_4M.md). It scales a launch of the bench step by its
+# reductions, for a four-lane wave only. Per launch it ranged from 16.4 to 26.6 B, so the scaled
+# figure is an estimate. It must be re-measured whenever the push kernel changes.
+PUSH_DRAM_BYTES_PER_RED, PUSH_TRAFFIC_LANES = 18.3, 4
 
 
 def log(*a):

@@ -16,6 +16,9 @@ namespace agp {
 constexpr int kMaxLevels = AGP_MAX_LEVELS;
 constexpr int kChunk = 512;          // prefix edges per chunk record (one warp)
 constexpr int kMinBlocks = 4;        // resident CTAs per SM the level kernels are compiled for
+constexpr int kCompactBlocks = 4;    // resident CTAs per SM of the compaction kernels; their grid is
+                                     // this many per SM, so that every range is resident at once
+constexpr int kCountBatch = 8;       // units per step of the count pass (loads in flight per thread)
 constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
 constexpr float kLightSamples = 8.f; // tails expected to yield at most this many trials stay inline
 constexpr int kMinSeg = 256;         // shortest tail segment of a segment record

@@ -435,15 +435,37 @@ __device__ __forceinline__ void compact_range(const KArgs &A, int64_t &begin, in
     end = min(U, begin + per);
 }
 
-template <int W>
-__device__ __forceinline__ float4 *unit_ptr(const KArgs &A, int64_t unit, int &grp, int64_t &off_f, bool &live)
+// Position of a unit: its group and its index in the group's block. A block's units are
+// consecutive, so the cursor is set once by a division and then advanced unit by unit.
+struct UnitCursor {
+    int grp;
+    int64_t uig;
+};
+
+__device__ __forceinline__ UnitCursor unit_cursor(const KArgs &A, int64_t unit)
 {
-    grp = (int)(unit / A.units);
+    UnitCursor c;
+    c.grp = (int)(unit / A.units);
+    c.uig = unit - (int64_t)c.grp * A.units;
+    return c;
+}
+
+__device__ __forceinline__ void unit_next(const KArgs &A, UnitCursor &c)
+{
+    if (++c.uig == A.units) {
+        c.uig = 0;
+        ++c.grp;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ float4 *unit_at(const KArgs &A, const UnitCursor &c, int64_t &off_f, bool &live)
+{
     live = false;
 #pragma unroll
-    for (int j = 0; j < W; ++j) live |= A.level[grp * W + j] >= 0;
-    off_f = (unit - (int64_t)grp * A.units) * kScanUnit;  // float offset of the unit in its group block
-    return (float4 *)(A.R + (size_t)grp * A.ldR * W + off_f);
+    for (int j = 0; j < W; ++j) live |= __ldg(A.level + c.grp * W + j) >= 0;
+    off_f = c.uig * kScanUnit;  // float offset of the unit in its group block
+    return (float4 *)(A.R + (size_t)c.grp * A.ldR * W + off_f);
 }
 
 // frontier items in one float4 of a group block: nodes with a non-zero lane
@@ -487,7 +509,7 @@ __device__ __forceinline__ void compact_emit_body(const KArgs &A);
 __device__ __forceinline__ bool compact_one_pass(const KArgs &A);
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
+__global__ void __launch_bounds__(kBlock, kCompactBlocks) k_compact_count(KArgs A)
 {
     if (compact_one_pass(A)) {
         compact_emit_body<W, true>(A);
@@ -499,11 +521,31 @@ __global__ void __launch_bounds__(kBlock) k_compact_count(KArgs A)
     compact_range(A, begin, end);
     unsigned long long c = 0;
     const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t unit = begin; unit < end; ++unit) {
-        int grp;
+    // without pull levels the pass only counts: kCountBatch units at a time, so that as many loads
+    // of each thread are in flight together
+    const int64_t batched_end = A.C ? begin : end;
+    UnitCursor cur = unit_cursor(A, begin);
+    for (int64_t u0 = begin; u0 < batched_end; u0 += kCountBatch) {
+        float4 v[kCountBatch];
+#pragma unroll
+        for (int j = 0; j < kCountBatch; ++j) {
+            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (u0 + j < end) {
+                int64_t off_f;
+                bool live;
+                const float4 *p = unit_at<W>(A, cur, off_f, live);
+                if (live) v[j] = p[threadIdx.x];
+            }
+            unit_next(A, cur);
+        }
+#pragma unroll
+        for (int j = 0; j < kCountBatch; ++j) c += nz_items<W>(v[j]);
+    }
+    for (int64_t unit = A.C ? begin : end; unit < end; ++unit, unit_next(A, cur)) {
+        const int grp = cur.grp;
         int64_t off_f;
         bool live;
-        const float4 *p = unit_ptr<W>(A, unit, grp, off_f, live);
+        const float4 *p = unit_at<W>(A, cur, off_f, live);
         if (!live) continue;  // uniform over the block
         const float4 v = p[threadIdx.x];
         c += nz_items<W>(v);
@@ -599,6 +641,25 @@ __global__ void __launch_bounds__(1024) k_compact_scan(KArgs A)
 // (lane, node) at frontier density rho (W = 1) against 8 + 8 rho, the better choice below rho = 1/4.
 // The staging list is the c_item / k_item storage, which the expansion of the level rewrites.
 constexpr int kEmitBatch = 4;
+// Residues of the units u0 .. u0 + kEmitBatch - 1 (cursor at u0); returns the cursor after them.
+template <int W>
+__device__ __forceinline__ UnitCursor load_batch(const KArgs &A, UnitCursor cur, int64_t u0, int64_t end,
+                                                 float4 (&v)[kEmitBatch])
+{
+#pragma unroll
+    for (int j = 0; j < kEmitBatch; ++j) {
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u0 + j < end) {
+            int64_t off_f;
+            bool live;
+            const float4 *p = unit_at<W>(A, cur, off_f, live);
+            if (live) v[j] = p[threadIdx.x];
+        }
+        unit_next(A, cur);
+    }
+    return cur;
+}
+
 template <int W, bool kLocal>
 __device__ __forceinline__ void compact_emit_body(const KArgs &A)
 {
@@ -610,6 +671,10 @@ __device__ __forceinline__ void compact_emit_body(const KArgs &A)
     float *rval = kLocal ? A.c_item + begin * (kScanUnit / W) * W : A.rval;
     unsigned long long run = kLocal ? 0ull : (unsigned long long)A.part[blockIdx.x];
     int parity = 0;
+    // the next batch's residues are loaded while the current one is scanned and written
+    float4 v_next[kEmitBatch];
+    UnitCursor cur = unit_cursor(A, begin);  // at u0
+    UnitCursor nxt = load_batch<W>(A, cur, begin, end, v_next);  // at u0 + kEmitBatch
     for (int64_t u0 = begin; u0 < end; u0 += kEmitBatch, parity ^= 1) {
         float4 v[kEmitBatch];
         float4 *ptr[kEmitBatch];
@@ -618,19 +683,19 @@ __device__ __forceinline__ void compact_emit_body(const KArgs &A)
         unsigned long long packed = 0;
 #pragma unroll
         for (int j = 0; j < kEmitBatch; ++j) {
-            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            v[j] = v_next[j];
             ptr[j] = nullptr;
-            grps[j] = 0;
+            grps[j] = cur.grp;
             offs[j] = 0;
             if (u0 + j < end) {
                 bool live;
-                float4 *p = unit_ptr<W>(A, u0 + j, grps[j], offs[j], live);
-                if (live) {
-                    ptr[j] = p;
-                    v[j] = p[threadIdx.x];
-                }
+                float4 *p = unit_at<W>(A, cur, offs[j], live);
+                if (live) ptr[j] = p;
             }
+            unit_next(A, cur);
         }
+        // cur is now at u0 + kEmitBatch (= nxt); prefetch the batch after it
+        nxt = load_batch<W>(A, nxt, u0 + kEmitBatch, end, v_next);
 #pragma unroll
         for (int j = 0; j < kEmitBatch; ++j) packed |= (unsigned long long)nz_items<W>(v[j]) << (16 * j);
         unsigned long long x = packed;  // inclusive warp scan of the packed counts
@@ -716,7 +781,7 @@ __device__ __forceinline__ void compact_gather(const KArgs &A)
 __device__ __forceinline__ bool compact_one_pass(const KArgs &A) { return !A.C && A.ctrl->scan_mode == 0; }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_compact_emit(KArgs A)
+__global__ void __launch_bounds__(kBlock, kCompactBlocks) k_compact_emit(KArgs A)
 {
     if (compact_one_pass(A)) compact_gather<W>(A);
     else compact_emit_body<W, false>(A);
@@ -902,7 +967,13 @@ __device__ __forceinline__ void item_range(const KArgs &A, unsigned long long &b
 template <int W>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
 {
-    __shared__ unsigned long long tot_s[2][kBlock / 32];
+    // block totals of the two record kinds, gathered without a closing barrier: every warp adds its
+    // totals, and the last warp to finish writes them (warps that finish early leave at once)
+    __shared__ unsigned long long tot_s[2];
+    __shared__ unsigned int warps_done;
+    if (threadIdx.x < 2) tot_s[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) warps_done = 0u;
+    __syncthreads();
     unsigned long long begin, end;
     item_range(A, begin, end);
     // per-thread record totals (32-bit: a thread's items have far fewer than 2^32 records; the
@@ -927,13 +998,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_expand(KArgs A)
         wt[t] = tot[t];
         for (int o = 16; o > 0; o >>= 1) wt[t] += __shfl_down_sync(0xffffffffu, wt[t], o);
     }
-    if ((threadIdx.x & 31) == 0)
-        for (int t = 0; t < 2; ++t) tot_s[t][threadIdx.x >> 5] = wt[t];
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        unsigned long long s = 0;
-        for (int w = 0; w < kBlock / 32; ++w) s += tot_s[threadIdx.x][w];
-        A.rpart[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&tot_s[0], wt[0]);
+        atomicAdd(&tot_s[1], wt[1]);
+        __threadfence_block();  // the sums before the count of finished warps
+        if (atomicAdd(&warps_done, 1u) == kBlock / 32 - 1) {
+            __threadfence_block();
+            A.rpart[blockIdx.x] = atomicAdd(&tot_s[0], 0ull);
+            A.rpart[(size_t)gridDim.x + blockIdx.x] = atomicAdd(&tot_s[1], 0ull);
+        }
     }
 }
 
@@ -1709,7 +1782,9 @@ int create_workspace(agp_graph_s *g, int G, int W, Workspace **out, int grid)
     auto A = [&](int r) { if (rc == AGP_OK) rc = r; };
     const int64_t units = (int64_t)groups * (ws->ldR * W / kScanUnit);
     ws->grid = grid > 0 ? grid : grid_stride_blocks();
-    ws->part_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid, units));
+    // compaction ranges: one resident CTA each (kCompactBlocks per SM), at most the workspace's grid
+    ws->part_blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)ws->grid, (int64_t)kCompactBlocks * sm_count(), units}));
     A(dev_alloc(&ws->R, (size_t)G * ws->ldR, acc));
     A(dev_alloc(&ws->items, ws->cap_items, acc));
     A(dev_alloc(&ws->rval, ws->cap_items * W, acc));
@@ -2384,9 +2459,6 @@ int query_batch_ctx(agp_graph_s *g, ExecCtx *ctx, const agp_params_t *params, in
         return fail(AGP_EINVAL, "AGP_COLLECT_STATS / AGP_QUERY_TIMES need stats");
     for (int i = 0; i < n_params; ++i) AGP_TRY(validate_params_for(g, params[i]));
     AGP_CUDA_TRY(cudaSetDevice(g->device));
-    const bool plain = flags & AGP_PLAIN;
-    const bool profile = flags & AGP_PROFILE;
-    const int collect = (flags & AGP_COLLECT_STATS) ? 1 : 0;
     const int64_t n = g->n;
 
     // --- inputs on the device
