@@ -991,10 +991,27 @@ def main():
         ceil = atomic_ceiling(g, lanes, n)
         push_adds = (work[1, 0] + work[1, 2]) / args.steps
         rate = push_adds / (kern_ms["push"] / args.steps / 1e3)
+        # the same rate for one wave alone (the step's first `lanes` Katz queries as a call of their
+        # own: one wave, so no second wave shares the GPU with its pushes)
+        pk0, _ = all_params[args.warmup]
+        one_off = off[:lanes + 1]
+        agp.profile_read(g, reset=True)
+        agp.query_batch(g, pk0[:lanes], one_off, d_srcs[args.warmup * 2 * Q:args.warmup * 2 * Q + lanes], None,
+                        out_k, n, flags | agp.PROFILE)
+        one_ms, _, _ = agp.profile_read(g, reset=True)
+        st1 = agp.query_batch(g, pk0[:lanes], one_off, d_srcs[args.warmup * 2 * Q:args.warmup * 2 * Q + lanes],
+                              None, out_k, n, flags | agp.COLLECT_STATS)
+        w1 = sum(np.array([list(r) for r in s_.by_kernel], dtype=np.float64) for s_ in st1)
+        one_rate = (w1[1, 0] + w1[1, 2]) / (one_ms["push"] / 1e3) if one_ms["push"] > 0 else None
         atomics = {"push_adds_per_step": push_adds, "push_adds_per_s": rate,
                    "ceiling_adds_per_s": ceil, "frac_of_degree_weighted": rate / ceil["degree_weighted"],
+                   "one_wave_alone": {"push_adds_per_s": one_rate,
+                                      "frac_of_degree_weighted": (one_rate / ceil["degree_weighted"]
+                                                                  if one_rate else None),
+                                      "queries": int(lanes), "kind": "katz"},
                    "note": "push time from CUDA events around every k_push of the timed steps, which "
-                           "include the other wave's kernels sharing the GPU (an upper bound on its time)"}
+                           "include the other wave's kernels sharing the GPU (an upper bound on its time); "
+                           "one_wave_alone times the pushes of one Katz wave run by itself"}
 
     # ---- plain path: one query per launch sequence, host-synchronised frontier sizes. The same
     # queries run on both paths after a warm-up of each; a query's latency is its completion time
