@@ -19,10 +19,10 @@ constexpr int kMinBlocks = 4;        // resident CTAs per SM the level kernels a
 constexpr int kCompactBlocks = 4;    // resident CTAs per SM of the compaction kernels; their grid is
                                      // this many per SM, so that every range is resident at once
 constexpr int kCountBatch = 8;       // units per step of the count pass (loads in flight per thread)
-constexpr int kInlineDet = 32;       // prefixes up to this length stay with the expanding thread
-constexpr float kLightSamples = 8.f; // tails expected to yield at most this many trials stay inline
+constexpr int kInlineDet = 64;       // prefixes up to this length are pushed inline by the expansion
+constexpr float kLightSamples = 16.f; // tails expected to yield at most this many trials stay inline
 constexpr int kMinSeg = 256;         // shortest tail segment of a segment record
-constexpr float kSegSamples = 32.f;  // expected trials of one segment record (a thread's share of a
+constexpr float kSegSamples = 64.f;  // expected trials of one segment record (a thread's share of a
                                      // heavy tail; its setup is a chain of dependent loads)
 constexpr float kDenseP = 0.25f;     // tails whose largest probability is >= this are sampled per position
 constexpr uint32_t kOffsetsOnHost = 0x80000000u;  // internal query flag: x_off is host memory even
