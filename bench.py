@@ -915,13 +915,16 @@ def main():
         g.set_group_width(args.width)
         lanes = args.lanes
     else:
-        qs = min(Q, 32)
-        pk, _ = all_params[0]
+        # the sample has the step's mix: half Katz, half transition queries of the first step
+        h = min(Q, 16)
+        qs = 2 * h
+        pk, pt = all_params[0]
         t0 = time.perf_counter()
-        lanes, width, tuned_ms = agp.autotune(g, pk[:qs], off[:qs + 1], d_srcs[:qs], None, out_k, n,
-                                       candidates=[c for c in (1, 2, 4, 8, 16, 32) if c <= 2 * qs])
-        log(f"[bench] autotuned wave width {lanes} lanes, group width {width} ({tuned_ms:.1f} ms for {qs} Katz queries, "
-            f"{time.perf_counter() - t0:.1f}s)")
+        sample_src = torch.cat([d_srcs[:h], d_srcs[Q:Q + h]])
+        lanes, width, tuned_ms = agp.autotune(g, list(pk[:h]) + list(pt[:h]), off[:qs + 1], sample_src, None, out_k,
+                                              n, candidates=[c for c in (1, 2, 4, 8, 16, 32) if c <= 2 * qs])
+        log(f"[bench] autotuned wave width {lanes} lanes, group width {width} ({tuned_ms:.1f} ms for {h} Katz + "
+            f"{h} transition queries, {time.perf_counter() - t0:.1f}s)")
 
     for k in range(args.warmup):
         run_step(k)
