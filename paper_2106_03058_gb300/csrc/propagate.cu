@@ -10,12 +10,14 @@
 // One level of all lanes of a wave (Algorithm 2, inner loop over u with r^(i)(u) != 0):
 //   k_compact_count / _scan / _emit   dense scan of the lanes' residue vectors: the frontier
 //              F_i = {(lane, u) : r^(i)(u) != 0} as an ascending item list with the values
-//              r^(i)(u); the vectors are cleared as they are read.
+//              r^(i)(u); the vectors are cleared as they are read. Dense levels count, scan and
+//              emit (two reads); sparse levels emit to per-block staging, scan and move (one read).
 //   k_expand   one thread per item: reserve pi(u) += (w_i/Y_i) r^(i)(u); c = (Y_{i+1}/Y_i) r / d_u^b;
 //              deterministic prefix length k(u) = number of neighbours with c / d_v^a >= eps
 //              (binary search over the degree-sorted row, all or nothing when a = 0). Short
-//              prefixes and light tails (few expected trials) are done inline; long prefixes,
-//              dense tails (p >= 1/4) and heavy sparse tails become records.
+//              prefixes (pushed by the whole warp at group width 1) and light tails (few expected
+//              trials) are done inline; long prefixes, dense tails (p >= 1/4) and heavy sparse
+//              tails become records.
 //   k_push     one warp per 512-position record: r^(i+1)(v) += c / d_v^a over a prefix chunk, or
 //              one Bernoulli trial per position of a dense-tail chunk (kept: += eps).
 //   k_sample   one thread per segment record of a sparse tail: subset sampling (Section 4) with
