@@ -352,6 +352,11 @@ def end_to_end(agp, g, args, all_params, srcs, Q, n, world, dev):
     h_out_k = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
     h_out_t = torch.empty((Q, n), dtype=torch.float32, pin_memory=True)
     e2e_times = []
+    # one untimed step through the host path first (its staging buffers are allocated on first use)
+    pk, pt = all_params[max(args.warmup - 1, 0)]
+    base = max(args.warmup - 1, 0) * 2 * Q
+    agp.query_batch(g, pk, h_off, h_srcs[base:base + Q], None, h_out_k, n, 0)
+    agp.query_batch(g, pt, h_off, h_srcs[base + Q:base + 2 * Q], None, h_out_t, n, 0)
     torch.cuda.synchronize()
     for k in range(args.steps):
         pk, pt = all_params[args.warmup + k]

@@ -87,6 +87,7 @@ struct Ctrl {
     unsigned int error;          // 1: frontier overflow, 2: chunk overflow, 4: segment overflow, 16: bad level
     unsigned int lanes_used;     // lanes [0, lanes_used) hold work; the compaction scans only those
     unsigned int scan_mode;      // compaction of the next level: 0 one pass (sparse frontier), 1 two passes
+    unsigned long long prev_items;  // frontier size of the previous level (growth of the frontier)
 };
 
 constexpr int kProfKernels = 5;  // compact, expand, push, sample, level end

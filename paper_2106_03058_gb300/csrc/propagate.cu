@@ -1410,11 +1410,14 @@ __global__ void k_level_end(KArgs A)
     if (threadIdx.x == 0) {
         ctrl->n_det = 0;
         ctrl->n_smp = 0;
-        // the next level's compaction form, predicted from this level's frontier density: one pass
-        // below 1/16 of the scanned (group, node) pairs (break-even is 1/4; a frontier can grow
-        // several-fold in one level)
+        // the next level's compaction form: the frontier density predicted as this level's, times
+        // its growth over the previous level when it grew; one pass below a predicted 1/6 of the
+        // scanned (group, node) pairs (the break-even of the two forms is 1/4)
         const unsigned long long groups = (min((int)ctrl->lanes_used, A.G) + A.W - 1) / A.W;
-        ctrl->scan_mode = (ctrl->n_items * 16ull < groups * (unsigned long long)A.ldR) ? 0u : 1u;
+        const unsigned long long items = ctrl->n_items, prev = ctrl->prev_items;
+        const double grow = (prev > 0 && items > prev) ? (double)items / (double)prev : 1.0;
+        ctrl->scan_mode = ((double)items * grow * 6.0 < (double)(groups * (unsigned long long)A.ldR)) ? 0u : 1u;
+        ctrl->prev_items = items;
     }
 }
 
