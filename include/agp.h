@@ -474,6 +474,24 @@ AGP_API int agp_topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t 
                      int64_t ldo, void *stream);
 
 /*
+ * Approximation quality of an estimate against a reference (Section 6, local clustering with HKPR,
+ * and the Katz experiments of the appendix): MaxError = max_v |pi_est(v)/d_v - pi_ref(v)/d_v|
+ * (normalised by the degree) and Precision@k = |V_k ∩ V_hat_k| / k, where V_k and V_hat_k are the k
+ * nodes of largest normalised reference and estimated value. With deg = NULL both use the plain
+ * values (the Katz form of MaxError). A node with d_v = 0 has normalised value 0. MaxError is taken
+ * in FP64 from the FP32 inputs. The top-k sets use agp_topk's order (value descending, ties by
+ * ascending id) on the FP32 normalised values, so they are unique.
+ *   pi_est, pi_ref  device FP32 n-vectors (no NaN)
+ *   deg             device int32 n-vector (a graph's degrees, see agp_graph_info) or NULL
+ *   k               1 <= k <= min(n, 2048), read only when precision_at_k is not NULL
+ *   max_error       host, required; precision_at_k host or NULL
+ * Allocates device scratch for the call (two n-vectors when normalising for Precision@k) and
+ * synchronises the stream. Errors: AGP_EINVAL, AGP_ENOMEM, AGP_ECUDA.
+ */
+AGP_API int agp_compare(const float *pi_est, const float *pi_ref, int64_t n, const int32_t *deg, int32_t k,
+                        double *max_error, double *precision_at_k, void *stream);
+
+/*
  * Level coefficients of Def. 3.1 as the level pipeline computes them on the device (FP64), for a
  * signal part of unit L1 norm: with Y_i = sum_{k>=i} w_k,
  *     keep[i] = Y_0 * w_i / Y_i   (reserve factor of level i: pi(u) += keep[i] * r^(i)(u)),

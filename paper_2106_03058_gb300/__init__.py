@@ -114,6 +114,7 @@ def lib():
                                           C.POINTER(Stats), _vp]
             L.agp_sweep.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_i64), _vp]
             L.agp_topk.argtypes = [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _i64, _vp]
+            L.agp_compare.argtypes = [_vp, _vp, _i64, _vp, _i32, C.POINTER(_dbl), C.POINTER(_dbl), _vp]
             L.agp_coefficients.argtypes = [C.POINTER(Params), _vp, _vp, C.POINTER(_dbl), C.c_int, _vp]
             L.agp_profile_read.argtypes = [_vp, C.POINTER(_dbl), C.POINTER(_i64), C.POINTER(_i64), C.c_int]
             L.agp_graph_set_wave_lanes.argtypes = [_vp, _i32]
@@ -140,7 +141,7 @@ def lib():
             for f in ("agp_build_graph", "agp_graph_info", "agp_graph_destroy", "agp_graph_set_memory_budget",
                       "agp_query_batch", "agp_query", "agp_feature_propagate", "agp_katz_beta", "agp_threshold",
                       "agp_profile_read", "agp_graph_set_wave_lanes", "agp_autotune", "agp_coefficients", "agp_query_dense",
-                      "agp_graph_set_group_width", "agp_topk", "agp_sweep", "agp_graph_set_column_tile",
+                      "agp_graph_set_group_width", "agp_topk", "agp_compare", "agp_sweep", "agp_graph_set_column_tile",
                       "agp_graph_set_pull_threshold"):
                 getattr(L, f).restype = C.c_int
             _lib = L
@@ -540,6 +541,17 @@ def topk(pi, k, stream=None):
     _check("agp_topk", lib().agp_topk(pi.data_ptr(), n, int(pi.stride(0)), Q, int(k), val.data_ptr(), idx.data_ptr(),
                                        k, _stream(stream)))
     return val, idx
+
+
+def compare(pi_est, pi_ref, deg=None, k=None, stream=None):
+    """``agp_compare`` on CUDA float32 n-vectors: returns (MaxError, Precision@k or None). deg: the
+    graph's int32 degrees (CUDA) to normalise by d_v, or None for the plain values."""
+    n = int(pi_est.numel())
+    me, pk = _dbl(), _dbl()
+    _check("agp_compare", lib().agp_compare(pi_est.data_ptr(), pi_ref.data_ptr(), n,
+                                             deg.data_ptr() if deg is not None else None, int(k or 0), C.byref(me),
+                                             C.byref(pk) if k else None, _stream(stream)))
+    return me.value, (pk.value if k else None)
 
 
 def sweep(g, pi, stream=None):

@@ -140,6 +140,8 @@ int sweep(agp_graph_s *g, const float *pi, int32_t *order_out, double *phi_out, 
           int64_t *swept, cudaStream_t s);
 int topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t k, float *val, int32_t *idx, int64_t ldo,
          cudaStream_t s);
+int compare(const float *pi_est, const float *pi_ref, int64_t n, const int32_t *deg, int32_t k, double *max_error,
+            double *precision_at_k, cudaStream_t s);
 int coefficients(const agp_params_t *p, double *keep, double *push, double *y0, int device, cudaStream_t s);
 int validate_params(const agp_params_t &p);
 int threshold(agp_graph_s *g, double a, double eps, int64_t count, const int32_t *nodes,

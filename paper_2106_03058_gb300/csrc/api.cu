@@ -397,6 +397,12 @@ int agp_topk(const float *pi, int64_t n, int64_t ld, int32_t Q, int32_t k, float
     return agp::topk(pi, n, ld, Q, k, val, idx, ldo, (cudaStream_t)stream);
 }
 
+int agp_compare(const float *pi_est, const float *pi_ref, int64_t n, const int32_t *deg, int32_t k, double *max_error,
+                double *precision_at_k, void *stream)
+{
+    return agp::compare(pi_est, pi_ref, n, deg, k, max_error, precision_at_k, (cudaStream_t)stream);
+}
+
 int agp_threshold(agp_graph_t g, double a, double eps, int64_t count, const int32_t *nodes, const float *c,
                   int32_t *k_out, void *stream)
 {
