@@ -362,7 +362,8 @@ AGP_API int agp_serve_wait(agp_server_t s, uint64_t ticket, int64_t timeout_us, 
  * *ticket and *out are filled (AGP_OK), or AGP_ETIMEDOUT when none finished in time. Every finished
  * request is reported once; one released before it is reported is skipped. A client that takes its
  * results this way can release each as it arrives, which keeps the result budget free for
- * admissions. */
+ * admissions. The queue of unreported completions is pruned of released requests, so a client that
+ * never calls this function does not make it grow without bound. */
 AGP_API int agp_serve_next(agp_server_t s, int64_t timeout_us, uint64_t *ticket, agp_result_t *out);
 /* Free the result buffer of a finished request (pending requests: AGP_EINVAL). */
 AGP_API int agp_serve_release(agp_server_t s, uint64_t ticket);

@@ -166,6 +166,16 @@ void finish(agp_server_s *S, Request *q, int status)
     q->t_done = now_us();
     ++S->completed;
     S->done_q.push_back(q->ticket);
+    // a client that waits ticket by ticket never takes these: drop the entries of released requests
+    // once the queue is much longer than the requests still held, so it stays bounded
+    if (S->done_q.size() > 2 * S->all.size() + 1024) {
+        std::deque<uint64_t> keep;
+        for (const uint64_t t : S->done_q) {
+            auto it = S->all.find(t);
+            if (it != S->all.end() && !it->second->released) keep.push_back(t);
+        }
+        S->done_q.swap(keep);
+    }
     S->cv_done.notify_all();
 }
 
