@@ -245,7 +245,7 @@ def run_reference(args, wl, rank):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = threads * args.steps / total
-    sample = (f"{threads} of the 256 L=4 transition queries of each step, one per host thread on all "
+    sample = (f"{threads} of the {wl['Q']} L=4 transition queries of each step, one per host thread on all "
               f"{threads} cores ({cpu_model()}); the oracle runs per-neighbour Bernoulli trials, and its eps=1e-8 "
               f"Katz queries take minutes each and are left out")
     line = {"impl": "reference", "metric": "queries/s", "value": value, "unit": "queries/s", "n_gpus": args.gpus,
@@ -1088,7 +1088,7 @@ def main():
         used, dt = oracle_sample(og, n, srcs[base:base + threads], eps, 4, threads)
         cpu = {"value": used / dt, "unit": "queries/s", "cores": used, "nproc": host_cores(), "cpu_model": cpu_model(),
                "kind": "oracle",
-               "sample": f"{used} of the 256 L=4 transition queries of one step, one per host thread on all "
+               "sample": f"{used} of the {Q} L=4 transition queries of one step, one per host thread on all "
                          f"{used} cores, FP64 Algorithm 2 with per-neighbour Bernoulli trials ({dt:.1f}s; CSR build "
                          f"{t_csr:.1f}s excluded; Katz queries at eps=1e-8 take minutes each in the oracle and are "
                          f"left out)"}
