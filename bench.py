@@ -272,6 +272,11 @@ def row_accuracy(og, kind, a, b, L, w, Y, eps, s_, row):
         res[f"nodes_{name}"] = int(big.sum())
         res[f"frac_ok_{name}"] = float(np.mean(rel[big] <= 0.1)) if big.any() else None
     res["rel_l1"] = float(np.abs(row - exact).sum() / np.abs(exact).sum())
+    # the paper's measures (appendix, Katz experiments): MaxError = max_v |pi(v) - pi_hat(v)| and
+    # Precision@50 = overlap of the 50 largest entries (ties by id)
+    res["max_error"] = float(np.abs(row.astype(np.float64) - exact).max())
+    top = lambda x: set(np.lexsort((np.arange(x.size), -x))[:50].tolist())
+    res["precision_at_50"] = len(top(row.astype(np.float64)) & top(exact)) / 50.0
     # the smallest delta at which >= 99% of the nodes with pi >= delta have relative error <= 0.1
     order = np.argsort(-exact)
     order = order[exact[order] > 0]
@@ -309,6 +314,8 @@ def accuracy_vs_oracle(og, checks, eps, beta, L_katz, threads):
                                            "mean": float(np.mean(vals)) if vals else None,
                                            "queries": len(vals)}
     summ["rel_l1_max"] = float(max(r["rel_l1"] for r in per))
+    summ["max_error_max"] = float(max(r["max_error"] for r in per))
+    summ["precision_at_50_min"] = float(min(r["precision_at_50"] for r in per))
     for kind in ("katz", "transition"):
         d99 = [r["delta_99"] for r in per if r["kind"] == kind and r["delta_99"] is not None]
         summ[f"delta_99_{kind}"] = {"max": float(max(d99)) if d99 else None,
@@ -776,6 +783,8 @@ def run_serve(args, wl):
             summ[f"frac_ok_at_delta_{name}"] = {"min": float(min(vals)) if vals else None,
                                                "mean": float(np.mean(vals)) if vals else None, "queries": len(vals)}
         summ["rel_l1_max"] = float(max(r["rel_l1"] for r in per))
+        summ["max_error_max"] = float(max(r["max_error"] for r in per))
+        summ["precision_at_50_min"] = float(min(r["precision_at_50"] for r in per))
         d99 = [r["delta_99"] for r in per if r["delta_99"] is not None]
         summ["delta_99"] = {"max": float(max(d99)) if d99 else None, "median": float(np.median(d99)) if d99 else None}
         summ["queries_checked"] = len(per)
